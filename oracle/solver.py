@@ -1,0 +1,315 @@
+"""Per-frame PNCG-IPC solve (oracle, FP64), Supp. A.
+
+One frame minimises E of Eq. (ipc_energy) from x^t with xhat = x^t + h v^t
+(Eq. varopt) by the Dai-Kou preconditioned nonlinear CG of Eq. (dk_direction)
+with the step rule of Eq. (step_size). Readings where the paper is silent:
+
+  * preconditioner: P = (3x3 diagonal blocks of H)^-1 per free vertex
+    (block-Jacobi; ``precond="scalar"`` gives the literal diag(H)^-1);
+  * step: alpha = min(alpha_upper, alpha_ccd, alpha_bar) with
+    alpha_upper = dhat / (2 max_i |p_i|), alpha_ccd = eta * min_k d_k /
+    max_{i in gel side of k} |p_i| (eta = 0.9), alpha_bar = -g^T p / p^T H p
+    (dropped when p^T H p <= 0); then Armijo backtracking (c = 1e-4, halve
+    up to 20 times). The Armijo test E(x + a p) <= E(x) + c a g^T p is
+    evaluated in its equivalent remainder form R(a) <= (1 - c) a |g^T p|,
+    R(a) = E(x + a p) - E(x) - a g^T p summed element by element;
+  * direction restart (beta = 0) when |y^T p| is negligible or the new p
+    is not a descent direction;
+  * stopping: max_i |g_i| (free DOFs) <= tol * g_ref, g_ref = kappa * dhat;
+  * indenter motion: the indenter vertices move on the straight path
+    y(s) = (1 - s) y^t + s y^{t+1}; s advances in substeps of at most
+    eta * min_k d_k / max_j |y_j^{t+1} - y_j^t| (the gel held fixed), each
+    followed by PNCG to tol_advance (1e-2) relative, the last (s = 1) to tol;
+  * candidate set: rebuilt whenever the accumulated motion bound since the
+    last build would exceed the margin m (= dhat), so pairs outside the set
+    stay farther than dhat;
+  * friction lag (lambda_n, normal, closest-point weights) from x^t with the
+    indenter at y^t, once per frame.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from . import broadphase as BP
+from . import energy as En
+from . import geometry as G
+
+CONVERGED, MAXITER, NONFINITE, LINESEARCH = 0, 1, 2, 3
+
+
+@dataclasses.dataclass
+class Params:
+    tol: float = 1e-6
+    tol_advance: float = 1e-2
+    max_iter: int = 10000
+    eta: float = 0.9
+    armijo_c: float = 1e-4
+    max_halvings: int = 20
+    max_substeps: int = 1000
+    margin_factor: float = 1.0        # m = margin_factor * dhat
+    precond: str = "block"
+
+
+@dataclasses.dataclass
+class State:
+    x: np.ndarray        # [V, 3] positions
+    v: np.ndarray        # [V, 3] velocities
+    pose: np.ndarray     # [6] indenter pose of this state
+
+
+def rest_state(pad, pose):
+    return State(x=pad.rest.copy(), v=np.zeros_like(pad.rest), pose=np.asarray(pose, np.float64).copy())
+
+
+def precondition(blk, free, mode):
+    """P per vertex: inverse of the 3x3 diagonal block (block mode) or of its
+    diagonal (scalar mode); zero on Dirichlet vertices."""
+    P = np.zeros_like(blk)
+    if mode == "block":
+        P[free] = np.linalg.inv(blk[free])
+    else:
+        dg = np.einsum("nii->ni", blk[free])
+        P[free] = np.einsum("ni,ij->nij", 1.0 / dg, np.eye(3))
+    return P
+
+
+def apply_P(P, v):
+    return np.einsum("nij,nj->ni", P, v)
+
+
+def vnorm_max(v):
+    """max over vertices of the Euclidean norm."""
+    return float(np.sqrt((v * v).sum(axis=1)).max()) if v.size else 0.0
+
+
+def ccd_bound(fr, x, p, s, pairs, eta):
+    """eta * min_k d_k / max_{gel slots of k} |p_i| over the candidates."""
+    if len(pairs) == 0:
+        return np.inf
+    d, w, (ty, gid, iid) = En.distances(pairs, x, fr.y(s), fr.pad, fr.ind)
+    pn = np.sqrt((p * p).sum(axis=1))
+    pk = np.zeros(len(pairs))
+    for sl in range(4):
+        m = gid[:, sl] >= 0
+        pk[m] = np.maximum(pk[m], pn[gid[m, sl]])
+    ok = pk > 0
+    if not np.any(ok):
+        return np.inf
+    return float(np.min(eta * d[ok] / pk[ok]))
+
+
+def dk_beta(g_new, yv, p, P_new):
+    """Dai-Kou conjugate parameter of Eq. (dk_direction):
+        beta = g^T P y / y^T p - (y^T P y / y^T p) (p^T g / y^T p)
+    with g = g_{k+1}, y = g_{k+1} - g_k, p = p_k, P = P_{k+1}; 0 when y^T p
+    is negligible (restart)."""
+    yp = float(np.sum(yv * p))
+    if not (abs(yp) > 1e-300 and abs(yp) > 1e-14 * np.linalg.norm(yv) * np.linalg.norm(p)):
+        return 0.0
+    Py = apply_P(P_new, yv)
+    return float(np.sum(g_new * Py)) / yp - (float(np.sum(yv * Py)) / yp) * (float(np.sum(p * g_new)) / yp)
+
+
+def min_distance(fr, x, s, pairs):
+    if len(pairs) == 0:
+        return np.inf
+    d, _, _ = En.distances(pairs, x, fr.y(s), fr.pad, fr.ind)
+    return float(d.min())
+
+
+def remainder(fr, x, p, alpha, s, pairs):
+    """R(alpha) = E(x + alpha p) - E(x) - alpha g^T p, summed per element:
+    inertia (exact: alpha^2/2 p^T M p), each tet, each pair, each lagged
+    friction pair. +inf when the trial state inverts a tet or closes a gap."""
+    pad = fr.pad
+    y = fr.y(s)
+    xa = x + alpha * p
+    R = 0.5 * alpha * alpha * float(np.sum(pad.mass[:, None] * p * p))
+    # elasticity
+    F0 = En.deformation_gradient(x, pad)
+    F1 = En.deformation_gradient(xa, pad)
+    if np.any(np.linalg.det(F1) <= 0):
+        return np.inf
+    t = pad.tets
+    Dp = np.stack([p[t[:, 1]] - p[t[:, 0]], p[t[:, 2]] - p[t[:, 0]], p[t[:, 3]] - p[t[:, 0]]], axis=2)
+    dF = Dp @ pad.Dm_inv
+    P0 = En.first_piola(F0, pad.mu, pad.lam)
+    psi0 = En.neo_hookean_density(F0, pad.mu, pad.lam)
+    psi1 = En.neo_hookean_density(F1, pad.mu, pad.lam)
+    R += pad.h * pad.h * float(np.sum(pad.vol * (psi1 - psi0 - alpha * np.einsum("tij,tij->t", P0, dF))))
+    # barrier
+    if len(pairs):
+        d0, w, (ty, gid, iid) = En.distances(pairs, x, y, pad, fr.ind)
+        d1, _, _ = En.distances(pairs, xa, y, pad, fr.ind)
+        if np.any(d1 <= 0):
+            return np.inf
+        P = En._slot_positions(gid, iid, x, y)
+        r = np.einsum("ns,nsk->nk", w, P)
+        rhat = r / d0[:, None]
+        pslots = np.zeros(gid.shape + (3,))
+        gm = gid >= 0
+        pslots[gm] = p[gid[gm]]
+        ddot = np.einsum("ns,nsk,nk->n", w * gm, pslots, rhat)       # grad d . p
+        R += pad.kappa * float(np.sum(En.barrier(d1, pad.dhat) - En.barrier(d0, pad.dhat)
+                                      - alpha * En.barrier_d1(d0, pad.dhat) * ddot))
+    # friction
+    lag = fr.lag
+    if lag["lam"].size and pad.mu_f > 0:
+        eps = pad.eps_v
+        nrm = lag["n"]
+        Pi = np.eye(3)[None] - np.einsum("ni,nj->nij", nrm, nrm)
+        D0 = En._friction_disp(lag, x, fr.x_t, y, fr.y_t)
+        D1 = En._friction_disp(lag, xa, fr.x_t, y, fr.y_t)
+        tD0 = np.einsum("nij,nj->ni", Pi, D0)
+        tD1 = np.einsum("nij,nj->ni", Pi, D1)
+        s0, s1 = np.linalg.norm(tD0, axis=1), np.linalg.norm(tD1, axis=1)
+        gid, w = lag["gid"], lag["w"]
+        pd = np.zeros_like(D0)
+        for sl in range(4):
+            m = gid[:, sl] >= 0
+            pd[m] += w[m, sl][:, None] * p[gid[m, sl]]
+        c = pad.mu_f * lag["lam"]
+        first = c * En.mollifier_d1_over_s(s0, eps) * np.einsum("ni,ni->n", tD0, pd)
+        R += float(np.sum(c * (En.mollifier(s1, eps) - En.mollifier(s0, eps)) - alpha * first))
+    return R
+
+
+@dataclasses.dataclass
+class FrameInfo:
+    status: int = CONVERGED
+    iters: int = 0
+    substeps: int = 0
+    rebuilds: int = 0
+    halvings: int = 0
+    grad_inf: float = 0.0
+    g_ref: float = 0.0
+    min_gap: float = np.inf
+    energy_monotone: bool = True
+
+
+def solve_frame(pad, ind, state, pose_next, prm=Params(), trace=None):
+    """Advance one frame from ``state`` to the indenter pose ``pose_next``.
+    Returns (new State, FrameInfo). ``trace``, if a list, receives per
+    iteration (x-step size, energy, |g|_inf)."""
+    info = FrameInfo(g_ref=pad.g_ref)
+    h, dhat = pad.h, pad.dhat
+    margin = prm.margin_factor * dhat
+    r_inf = dhat + margin
+    x_t = state.x.copy()
+    xhat = x_t + h * state.v
+    y_t = G.indenter_world(ind.verts, state.pose)
+    y_n = G.indenter_world(ind.verts, pose_next)
+    cand = BP.candidates(x_t, y_t, pad, ind, r_inf)
+    lag = En.friction_lag(cand, x_t, y_t, pad, ind)
+    fr = En.Frame(pad, ind, x_t, xhat, y_t, y_n, lag)
+    Dy = float(np.sqrt(((y_n - y_t) ** 2).sum(axis=1)).max())
+    free = pad.free
+    x = x_t.copy()
+    s, M = 0.0, 0.0
+    info.min_gap = min_distance(fr, x, s, cand)
+    tol_abs = prm.tol * pad.g_ref
+    tol_sub = max(prm.tol, prm.tol_advance) * pad.g_ref
+    while True:
+        if s < 1.0:
+            if Dy == 0.0:
+                ds = 1.0 - s
+            else:
+                dmin = min_distance(fr, x, s, cand)
+                ds = min(1.0 - s, prm.eta * dmin / Dy)
+                if M + ds * Dy > margin:
+                    cand = BP.candidates(x, fr.y(s), pad, ind, r_inf)
+                    info.rebuilds += 1
+                    M = 0.0
+                    dmin = min_distance(fr, x, s, cand)
+                    ds = min(1.0 - s, prm.eta * dmin / Dy, margin / Dy)
+            s = 1.0 if ds >= 1.0 - s else s + ds
+            M += ds * Dy
+            info.substeps += 1
+        E, g, blk = En.total(fr, x, s, cand)
+        if not np.isfinite(E):
+            info.status = NONFINITE
+            break
+        P = precondition(blk, free, prm.precond)
+        p = -apply_P(P, g)
+        target = tol_abs if s >= 1.0 else tol_sub
+        while np.abs(g[free]).max(initial=0.0) > target and info.iters < prm.max_iter:
+            pn = vnorm_max(p)
+            gTp = float(np.sum(g * p))
+            if pn == 0.0 or gTp >= 0.0:
+                p = -apply_P(P, g)
+                pn, gTp = vnorm_max(p), float(np.sum(g * p))
+            a_up = dhat / (2.0 * pn)
+            a_ccd = ccd_bound(fr, x, p, s, cand, prm.eta)
+            jet = En.total_line(fr, x, p, s, cand)
+            pHp = float(jet.dd)
+            a_bar = -gTp / pHp if pHp > 0 else np.inf
+            alpha = min(a_up, a_ccd, a_bar)
+            if M + alpha * pn > margin:
+                cand = BP.candidates(x, fr.y(s), pad, ind, r_inf)
+                info.rebuilds += 1
+                M = 0.0
+                a_ccd = ccd_bound(fr, x, p, s, cand, prm.eta)
+                alpha = min(a_up, a_ccd, a_bar)
+            accepted = False
+            for _ in range(prm.max_halvings + 1):
+                R = remainder(fr, x, p, alpha, s, cand)
+                if R <= (1.0 - prm.armijo_c) * alpha * (-gTp):
+                    accepted = True
+                    break
+                alpha *= 0.5
+                info.halvings += 1
+            if not accepted:
+                info.status = LINESEARCH
+                break
+            x = x + alpha * p
+            M += alpha * pn
+            E_new, g_new, blk_new = En.total(fr, x, s, cand)
+            if not np.isfinite(E_new):
+                info.status = NONFINITE
+                break
+            if E_new > E + 1e-9 * abs(E):
+                info.energy_monotone = False
+            info.min_gap = min(info.min_gap, min_distance(fr, x, s, cand))
+            P_new = precondition(blk_new, free, prm.precond)
+            z = apply_P(P_new, g_new)
+            beta = dk_beta(g_new, g_new - g, p, P_new)
+            p = -z + beta * p
+            if float(np.sum(g_new * p)) >= 0.0:
+                p = -z
+            g, P, E = g_new, P_new, E_new
+            info.iters += 1
+            if trace is not None:
+                trace.append((alpha * pn, E, float(np.abs(g[free]).max())))
+        if info.status != CONVERGED:
+            break
+        if s >= 1.0:
+            if np.abs(g[free]).max(initial=0.0) > target:
+                info.status = MAXITER
+            break
+        if info.substeps >= prm.max_substeps or info.iters >= prm.max_iter:
+            info.status = MAXITER
+            break
+    info.grad_inf = float(np.abs(g[free]).max(initial=0.0)) if info.status != NONFINITE else np.inf
+    new = State(x=x, v=(x - x_t) / h, pose=np.asarray(pose_next, np.float64).copy())
+    return new, info
+
+
+def markers(pad, x):
+    """Marker displacement (u_x, u_y) = sum_i w_i (x_i - X_i), first two
+    components, on the rest top-face triangle of each marker (Sec. 3.2)."""
+    u = x - pad.rest
+    return np.einsum("mk,mkc->mc", pad.marker_w, u[pad.marker_ids])[:, :2]
+
+
+def run(pad, ind, poses, prm=Params()):
+    """Run frames 1..F of a pose sequence [F+1, 6] from rest. Returns the
+    list of states (frame 0 = rest) and infos."""
+    st = rest_state(pad, poses[0])
+    states, infos = [st], []
+    for f in range(1, len(poses)):
+        st, info = solve_frame(pad, ind, st, poses[f], prm)
+        states.append(st)
+        infos.append(info)
+    return states, infos
