@@ -1,0 +1,197 @@
+/*
+ * tac.h -- C ABI of the batched PNCG-IPC gel-pad contact solve.
+ *
+ * Each frame solves, for every pad of the batch, the implicit-Euler
+ * incremental potential of the paper's Supplementary A, Eq. (ipc_energy):
+ *
+ *   E(x) = 1/2 (x - xhat)^T M (x - xhat) + h^2 Psi(x)
+ *          + kappa * sum_{k in C} b(d_k(x)) + D(x),   xhat = x^t + h v^t,
+ *
+ * with Neo-Hookean Psi over linear tetrahedra, the C^2 log barrier b over
+ * point-triangle / edge-edge pairs between the gel surface and a rigid
+ * triangle-mesh indenter, and the lagged friction D of Eq. (friction_energy)
+ * with the mollifier of Eq. (friction_mollifier). The minimiser is found by
+ * the Dai-Kou preconditioned nonlinear CG of Eq. (dk_direction) with a 3x3
+ * block-Jacobi preconditioner and the step rule of Eq. (step_size), bounded
+ * by a per-pair conservative step (CCD) and accepted by an Armijo test.
+ * Marker displacements are read out by barycentric interpolation of the
+ * deformed mesh (Sec. 3.2, "Tactile Representation").
+ *
+ * Units are SI. A pad lives in its own frame: rest vertices in float32,
+ * bottom-face Dirichlet vertices given explicitly, markers on the top face
+ * (the face at maximum rest z). An indenter pose is a rotation vector (3)
+ * followed by a translation (3) that maps the indenter's local vertices into
+ * the pad frame.
+ *
+ * Conventions:
+ *  - Every function returns TAC_OK (0) or a negative TAC_ERR_* code; the
+ *    message of the last error on the calling thread is tac_last_error().
+ *    The library never aborts and device code never traps: per-pad solve
+ *    outcomes are TAC_PAD_* codes written to a caller-owned status array.
+ *  - Host pointers (marked "host") are read during the call and may be freed
+ *    afterwards. Device pointers (marked "device") belong to the caller and
+ *    must stay valid until the stream-ordered work that reads or writes them
+ *    has completed.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Every call is
+ *    stream-ordered and asynchronous unless stated otherwise; results are
+ *    visible after the stream is synchronised.
+ *  - One device: the batch lives on the device that is current when
+ *    tac_create_batch is called; later calls must be made with that device
+ *    current.
+ */
+#ifndef TAC_H_
+#define TAC_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes --------------------------------------------------------- */
+#define TAC_OK 0
+#define TAC_ERR_INVALID_ARG (-1)   /* null / out-of-range argument               */
+#define TAC_ERR_INVALID_MESH (-2)  /* bad index, non-positive tet volume, marker off the top face */
+#define TAC_ERR_PENETRATION (-3)   /* gel and indenter intersect in the given state */
+#define TAC_ERR_CUDA (-4)          /* a CUDA runtime call failed                 */
+#define TAC_ERR_OOM (-5)           /* device allocation failed                   */
+#define TAC_ERR_STATE (-6)         /* call not valid in the batch's current state */
+
+/* ---- per-pad solve status (tac_step) -------------------------------------- */
+#define TAC_PAD_CONVERGED 0        /* max |g_i| <= tol * g_ref at the end pose    */
+#define TAC_PAD_MAXITER 1          /* iteration or substep cap reached           */
+#define TAC_PAD_NONFINITE 2        /* non-finite value met (state left as is)    */
+#define TAC_PAD_LINESEARCH 3       /* 20 Armijo halvings without acceptance      */
+#define TAC_PAD_PAIR_OVERFLOW 4    /* more contact candidates than pair_capacity */
+
+typedef struct tac_batch* tac_handle;   /* opaque, library-owned */
+
+/* One pad mesh (host arrays, copied at creation). */
+typedef struct {
+    int n_verts, n_tets, n_fixed, n_markers;
+    const float* rest_xyz;   /* host [n_verts*3] rest positions                   */
+    const int* tets;         /* host [n_tets*4] vertex ids, positive orientation */
+    const int* fixed_idx;    /* host [n_fixed] Dirichlet vertex ids              */
+    const float* marker_xy;  /* host [n_markers*2] marker (x, y) on the top face */
+} tac_pad_desc;
+
+/* One rigid indenter mesh per environment (host arrays, copied). */
+typedef struct {
+    int n_verts, n_tris;
+    const float* verts;      /* host [n_verts*3] local frame                     */
+    const int* tris;         /* host [n_tris*3]                                  */
+} tac_indenter_desc;
+
+/* Per-pad material and solver parameters.
+ *  E, nu          Young's modulus [Pa] and Poisson ratio (Neo-Hookean Lame pair)
+ *  rho, h         density [kg/m^3] and time step [s] (lumped mass; Eq. varopt)
+ *  dhat           barrier activation distance [m] (Eq. ipc_energy)
+ *  kappa          barrier stiffness; <= 0 selects h^2 * E * (mean surface edge)
+ *  mu_f, eps_v    friction coefficient and mollifier width [m]; eps_v <= 0
+ *                 selects 1e-3 m/s * h
+ *  tol_rel_grad   stop when max |g_i| <= tol_rel_grad * kappa * dhat
+ *  tol_advance    looser tolerance of the intermediate indenter substeps
+ *  max_iter       PNCG iteration cap per frame
+ *  precond_mode   0 = 3x3 block Jacobi, 1 = scalar Jacobi diag(H)^-1 */
+typedef struct {
+    float E, nu, rho, h, dhat, kappa, mu_f, eps_v;
+    float tol_rel_grad, tol_advance;
+    int max_iter, precond_mode;
+} tac_params;
+
+/* Batch options. pair_capacity: candidate pairs stored per pad (0 = 16384).
+ * share_meshes: pads whose tac_pad_desc points at the same host arrays share
+ * one device copy of the static mesh data (1) or each get their own (0). */
+typedef struct {
+    int pair_capacity;
+    int share_meshes;
+} tac_options;
+
+/* Create a batch of n_pads pads, pads_per_env consecutive pads per
+ * environment (n_pads = n_envs * pads_per_env), one indenter per
+ * environment. params has n_pads entries. opts may be NULL (defaults).
+ * Validates every mesh on the host (TAC_ERR_INVALID_MESH with the pad index
+ * in tac_last_error), builds the rest shape (Dm^-1, volumes, lumped masses),
+ * surface primitives, marker weights and the tet patches, allocates all
+ * device state and leaves every pad at rest with pose 0. Blocking. */
+int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_pads,
+                     const tac_indenter_desc* indenters, int n_envs, int pads_per_env,
+                     const tac_options* opts, void* stream, tac_handle* out);
+
+/* Free all device and host resources of the batch (synchronises its work). */
+int tac_destroy_batch(tac_handle h);
+
+/* Reset every pad to rest (x = X, v = 0) with the current indenter pose set
+ * to pose6_dev (device [n_pads*6]). */
+int tac_reset(tac_handle h, const float* pose6_dev, void* stream);
+
+/* Set the indenter pose the next tac_step moves to, per pad (the plugin
+ * input of Sec. 3.3: the object's pose relative to the sensor).
+ * pose6_dev: device [n_pads*6] (rotation vector, translation) or NULL;
+ * twist6_dev: device [n_pads*6] (angular velocity, linear velocity) or NULL.
+ * With pose6_dev NULL the target is the current pose advanced by h * twist
+ * (translation += h v, rotation composed with exp(h w)); with both given the
+ * pose is used and the twist ignored; both NULL is TAC_ERR_INVALID_ARG. */
+int tac_set_indenter(tac_handle h, const float* pose6_dev, const float* twist6_dev, void* stream);
+
+/* Solve one frame for every pad: move each indenter from its current pose to
+ * its target pose and minimise E (Supp. A). Writes the per-pad status
+ * (TAC_PAD_*) and iteration count to caller-owned device arrays
+ * pad_status_dev [n_pads] and iters_dev [n_pads] (either may be NULL), then
+ * v = (x - x^t) / h and the current pose becomes the target pose. */
+int tac_step(tac_handle h, int* pad_status_dev, int* iters_dev, void* stream);
+
+/* Marker displacement field (u_x, u_y) per marker of every pad, in pad order:
+ * out_dev: device [sum_p n_markers(p) * 2] float (Sec. 3.2). */
+int tac_markers(tac_handle h, float* out_dev, void* stream);
+
+/* Copy the vertex state out / in: x_dev, v_dev device [total_verts*3] float
+ * (positions and velocities, pads concatenated in order). tac_set_state
+ * keeps the current pose. */
+int tac_get_state(tac_handle h, float* x_dev, float* v_dev, void* stream);
+int tac_set_state(tac_handle h, const float* x_dev, const float* v_dev, void* stream);
+
+/* Replace the material / solver parameters of all pads (host [n_pads]). */
+int tac_set_params(tac_handle h, const tac_params* per_pad, int n);
+
+/* Candidate contact set (the set C of Eq. ipc_energy) of one pad for given
+ * positions: every (type, i, j) whose gel-primitive AABB inflated by r
+ * overlaps the indenter-primitive AABB, decided in float64 on the float32
+ * inputs. type 0 = gel vertex i x indenter triangle j; 1 = gel surface
+ * triangle i x indenter vertex j; 2 = gel surface edge i x indenter edge j
+ * (canonical surface order: boundary faces with sorted vertex ids, sorted;
+ * distinct surface edges (lo, hi), sorted; indenter edges likewise).
+ * x_dev: device [n_verts(pad)*3] gel positions; y_dev: device
+ * [n_indenter_verts*3] indenter world vertices; pairs_out_dev: device
+ * [capacity*3] int, sorted lexicographically; count_dev: device int, the
+ * full count (entries beyond capacity are not written). */
+int tac_broadphase(tac_handle h, int pad, const float* x_dev, const float* y_dev, double r,
+                   int* pairs_out_dev, int capacity, int* count_dev, void* stream);
+
+/* Verification entry point: evaluate the pieces of one PNCG iteration for
+ * every pad at displacement u (x = X + u) along direction p with the
+ * indenter at its current pose, inertia centred at u (xhat = x) and no
+ * friction lag. Inputs u_dev, p_dev: device [total_verts*3] float.
+ * Outputs (device, any may be NULL):
+ *   grad_dev  [total_verts*3]  float  gradient at u + alpha p
+ *   blk_dev   [total_verts*6]  float  diagonal blocks at u + alpha p
+ *                                     (xx, yy, zz, xy, xz, yz)
+ *   scal_dev  [n_pads*8]       double (p^T H p: elastic, contact, inertia;
+ *             E(u + alpha p) - E(u): total; alpha_ccd; min distance at u;
+ *             number of candidate pairs; max |g_i| at u + alpha p) */
+int tac_debug_eval(tac_handle h, const float* u_dev, const float* p_dev, float alpha,
+                   float* grad_dev, float* blk_dev, double* scal_dev, void* stream);
+
+/* Per-pad counters of the last tac_step (device [n_pads*8] long long):
+ * iterations, substeps, broad-phase rebuilds, Armijo halvings, tet passes,
+ * vertex passes, pair evaluations, peak candidate count. */
+int tac_stats(tac_handle h, long long* stats_dev, void* stream);
+
+/* Sizes: total vertices, total markers, candidate capacity per pad. */
+int tac_sizes(tac_handle h, int* total_verts, int* total_markers, int* pair_capacity);
+
+/* Message of the last error on this thread (static storage, never NULL). */
+const char* tac_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TAC_H_ */

@@ -1,0 +1,336 @@
+// Device arithmetic of the PNCG-IPC solve: Neo-Hookean per-tet terms in a
+// small-strain-stable float32 form, contact distances with their first and
+// second directional derivatives in float64, barrier and friction terms.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace tac {
+
+// ---------------------------------------------------------------------------
+// Neo-Hookean, Psi(F) = mu/2 (|F|^2 - 3) - mu ln J + lam/2 (ln J)^2 (Supp. A).
+// All quantities are formed from the displacement gradient G = F - I so that
+// nothing cancels against the identity: J - 1 = tr G + i2(G) + det G,
+// cof(F) = (1 + tr G) I - G^T + cof(G), and
+// J F - cof(F) = G + G^T + (i2 + det G) I + (J - 1) G - cof(G).
+
+struct FAnalysis {
+    float cof[9];   // cof(F) (row-major), F^-T = cof / J
+    float J, lnJ, invJ;
+    float Q[9];     // J F - cof(F)
+};
+
+__device__ __forceinline__ void f_analysis(const float G[9], FAnalysis& f) {
+    float cg0 = G[4] * G[8] - G[5] * G[7];
+    float cg1 = G[5] * G[6] - G[3] * G[8];
+    float cg2 = G[3] * G[7] - G[4] * G[6];
+    float cg3 = G[2] * G[7] - G[1] * G[8];
+    float cg4 = G[0] * G[8] - G[2] * G[6];
+    float cg5 = G[1] * G[6] - G[0] * G[7];
+    float cg6 = G[1] * G[5] - G[2] * G[4];
+    float cg7 = G[2] * G[3] - G[0] * G[5];
+    float cg8 = G[0] * G[4] - G[1] * G[3];
+    float trG = G[0] + G[4] + G[8];
+    float i2 = cg0 + cg4 + cg8;
+    float detG = G[0] * cg0 + G[1] * cg1 + G[2] * cg2;
+    float a = trG + (i2 + detG);
+    f.J = 1.0f + a;
+    f.lnJ = log1pf(a);
+    f.invJ = 1.0f / f.J;
+    float d = 1.0f + trG;
+    f.cof[0] = cg0 - G[0] + d; f.cof[1] = cg1 - G[3];     f.cof[2] = cg2 - G[6];
+    f.cof[3] = cg3 - G[1];     f.cof[4] = cg4 - G[4] + d; f.cof[5] = cg5 - G[7];
+    f.cof[6] = cg6 - G[2];     f.cof[7] = cg7 - G[5];     f.cof[8] = cg8 - G[8] + d;
+    float s2 = i2 + detG;
+    f.Q[0] = 2.0f * G[0] + s2 + a * G[0] - cg0;
+    f.Q[4] = 2.0f * G[4] + s2 + a * G[4] - cg4;
+    f.Q[8] = 2.0f * G[8] + s2 + a * G[8] - cg8;
+    f.Q[1] = G[1] + G[3] + a * G[1] - cg1;
+    f.Q[3] = G[3] + G[1] + a * G[3] - cg3;
+    f.Q[2] = G[2] + G[6] + a * G[2] - cg2;
+    f.Q[6] = G[6] + G[2] + a * G[6] - cg6;
+    f.Q[5] = G[5] + G[7] + a * G[5] - cg5;
+    f.Q[7] = G[7] + G[5] + a * G[7] - cg7;
+}
+
+// ln(1 + q) - q, accurate for small q (series below 1e-2).
+__device__ __forceinline__ float log1p_minus(float q) {
+    if (fabsf(q) < 1e-2f) {
+        float q2 = q * q;
+        return q2 * (-0.5f + q * (1.0f / 3.0f + q * (-0.25f + q * 0.2f)));
+    }
+    return log1pf(q) - q;
+}
+
+// A = F^-1 dF = cof(F)^T dF / J; returns tr A, tr(A^2) and the invariants
+// of A needed by the line remainder.
+struct AInv {
+    float c1, c2, c3, trA2;
+};
+
+__device__ __forceinline__ AInv a_invariants(const FAnalysis& f, const float dF[9]) {
+    float A[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            A[3 * i + j] = (f.cof[i] * dF[j] + f.cof[3 + i] * dF[3 + j] + f.cof[6 + i] * dF[6 + j]) * f.invJ;
+    AInv r;
+    r.c1 = A[0] + A[4] + A[8];
+    float m0 = A[4] * A[8] - A[5] * A[7];
+    float m4 = A[0] * A[8] - A[2] * A[6];
+    float m8 = A[0] * A[4] - A[1] * A[3];
+    r.c2 = m0 + m4 + m8;
+    r.c3 = A[0] * m0 - A[1] * (A[3] * A[8] - A[5] * A[6]) + A[2] * (A[3] * A[7] - A[4] * A[6]);
+    r.trA2 = A[0] * A[0] + A[4] * A[4] + A[8] * A[8] + 2.0f * (A[1] * A[3] + A[2] * A[6] + A[5] * A[7]);
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Barrier b(d) = -(d - dhat)^2 ln(d / dhat) on 0 < d < dhat (Eq. ipc_energy).
+
+__device__ __forceinline__ double barrier_b(double d, double dh) {
+    if (d >= dh) return 0.0;
+    double t = d - dh;
+    return -t * t * log(d / dh);
+}
+__device__ __forceinline__ double barrier_b1(double d, double dh) {
+    if (d >= dh) return 0.0;
+    double t = d - dh;
+    return -2.0 * t * log(d / dh) - t * t / d;
+}
+__device__ __forceinline__ double barrier_b2(double d, double dh) {
+    if (d >= dh) return 0.0;
+    double t = d - dh;
+    return -2.0 * log(d / dh) - 4.0 * t / d + t * t / (d * d);
+}
+
+// ---------------------------------------------------------------------------
+// Contact features. A pair has 4 slots; r = sum_s w_s v_s is the vector
+// between the closest points (indenter -> gel), d = |r|. Within the active
+// feature the weights are affine in nf free parameters theta:
+// w = w0 + sum_k theta_k e_k, which gives the directional derivatives.
+
+template <typename T>
+struct V3 {
+    T x, y, z;
+};
+template <typename T>
+__device__ __forceinline__ V3<T> v3(T a, T b, T c) { return V3<T>{a, b, c}; }
+template <typename T>
+__device__ __forceinline__ V3<T> operator-(V3<T> a, V3<T> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <typename T>
+__device__ __forceinline__ V3<T> operator+(V3<T> a, V3<T> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <typename T>
+__device__ __forceinline__ V3<T> operator*(T s, V3<T> a) { return {s * a.x, s * a.y, s * a.z}; }
+template <typename T>
+__device__ __forceinline__ T dot(V3<T> a, V3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <typename T>
+__device__ __forceinline__ V3<T> cross(V3<T> a, V3<T> b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+template <typename T>
+struct Feature {
+    T d;
+    T w[4];
+    T e[2][4];
+    int nf;
+};
+
+template <typename T>
+__device__ __forceinline__ T clamp01(T t) { return t < T(0) ? T(0) : (t > T(1) ? T(1) : t); }
+
+// point P vs segment AB: squared distance and parameter t (Q = A + t (B - A))
+template <typename T>
+__device__ __forceinline__ T seg_param(V3<T> P, V3<T> A, V3<T> B, T& t) {
+    V3<T> e = B - A;
+    T ee = dot(e, e);
+    t = ee > T(0) ? clamp01(dot(P - A, e) / ee) : T(0);
+    V3<T> r = P - (A + t * e);
+    return dot(r, r);
+}
+
+// Point-triangle feature with slots [P, A, B, C], r = P - closest.
+// Candidates: face interior (if the projection is inside), then edges AB,
+// BC, CA with clamped parameters; the first minimum wins.
+template <typename T>
+__device__ Feature<T> pt_feature(V3<T> P, V3<T> A, V3<T> B, V3<T> C) {
+    Feature<T> f;
+    V3<T> v0 = B - A, v1 = C - A, v2 = P - A;
+    T d00 = dot(v0, v0), d01 = dot(v0, v1), d11 = dot(v1, v1), d20 = dot(v2, v0), d21 = dot(v2, v1);
+    T den = d00 * d11 - d01 * d01;
+    T l1 = (d11 * d20 - d01 * d21) / den;
+    T l2 = (d00 * d21 - d01 * d20) / den;
+    T l0 = T(1) - l1 - l2;
+    T best = sizeof(T) == 8 ? T(1e300) : T(3e38);
+    int k = -1;
+    T tab, tbc, tca;
+    if (l0 >= T(0) && l1 >= T(0) && l2 >= T(0) && den > T(0)) {
+        V3<T> n = cross(v0, v1);
+        T s = dot(v2, n);
+        best = s * s / dot(n, n);
+        k = 0;
+    }
+    T dab = seg_param(P, A, B, tab);
+    if (k < 0 || dab < best) { best = dab; k = 1; }
+    T dbc = seg_param(P, B, C, tbc);
+    if (dbc < best) { best = dbc; k = 2; }
+    T dca = seg_param(P, C, A, tca);
+    if (dca < best) { best = dca; k = 3; }
+    f.d = sqrt(best);
+    f.nf = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) f.e[0][i] = f.e[1][i] = T(0);
+    f.w[0] = T(1);
+    if (k == 0) {
+        f.w[1] = -l0; f.w[2] = -l1; f.w[3] = -l2;
+        f.nf = 2;
+        f.e[0][1] = T(1); f.e[0][2] = T(-1);
+        f.e[1][1] = T(1); f.e[1][3] = T(-1);
+    } else if (k == 1) {
+        f.w[1] = -(T(1) - tab); f.w[2] = -tab; f.w[3] = T(0);
+        if (tab > T(0) && tab < T(1)) { f.nf = 1; f.e[0][1] = T(1); f.e[0][2] = T(-1); }
+    } else if (k == 2) {
+        f.w[1] = T(0); f.w[2] = -(T(1) - tbc); f.w[3] = -tbc;
+        if (tbc > T(0) && tbc < T(1)) { f.nf = 1; f.e[0][2] = T(1); f.e[0][3] = T(-1); }
+    } else {
+        f.w[1] = -tca; f.w[2] = T(0); f.w[3] = -(T(1) - tca);
+        if (tca > T(0) && tca < T(1)) { f.nf = 1; f.e[0][3] = T(1); f.e[0][1] = T(-1); }
+    }
+    return f;
+}
+
+// Segment-segment feature with slots [P0, P1, Q0, Q1], r = P(s) - Q(t).
+// Candidates: both interior (non-parallel, unconstrained solution inside
+// [0,1]^2), then P0-vs-Q, P1-vs-Q, Q0-vs-P, Q1-vs-P; the first minimum wins.
+template <typename T>
+__device__ Feature<T> ee_feature(V3<T> P0, V3<T> P1, V3<T> Q0, V3<T> Q1) {
+    Feature<T> f;
+    V3<T> u = P1 - P0, v = Q1 - Q0, w = P0 - Q0;
+    T a = dot(u, u), b = dot(u, v), c = dot(v, v), dd = dot(u, w), e = dot(v, w);
+    T D = a * c - b * b;
+    T best = sizeof(T) == 8 ? T(1e300) : T(3e38);
+    int k = -1;
+    T s = T(0), t = T(0);
+    if (D > T(1e-12) * a * c) {
+        s = (b * e - c * dd) / D;
+        t = (a * e - b * dd) / D;
+        if (s >= T(0) && s <= T(1) && t >= T(0) && t <= T(1)) {
+            V3<T> r = w + s * u - t * v;
+            best = dot(r, r);
+            k = 0;
+        }
+    }
+    T t0, t1, t2, t3;
+    T d0 = seg_param(P0, Q0, Q1, t0);
+    if (k < 0 || d0 < best) { best = d0; k = 1; }
+    T d1 = seg_param(P1, Q0, Q1, t1);
+    if (d1 < best) { best = d1; k = 2; }
+    T d2 = seg_param(Q0, P0, P1, t2);
+    if (d2 < best) { best = d2; k = 3; }
+    T d3 = seg_param(Q1, P0, P1, t3);
+    if (d3 < best) { best = d3; k = 4; }
+    f.d = sqrt(best);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) f.e[0][i] = f.e[1][i] = T(0);
+    f.nf = 0;
+    T sp, tq;
+    bool sfree = false, tfree = false;
+    if (k == 0) { sp = s; tq = t; sfree = tfree = true; }
+    else if (k == 1) { sp = T(0); tq = t0; tfree = t0 > T(0) && t0 < T(1); }
+    else if (k == 2) { sp = T(1); tq = t1; tfree = t1 > T(0) && t1 < T(1); }
+    else if (k == 3) { sp = t2; tq = T(0); sfree = t2 > T(0) && t2 < T(1); }
+    else { sp = t3; tq = T(1); sfree = t3 > T(0) && t3 < T(1); }
+    f.w[0] = T(1) - sp; f.w[1] = sp; f.w[2] = -(T(1) - tq); f.w[3] = -tq;
+    if (sfree) { f.e[f.nf][0] = T(-1); f.e[f.nf][1] = T(1); f.nf++; }
+    if (tfree) { f.e[f.nf][2] = T(1); f.e[f.nf][3] = T(-1); f.nf++; }
+    return f;
+}
+
+// r of a feature for slot positions X[4]
+template <typename T>
+__device__ __forceinline__ V3<T> feat_r(const Feature<T>& f, const V3<T> X[4]) {
+    V3<T> r = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int s = 0; s < 4; ++s) r = r + f.w[s] * X[s];
+    return r;
+}
+
+// First and second derivative of d along slot directions dl[4] (sensitivity
+// of the closest-point problem restricted to the active feature):
+//   D = d^2, D' = 2 r.rdot, D'' = 2|rdot|^2 - 2 b^T (J^T J)^-1 b,
+//   J_k = sum_s e_ks X_s, b_k = (sum_s e_ks dl_s).r + J_k.rdot,
+//   d' = D'/(2d), d'' = (D'' - 2 d'^2) / (2d).
+__device__ __forceinline__ void feat_dir_derivs(const Feature<double>& f, const V3<double> X[4],
+                                                const V3<double> dl[4], double& d1, double& d2) {
+    V3<double> r = feat_r(f, X);
+    V3<double> rd = {0, 0, 0};
+#pragma unroll
+    for (int s = 0; s < 4; ++s) rd = rd + f.w[s] * dl[s];
+    double D2 = 2.0 * dot(rd, rd);
+    if (f.nf > 0) {
+        V3<double> J[2], Gk[2];
+        double bk[2];
+        for (int k = 0; k < f.nf; ++k) {
+            J[k] = {0, 0, 0};
+            Gk[k] = {0, 0, 0};
+            for (int s = 0; s < 4; ++s) {
+                J[k] = J[k] + f.e[k][s] * X[s];
+                Gk[k] = Gk[k] + f.e[k][s] * dl[s];
+            }
+            bk[k] = dot(Gk[k], r) + dot(J[k], rd);
+        }
+        if (f.nf == 1) {
+            double m = dot(J[0], J[0]);
+            if (m > 0) D2 -= 2.0 * bk[0] * bk[0] / m;
+        } else {
+            double m00 = dot(J[0], J[0]), m01 = dot(J[0], J[1]), m11 = dot(J[1], J[1]);
+            double det = m00 * m11 - m01 * m01;
+            if (det > 0) D2 -= 2.0 * (m11 * bk[0] * bk[0] - 2.0 * m01 * bk[0] * bk[1] + m00 * bk[1] * bk[1]) / det;
+        }
+    }
+    d1 = dot(r, rd) / f.d;
+    d2 = (D2 - 2.0 * d1 * d1) / (2.0 * f.d);
+}
+
+// ---------------------------------------------------------------------------
+// Friction mollifier f(s) of Eq. (friction_mollifier) and helpers.
+
+__device__ __forceinline__ double moll_f(double s, double eps) {
+    return s < eps ? -s * s * s / (3.0 * eps * eps) + s * s / eps + eps / 3.0 : s;
+}
+__device__ __forceinline__ double moll_f1_over_s(double s, double eps) {
+    return s < eps ? -s / (eps * eps) + 2.0 / eps : 1.0 / s;
+}
+// coefficient c(s) of the u u^T term of the tangent Hessian
+__device__ __forceinline__ double moll_c(double s, double eps) {
+    return s < eps ? s / (eps * eps) : (s > 0 ? 1.0 / s : 0.0);
+}
+
+// ---------------------------------------------------------------------------
+// 3x3 symmetric block helpers; blocks are stored (xx, yy, zz, xy, xz, yz).
+
+__device__ __forceinline__ bool sym_inverse(const float K[6], float Kinv[6]) {
+    float a = K[0], b = K[1], c = K[2], d = K[3], e = K[4], f = K[5];
+    float c00 = b * c - f * f, c01 = e * f - d * c, c02 = d * f - b * e;
+    float det = a * c00 + d * c01 + e * c02;
+    if (!(det > 0.0f)) return false;
+    float id = 1.0f / det;
+    Kinv[0] = c00 * id;
+    Kinv[1] = (a * c - e * e) * id;
+    Kinv[2] = (a * b - d * d) * id;
+    Kinv[3] = c01 * id;
+    Kinv[4] = c02 * id;
+    Kinv[5] = (d * e - a * f) * id;
+    return true;
+}
+
+__device__ __forceinline__ void sym_apply(const float K[6], const float v[3], float o[3]) {
+    o[0] = K[0] * v[0] + K[3] * v[1] + K[4] * v[2];
+    o[1] = K[3] * v[0] + K[1] * v[1] + K[5] * v[2];
+    o[2] = K[4] * v[0] + K[5] * v[1] + K[2] * v[2];
+}
+
+}  // namespace tac

@@ -1,0 +1,1499 @@
+// Kernels of the PNCG-IPC gel-pad solve (see solve.cuh for the data layout).
+//
+// Readings of the paper that these kernels share with the FP64 oracle:
+//  * step alpha = min(dhat / (2 max_i |p_i|), alpha_ccd, -g^T p / p^T H p)
+//    (Eq. step_size plus a conservative per-pair bound eta d_k / max |p_i|),
+//    then Armijo backtracking on E(x + alpha p) - E(x) <= c alpha g^T p,
+//    evaluated as alpha g(x + alpha p)^T p - R'(alpha) with R' the
+//    element-wise second-order remainder expanded at the trial point;
+//  * beta of Eq. (dk_direction); restart when y^T p is negligible or the new
+//    direction is not a descent direction;
+//  * the indenter moves on the straight per-vertex path between its frame
+//    poses in substeps of eta * d_min / max |y^{t+1} - y^t|;
+//  * the candidate set is rebuilt before the accumulated motion bound since
+//    the last build exceeds the margin m = dhat.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cstdint>
+
+#include "solve.cuh"
+
+namespace tac {
+
+constexpr float kEta = 0.9f;          // safety factor of the step bounds
+constexpr double kArmijoC = 1e-4;
+constexpr int kMaxHalvings = 20;
+constexpr int kMaxSubsteps = 1000;
+constexpr int kWarps = kThreads / 32;
+
+// ---------------------------------------------------------------------------
+// shared memory of one CTA
+
+struct Shared {
+    float su[3][kThreads];
+    float sp[3][kThreads];
+    float stg[9][kStage];
+    double rd[kWarps][8];
+    float rf[kWarps][4];
+    int ri[kWarps];
+    int cnt[4];
+    float box[12];
+    int pad;
+    int flag;
+    int expired;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// true (in every thread) once the pad's solve has run longer than budget_ns;
+// thread 0 reads the clock and broadcasts so that the decision is uniform
+__device__ __forceinline__ bool over_budget(unsigned long long t0, unsigned long long budget_ns, Shared& S) {
+    if (threadIdx.x == 0) S.expired = (global_ns() - t0) > budget_ns ? 1 : 0;
+    __syncthreads();
+    bool e = S.expired != 0;
+    __syncthreads();
+    return e;
+}
+
+// ---------------------------------------------------------------------------
+// block-wide helpers (every thread receives the same result)
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], Shared& S) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) S.rd[w][k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double t = 0.0;
+#pragma unroll
+        for (int i = 0; i < kWarps; ++i) t += S.rd[i][k];
+        v[k] = t;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double block_min_d(double v, Shared& S) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) S.rd[w][7] = v;
+    __syncthreads();
+    double t = S.rd[0][7];
+#pragma unroll
+    for (int i = 1; i < kWarps; ++i) t = fmin(t, S.rd[i][7]);
+    __syncthreads();
+    return t;
+}
+
+// max of up to 4 floats
+template <int K>
+__device__ __forceinline__ void block_max_f(float (&v)[K], Shared& S) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] = fmaxf(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) S.rf[w][k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float t = S.rf[0][k];
+#pragma unroll
+        for (int i = 1; i < kWarps; ++i) t = fmaxf(t, S.rf[i][k]);
+        v[k] = t;
+    }
+    __syncthreads();
+}
+
+// exclusive scan of one int per thread; total to every thread
+__device__ __forceinline__ int block_scan(int v, int& total, Shared& S) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) S.ri[w] = x;
+    __syncthreads();
+    int before = 0, tot = 0;
+#pragma unroll
+    for (int i = 0; i < kWarps; ++i) {
+        int c = S.ri[i];
+        before += (i < w) ? c : 0;
+        tot += c;
+    }
+    __syncthreads();
+    total = tot;
+    return before + x - v;
+}
+
+// ---------------------------------------------------------------------------
+// positions
+
+struct Ctx {
+    const Dev& D;
+    const PadDev& P;
+    const MeshDev& M;
+    const EnvDev& E;
+};
+
+__device__ __forceinline__ double gel_pos64(const Dev& D, const PadDev& P, const MeshDev& M, int gv, int c,
+                                            float alpha) {
+    int si = c * D.Vt + P.v_off + gv;
+    return (double)D.X[c * D.XVt + M.xv_off + gv] + (double)D.uh[si] + (double)D.ul[si] +
+           (double)(alpha * D.p[si]);
+}
+
+__device__ __forceinline__ float gel_pos32(const Dev& D, const PadDev& P, const MeshDev& M, int gv, int c,
+                                           float alpha) {
+    int si = c * D.Vt + P.v_off + gv;
+    return D.X[c * D.XVt + M.xv_off + gv] + ((D.uh[si] + D.ul[si]) + alpha * D.p[si]);
+}
+
+// indenter vertex j (env-local) of this pad at path parameter s
+__device__ __forceinline__ double ind_pos64(const Dev& D, const PadDev& P, int j, int c, double s) {
+    double a = D.Yt[3 * (P.yw_off + j) + c], b = D.Yn[3 * (P.yw_off + j) + c];
+    return a + s * (b - a);
+}
+__device__ __forceinline__ float ind_pos32(const Dev& D, const PadDev& P, int j, int c, float s) {
+    float a = D.Yt[3 * (P.yw_off + j) + c], b = D.Yn[3 * (P.yw_off + j) + c];
+    return a + s * (b - a);
+}
+
+// slots of a candidate pair: gel mesh vertex ids (or -1) and indenter env
+// vertex ids (or -1), canonical order [gel..., indenter...]
+__device__ __forceinline__ void pair_slots(const Dev& D, const MeshDev& M, const EnvDev& E, int4 q, int gsl[4],
+                                           int isl[4]) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) gsl[s] = isl[s] = -1;
+    if (q.x == 0) {
+        gsl[0] = q.y;
+        const int* t = D.it + 3 * (E.t_off + q.z);
+        isl[1] = t[0]; isl[2] = t[1]; isl[3] = t[2];
+    } else if (q.x == 1) {
+        const int* t = D.st + 3 * (M.st_off + q.y);
+        gsl[0] = t[0]; gsl[1] = t[1]; gsl[2] = t[2];
+        isl[3] = q.z;
+    } else {
+        const int* e = D.se + 2 * (M.se_off + q.y);
+        gsl[0] = e[0]; gsl[1] = e[1];
+        const int* f = D.ie + 2 * (E.e_off + q.z);
+        isl[2] = f[0]; isl[3] = f[1];
+    }
+}
+
+// feature of a pair from slot positions; type 1 is re-expressed with the gel
+// triangle first and r pointing from the indenter to the gel
+template <typename T>
+__device__ __forceinline__ Feature<T> pair_feature(int type, const V3<T> X[4]) {
+    if (type == 0) return pt_feature<T>(X[0], X[1], X[2], X[3]);
+    if (type == 2) return ee_feature<T>(X[0], X[1], X[2], X[3]);
+    Feature<T> f = pt_feature<T>(X[3], X[0], X[1], X[2]);
+    Feature<T> g;
+    g.d = f.d;
+    g.nf = f.nf;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        g.w[s] = -f.w[s + 1];
+        g.e[0][s] = -f.e[0][s + 1];
+        g.e[1][s] = -f.e[1][s + 1];
+    }
+    g.w[3] = -f.w[0];
+    g.e[0][3] = -f.e[0][0];
+    g.e[1][3] = -f.e[1][0];
+    return g;
+}
+
+template <typename T>
+__device__ __forceinline__ void load_slots(const Dev& D, const PadDev& P, const MeshDev& M, const int gsl[4],
+                                           const int isl[4], float alpha, double s, V3<T> X[4]);
+
+template <>
+__device__ __forceinline__ void load_slots<double>(const Dev& D, const PadDev& P, const MeshDev& M,
+                                                   const int gsl[4], const int isl[4], float alpha, double s,
+                                                   V3<double> X[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (gsl[k] >= 0)
+            X[k] = {gel_pos64(D, P, M, gsl[k], 0, alpha), gel_pos64(D, P, M, gsl[k], 1, alpha),
+                    gel_pos64(D, P, M, gsl[k], 2, alpha)};
+        else
+            X[k] = {ind_pos64(D, P, isl[k], 0, s), ind_pos64(D, P, isl[k], 1, s), ind_pos64(D, P, isl[k], 2, s)};
+    }
+}
+
+template <>
+__device__ __forceinline__ void load_slots<float>(const Dev& D, const PadDev& P, const MeshDev& M,
+                                                  const int gsl[4], const int isl[4], float alpha, double s,
+                                                  V3<float> X[4]) {
+    float sf = (float)s;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (gsl[k] >= 0)
+            X[k] = {gel_pos32(D, P, M, gsl[k], 0, alpha), gel_pos32(D, P, M, gsl[k], 1, alpha),
+                    gel_pos32(D, P, M, gsl[k], 2, alpha)};
+        else
+            X[k] = {ind_pos32(D, P, isl[k], 0, sf), ind_pos32(D, P, isl[k], 1, sf), ind_pos32(D, P, isl[k], 2, sf)};
+    }
+}
+
+// distance of a pair: float32 estimate, float64 when close (relative band)
+__device__ __forceinline__ double pair_distance(const Dev& D, const PadDev& P, const MeshDev& M, int type,
+                                                const int gsl[4], const int isl[4], float alpha, double s,
+                                                double near) {
+    V3<float> Xf[4];
+    load_slots<float>(D, P, M, gsl, isl, alpha, s, Xf);
+    float df = pair_feature<float>(type, Xf).d;
+    if ((double)df > near) return (double)df * (1.0 - 1e-5);
+    V3<double> Xd[4];
+    load_slots<double>(D, P, M, gsl, isl, alpha, s, Xd);
+    return pair_feature<double>(type, Xd).d;
+}
+
+// ---------------------------------------------------------------------------
+// tet passes
+
+struct TetOut {
+    double acc;       // p^T H_e p (pass 0) or remainder R' (pass 1)
+    int bad;          // trial state inverted a tet
+};
+
+// Loads the patch's local vertices: su = patch-relative displacement at
+// u + alpha p, sp = p.
+__device__ __forceinline__ void load_patch(const Dev& D, const PadDev& P, const MeshDev& M, int vb, int nv,
+                                           float alpha, Shared& S) {
+    int ref = D.pvert[M.pvert_off + vb] & ((1 << 29) - 1);
+    int tid = threadIdx.x;
+    if (tid < nv) {
+        int gv = D.pvert[M.pvert_off + vb + tid] & ((1 << 29) - 1);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            int si = c * D.Vt + P.v_off + gv, sr = c * D.Vt + P.v_off + ref;
+            float pv = D.p[si];
+            S.su[c][tid] = ((D.uh[si] - D.uh[sr]) + (D.ul[si] - D.ul[sr])) + alpha * pv;
+            S.sp[c][tid] = pv;
+        }
+    }
+}
+
+// pass 0: p^T H_e p at u; pass 1: gradient, diagonal blocks and remainder at
+// u + alpha p, scattered into g[gb], blk[gb].
+template <int PASS>
+__device__ TetOut tet_pass(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, int gb, Shared& S) {
+    TetOut out{0.0, 0};
+    const int tid = threadIdx.x;
+    const float mu = P.mu, lam = P.lam, h2 = P.h * P.h;
+    for (int pi = 0; pi < M.n_patch; ++pi) {
+        int4 ph = D.patch[M.patch_off + pi];
+        int tb = ph.x, vb = ph.y, nt = ph.z & 0xffff, nv = ph.z >> 16, cb = ph.w;
+        load_patch(D, P, M, vb, nv, alpha, S);
+        __syncthreads();
+        if (tid < nt) {
+            int t = M.tet_off + tb + tid;
+            uint32_t lc = D.lconn[t];
+            int l0 = lc & 255, l1 = (lc >> 8) & 255, l2 = (lc >> 16) & 255, l3 = lc >> 24;
+            float Bm[9];
+#pragma unroll
+            for (int e = 0; e < 9; ++e) Bm[e] = D.B[(size_t)e * D.Tt + t];
+            float Du[9], Dp[9];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                float a0 = S.su[r][l0], p0 = S.sp[r][l0];
+                Du[3 * r + 0] = S.su[r][l1] - a0;
+                Du[3 * r + 1] = S.su[r][l2] - a0;
+                Du[3 * r + 2] = S.su[r][l3] - a0;
+                Dp[3 * r + 0] = S.sp[r][l1] - p0;
+                Dp[3 * r + 1] = S.sp[r][l2] - p0;
+                Dp[3 * r + 2] = S.sp[r][l3] - p0;
+            }
+            float G[9], dF[9];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    G[3 * r + c] = Du[3 * r] * Bm[c] + Du[3 * r + 1] * Bm[3 + c] + Du[3 * r + 2] * Bm[6 + c];
+                    dF[3 * r + c] = Dp[3 * r] * Bm[c] + Dp[3 * r + 1] * Bm[3 + c] + Dp[3 * r + 2] * Bm[6 + c];
+                }
+            float detB = Bm[0] * (Bm[4] * Bm[8] - Bm[5] * Bm[7]) - Bm[1] * (Bm[3] * Bm[8] - Bm[5] * Bm[6]) +
+                         Bm[2] * (Bm[3] * Bm[7] - Bm[4] * Bm[6]);
+            float hV = h2 / (6.0f * detB);
+            FAnalysis f;
+            f_analysis(G, f);
+            float dF2 = 0.f;
+#pragma unroll
+            for (int e = 0; e < 9; ++e) dF2 += dF[e] * dF[e];
+            AInv ai = a_invariants(f, dF);
+            if (PASS == 0) {
+                out.acc += (double)(hV * (mu * dF2 + (mu - lam * f.lnJ) * ai.trA2 + lam * ai.c1 * ai.c1));
+            } else {
+                if (!(f.J > 0.0f)) out.bad = 1;
+                // remainder of the line expanded at the trial point (step -alpha)
+                float q = alpha * (-ai.c1 + alpha * (ai.c2 - alpha * ai.c3));
+                float a2c = alpha * alpha * (ai.c2 - alpha * ai.c3);
+                float dl = log1p_minus(q) + a2c;          // ln det(I - aA) + a tr A
+                float dlnJ = log1pf(q);
+                out.acc += (double)(hV * (0.5f * mu * alpha * alpha * dF2 + (lam * f.lnJ - mu) * dl +
+                                          0.5f * lam * dlnJ * dlnJ));
+                // first Piola-Kirchhoff stress P = (mu Q + lam ln J cof) / J
+                float Pm[9];
+#pragma unroll
+                for (int e = 0; e < 9; ++e) Pm[e] = (mu * f.Q[e] + lam * f.lnJ * f.cof[e]) * f.invJ;
+                // H = hV P B^T: column k is the force on corner k+1
+                float Hc[3][3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+                        Hc[k][r] = hV * (Pm[3 * r] * Bm[3 * k] + Pm[3 * r + 1] * Bm[3 * k + 1] + Pm[3 * r + 2] * Bm[3 * k + 2]);
+                float coef = fmaxf(mu + lam * (1.0f - f.lnJ), 0.0f) * f.invJ * f.invJ;
+                uint64_t sl = D.slot[t];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float b[3], fo[3];
+                    if (k == 0) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            b[c] = -(Bm[c] + Bm[3 + c] + Bm[6 + c]);
+                            fo[c] = -(Hc[0][c] + Hc[1][c] + Hc[2][c]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            b[c] = Bm[3 * (k - 1) + c];
+                            fo[c] = Hc[k - 1][c];
+                        }
+                    }
+                    float cc[3];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) cc[r] = f.cof[3 * r] * b[0] + f.cof[3 * r + 1] * b[1] + f.cof[3 * r + 2] * b[2];
+                    float bb = mu * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+                    float cf = coef;
+                    int slot = (int)((sl >> (16 * k)) & 0xffff);
+                    S.stg[0][slot] = fo[0];
+                    S.stg[1][slot] = fo[1];
+                    S.stg[2][slot] = fo[2];
+                    S.stg[3][slot] = hV * (bb + cf * cc[0] * cc[0]);
+                    S.stg[4][slot] = hV * (bb + cf * cc[1] * cc[1]);
+                    S.stg[5][slot] = hV * (bb + cf * cc[2] * cc[2]);
+                    S.stg[6][slot] = hV * (cf * cc[0] * cc[1]);
+                    S.stg[7][slot] = hV * (cf * cc[0] * cc[2]);
+                    S.stg[8][slot] = hV * (cf * cc[1] * cc[2]);
+                }
+            }
+        }
+        __syncthreads();
+        if (PASS == 1) {
+            if (tid < nv) {
+                int pv = D.pvert[M.pvert_off + vb + tid];
+                int gv = pv & ((1 << 29) - 1);
+                bool first = (pv & (1 << 30)) != 0;
+                int s0 = D.pcsr[M.pcsr_off + cb + tid], s1 = D.pcsr[M.pcsr_off + cb + tid + 1];
+                float acc[9];
+#pragma unroll
+                for (int c = 0; c < 9; ++c) acc[c] = 0.f;
+                for (int s = s0; s < s1; ++s)
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) acc[c] += S.stg[c][s];
+                int si = P.v_off + gv;
+                float* g = D.g[gb];
+                float* k = D.blk[gb];
+                if (first) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) g[c * D.Vt + si] = acc[c];
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) k[c * D.Vt + si] = acc[3 + c];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) g[c * D.Vt + si] += acc[c];
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) k[c * D.Vt + si] += acc[3 + c];
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // every thread must see the same totals: the caller branches on them
+    double v[2] = {out.acc, (double)out.bad};
+    block_sum<2>(v, S);
+    out.acc = v[0];
+    out.bad = v[1] > 0.0 ? 1 : 0;
+    return out;
+}
+
+// ---------------------------------------------------------------------------
+// broad phase: candidate triples (type, i, j) sorted lexicographically
+
+struct BoxF {
+    float lo[3], hi[3];
+};
+
+// (glo - r) <= ihi and ilo <= (ghi + r) per axis, in float64 on float32
+// inputs; a float32 filter decides the cases far from the boundary.
+__device__ __forceinline__ bool bp_overlap(const BoxF& g, const BoxF& i, double r, float rlo, float rhi) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float t1 = g.lo[c] - i.hi[c];
+        bool a = t1 <= rlo ? true : (t1 > rhi ? false : ((double)g.lo[c] - r) <= (double)i.hi[c]);
+        if (!a) return false;
+        float t2 = i.lo[c] - g.hi[c];
+        bool b = t2 <= rlo ? true : (t2 > rhi ? false : (double)i.lo[c] <= ((double)g.hi[c] + r));
+        if (!b) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool box_near(const BoxF& a, const float* b /*lo3 hi3 inflated*/) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        if (a.hi[c] < b[c] || a.lo[c] > b[3 + c]) return false;
+    return true;
+}
+
+// Position sources: the solve state or caller arrays.
+struct SrcState {
+    const Dev* D;
+    const PadDev* P;
+    const MeshDev* M;
+    float s;
+    __device__ float gel(int gv, int c) const { return gel_pos32(*D, *P, *M, gv, c, 0.0f); }
+    __device__ float ind(int j, int c) const { return ind_pos32(*D, *P, j, c, s); }
+};
+struct SrcArrays {
+    const float* x;
+    const float* y;
+    __device__ float gel(int gv, int c) const { return x[3 * gv + c]; }
+    __device__ float ind(int j, int c) const { return y[3 * j + c]; }
+};
+
+template <class Src>
+__device__ __forceinline__ BoxF gel_box(const Src& src, const Dev& D, const MeshDev& M, int type, int i) {
+    BoxF b;
+    int v[3];
+    int n;
+    if (type == 0) { v[0] = D.sv[M.sv_off + i]; n = 1; }
+    else if (type == 1) { const int* t = D.st + 3 * (M.st_off + i); v[0] = t[0]; v[1] = t[1]; v[2] = t[2]; n = 3; }
+    else { const int* e = D.se + 2 * (M.se_off + i); v[0] = e[0]; v[1] = e[1]; n = 2; }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float x = src.gel(v[0], c);
+        b.lo[c] = b.hi[c] = x;
+        for (int k = 1; k < n; ++k) {
+            float y = src.gel(v[k], c);
+            b.lo[c] = fminf(b.lo[c], y);
+            b.hi[c] = fmaxf(b.hi[c], y);
+        }
+    }
+    return b;
+}
+
+template <class Src>
+__device__ __forceinline__ BoxF ind_box(const Src& src, const Dev& D, const EnvDev& E, int type, int j) {
+    BoxF b;
+    int v[3];
+    int n;
+    if (type == 0) { const int* t = D.it + 3 * (E.t_off + j); v[0] = t[0]; v[1] = t[1]; v[2] = t[2]; n = 3; }
+    else if (type == 1) { v[0] = j; n = 1; }
+    else { const int* e = D.ie + 2 * (E.e_off + j); v[0] = e[0]; v[1] = e[1]; n = 2; }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float x = src.ind(v[0], c);
+        b.lo[c] = b.hi[c] = x;
+        for (int k = 1; k < n; ++k) {
+            float y = src.ind(v[k], c);
+            b.lo[c] = fminf(b.lo[c], y);
+            b.hi[c] = fmaxf(b.hi[c], y);
+        }
+    }
+    return b;
+}
+
+// Builds the candidate list of one pad into out[0 .. cap); returns the full
+// count (> cap means overflow; entries beyond cap are not written).
+template <class Src>
+__device__ int bp_build(const Src& src, const Dev& D, const MeshDev& M, const EnvDev& E, int* ilist, double r,
+                        int4* out, int cap, Shared& S) {
+    const int tid = threadIdx.x;
+    const float rlo = (float)(r * (1.0 - 1e-5)), rhi = (float)(r * (1.0 + 1e-5));
+    const float rc = (float)(r * (1.0 + 1e-4)) + 1e-12f;     // conservative culling radius
+    // 1. indenter AABB
+    float mx[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX}, mn[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
+    for (int j = tid; j < E.n_v; j += kThreads)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float y = src.ind(j, c);
+            mx[c] = fmaxf(mx[c], y);
+            mn[c] = fmaxf(mn[c], -y);
+        }
+    block_max_f<4>(mx, S);
+    block_max_f<4>(mn, S);
+    float ibox[6] = {-mn[0] - rc, -mn[1] - rc, -mn[2] - rc, mx[0] + rc, mx[1] + rc, mx[2] + rc};
+    // 2. union box of gel surface triangles near the indenter box
+    float gx[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX}, gn[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
+    for (int i = tid; i < M.n_st; i += kThreads) {
+        BoxF b = gel_box(src, D, M, 1, i);
+        if (box_near(b, ibox))
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                gx[c] = fmaxf(gx[c], b.hi[c]);
+                gn[c] = fmaxf(gn[c], -b.lo[c]);
+            }
+    }
+    block_max_f<4>(gx, S);
+    block_max_f<4>(gn, S);
+    float gbox[6] = {-gn[0] - rc, -gn[1] - rc, -gn[2] - rc, gx[0] + rc, gx[1] + rc, gx[2] + rc};
+    bool any_gel = gx[0] > -FLT_MAX;
+    // 3. cull indenter primitives of each type against the gel box (order kept)
+    int nI[3];
+    int base_l[3];
+    int nprim[3] = {E.n_t, E.n_v, E.n_e};
+    int lbase = 0;
+    for (int ty = 0; ty < 3; ++ty) {
+        base_l[ty] = lbase;
+        int run = 0;
+        for (int b0 = 0; b0 < nprim[ty]; b0 += kThreads) {
+            int j = b0 + tid;
+            int keep = 0;
+            if (any_gel && j < nprim[ty]) keep = box_near(ind_box(src, D, E, ty, j), gbox) ? 1 : 0;
+            int tot;
+            int pos = block_scan(keep, tot, S);
+            if (keep) ilist[lbase + run + pos] = j;
+            run += tot;
+        }
+        nI[ty] = run;
+        lbase += nprim[ty];
+    }
+    // 4. per type: gel primitives in index order, matches in indenter order
+    int ngel[3] = {M.n_sv, M.n_st, M.n_se};
+    int total = 0;
+    for (int ty = 0; ty < 3; ++ty) {
+        const int* il = ilist + base_l[ty];
+        int nil = nI[ty];
+        for (int b0 = 0; b0 < ngel[ty]; b0 += kThreads) {
+            int i = b0 + tid;
+            int c = 0;
+            BoxF gb;
+            bool cand = false;
+            if (i < ngel[ty] && nil > 0) {
+                gb = gel_box(src, D, M, ty, i);
+                cand = box_near(gb, ibox);
+                if (cand)
+                    for (int q = 0; q < nil; ++q) c += bp_overlap(gb, ind_box(src, D, E, ty, il[q]), r, rlo, rhi) ? 1 : 0;
+            }
+            int tot;
+            int pos = block_scan(c, tot, S) + total;
+            if (c > 0) {
+                int gi = ty == 0 ? D.sv[M.sv_off + i] : i;
+                for (int q = 0; q < nil; ++q) {
+                    int j = il[q];
+                    if (bp_overlap(gb, ind_box(src, D, E, ty, j), r, rlo, rhi)) {
+                        if (pos < cap) out[pos] = make_int4(ty, gi, j, 0);
+                        ++pos;
+                    }
+                }
+            }
+            total += tot;
+        }
+    }
+    __syncthreads();          // candidate writes visible to the whole CTA
+    return total;
+}
+
+// ---------------------------------------------------------------------------
+// contact entries: per-vertex segmented reduction of pair / lag slot values
+
+struct ContactCtl {
+    int npairs, nlag, ncv;
+};
+
+__device__ void csr_build(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, ContactCtl& cc,
+                          Shared& S) {
+    const int tid = threadIdx.x;
+    int* cnt = D.cnt + P.v_off;
+    int* cvl = D.cvl + 6 * P.pair_off;
+    int* cvo = D.cvo + 6 * P.pair_off;
+    int* ent = D.ent + 6 * P.pair_off;
+    if (tid == 0) S.cnt[0] = 0;
+    __syncthreads();
+    const int4* pr = D.pairs + P.pair_off;
+    const LagRec* lg = D.lag + P.pair_off;
+    int np = cc.npairs, nl = cc.nlag;
+    for (int k = tid; k < np + nl; k += kThreads) {
+        int gs[3];
+        if (k < np) {
+            int gsl[4], isl[4];
+            pair_slots(D, M, E, pr[k], gsl, isl);
+            gs[0] = gsl[0]; gs[1] = gsl[1]; gs[2] = gsl[2];
+        } else {
+            const LagRec& L = lg[k - np];
+            gs[0] = L.g[0]; gs[1] = L.g[1]; gs[2] = L.g[2];
+        }
+        for (int s = 0; s < 3; ++s)
+            if (gs[s] >= 0) {
+                int old = atomicAdd(&cnt[gs[s]], 1);
+                if (old == 0) cvl[atomicAdd(&S.cnt[0], 1)] = gs[s];
+            }
+    }
+    __syncthreads();
+    int ncv = S.cnt[0];
+    int run = 0;
+    for (int b0 = 0; b0 < ncv; b0 += kThreads) {
+        int i = b0 + tid;
+        int c = i < ncv ? cnt[cvl[i]] : 0;
+        int tot;
+        int pos = block_scan(c, tot, S) + run;
+        if (i < ncv) cvo[i] = pos;
+        run += tot;
+    }
+    if (tid == 0) cvo[ncv] = run;
+    __syncthreads();
+    for (int i = tid; i < ncv; i += kThreads) cnt[cvl[i]] = cvo[i];
+    __syncthreads();
+    for (int k = tid; k < np + nl; k += kThreads) {
+        int gs[3];
+        if (k < np) {
+            int gsl[4], isl[4];
+            pair_slots(D, M, E, pr[k], gsl, isl);
+            gs[0] = gsl[0]; gs[1] = gsl[1]; gs[2] = gsl[2];
+        } else {
+            const LagRec& L = lg[k - np];
+            gs[0] = L.g[0]; gs[1] = L.g[1]; gs[2] = L.g[2];
+        }
+        int ebase = k < np ? 3 * k : 3 * (P.pair_cap + (k - np));
+        for (int s = 0; s < 3; ++s)
+            if (gs[s] >= 0) ent[atomicAdd(&cnt[gs[s]], 1)] = ebase + s;
+    }
+    __syncthreads();
+    for (int i = tid; i < ncv; i += kThreads) {
+        int a = cvo[i], b = cvo[i + 1];
+        for (int x = a + 1; x < b; ++x) {
+            int key = ent[x];
+            int y = x - 1;
+            while (y >= a && ent[y] > key) {
+                ent[y + 1] = ent[y];
+                --y;
+            }
+            ent[y + 1] = key;
+        }
+        cnt[cvl[i]] = 0;
+    }
+    __syncthreads();
+    cc.ncv = ncv;
+}
+
+// adds the slot values of every contact vertex into g[gb], blk[gb]
+__device__ void contact_gather(const Dev& D, const PadDev& P, const ContactCtl& cc, int gb) {
+    const int* cvl = D.cvl + 6 * P.pair_off;
+    const int* cvo = D.cvo + 6 * P.pair_off;
+    const int* ent = D.ent + 6 * P.pair_off;
+    const float* sb = D.slotbuf + (size_t)9 * 6 * P.pair_off;
+    for (int i = threadIdx.x; i < cc.ncv; i += kThreads) {
+        float acc[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) acc[c] = 0.f;
+        for (int x = cvo[i]; x < cvo[i + 1]; ++x) {
+            const float* e = sb + 9 * ent[x];
+#pragma unroll
+            for (int c = 0; c < 9; ++c) acc[c] += e[c];
+        }
+        int si = P.v_off + cvl[i];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) D.g[gb][c * D.Vt + si] += acc[c];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) D.blk[gb][c * D.Vt + si] += acc[3 + c];
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// pair passes
+
+// minimum distance over the candidates at (u, s)
+__device__ double pair_dmin(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np, double s,
+                            Shared& S) {
+    double dm = 1e300;
+    const int4* pr = D.pairs + P.pair_off;
+    for (int k = threadIdx.x; k < np; k += kThreads) {
+        int gsl[4], isl[4];
+        int4 q = pr[k];
+        pair_slots(D, M, E, q, gsl, isl);
+        dm = fmin(dm, pair_distance(D, P, M, q.x, gsl, isl, 0.0f, s, 2.0 * P.dhat));
+    }
+    return block_min_d(dm, S);
+}
+
+// p^T H p of the barrier and friction terms and the per-pair step bound
+__device__ void pair_php(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np, int nl, double s,
+                         double& php, double& accd, Shared& S) {
+    double acc = 0.0, amin = 1e300;
+    const int4* pr = D.pairs + P.pair_off;
+    const double dh = P.dhat, kap = P.kappa;
+    for (int k = threadIdx.x; k < np; k += kThreads) {
+        int gsl[4], isl[4];
+        int4 q = pr[k];
+        pair_slots(D, M, E, q, gsl, isl);
+        float pk = 0.f;
+        V3<double> dl[4];
+#pragma unroll
+        for (int sl = 0; sl < 4; ++sl) {
+            if (gsl[sl] >= 0) {
+                int si = P.v_off + gsl[sl];
+                float a = D.p[si], b = D.p[D.Vt + si], c = D.p[2 * D.Vt + si];
+                pk = fmaxf(pk, sqrtf(a * a + b * b + c * c));
+                dl[sl] = {a, b, c};
+            } else {
+                dl[sl] = {0.0, 0.0, 0.0};
+            }
+        }
+        V3<float> Xf[4];
+        load_slots<float>(D, P, M, gsl, isl, 0.0f, s, Xf);
+        float df = pair_feature<float>(q.x, Xf).d;
+        double d;
+        if ((double)df > 2.0 * dh) {
+            d = (double)df * (1.0 - 1e-5);
+        } else {
+            V3<double> X[4];
+            load_slots<double>(D, P, M, gsl, isl, 0.0f, s, X);
+            Feature<double> f = pair_feature<double>(q.x, X);
+            d = f.d;
+            if (d < dh) {
+                double d1, d2;
+                feat_dir_derivs(f, X, dl, d1, d2);
+                acc += kap * (barrier_b2(d, dh) * d1 * d1 + barrier_b1(d, dh) * d2);
+            }
+        }
+        if (pk > 0.f) amin = fmin(amin, (double)kEta * d / (double)pk);
+    }
+    // friction (lagged pairs)
+    const LagRec* lg = D.lag + P.pair_off;
+    if (P.mu_f > 0.f)
+        for (int l = threadIdx.x; l < nl; l += kThreads) {
+            const LagRec& L = lg[l];
+            double Dl[3] = {-s * L.dY[0], -s * L.dY[1], -s * L.dY[2]}, pd[3] = {0, 0, 0};
+            for (int gs = 0; gs < 3; ++gs)
+                if (L.g[gs] >= 0) {
+                    int si = P.v_off + L.g[gs];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        int sc = c * D.Vt + si;
+                        Dl[c] += (double)L.w[gs] * (double)((D.uh[sc] - D.u0h[sc]) + (D.ul[sc] - D.u0l[sc]));
+                        pd[c] += (double)L.w[gs] * (double)D.p[sc];
+                    }
+                }
+            double nD = L.n[0] * Dl[0] + L.n[1] * Dl[1] + L.n[2] * Dl[2];
+            double np_ = L.n[0] * pd[0] + L.n[1] * pd[1] + L.n[2] * pd[2];
+            double tD[3], tp[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                tD[c] = Dl[c] - L.n[c] * nD;
+                tp[c] = pd[c] - L.n[c] * np_;
+            }
+            double sv = sqrt(tD[0] * tD[0] + tD[1] * tD[1] + tD[2] * tD[2]);
+            double eps = P.eps_v, cf = (double)P.mu_f * L.lam;
+            double tp2 = tp[0] * tp[0] + tp[1] * tp[1] + tp[2] * tp[2];
+            double up = sv > 0 ? (tD[0] * tp[0] + tD[1] * tp[1] + tD[2] * tp[2]) / sv : 0.0;
+            acc += cf * (moll_f1_over_s(sv, eps) * tp2 - moll_c(sv, eps) * up * up);
+        }
+    double v[1] = {acc};
+    block_sum<1>(v, S);
+    php = v[0];
+    accd = block_min_d(amin, S);
+}
+
+// trial pass over pairs at u + alpha p: slot contributions and remainders
+__device__ void pair_trial(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np, int nl, double s,
+                           float alpha, double& rem, int& bad, Shared& S) {
+    double acc = 0.0;
+    int badl = 0;
+    const int4* pr = D.pairs + P.pair_off;
+    float* sb = D.slotbuf + (size_t)9 * 6 * P.pair_off;
+    const double dh = P.dhat, kap = P.kappa;
+    for (int k = threadIdx.x; k < np; k += kThreads) {
+        int gsl[4], isl[4];
+        int4 q = pr[k];
+        pair_slots(D, M, E, q, gsl, isl);
+        V3<float> Xf[4];
+        load_slots<float>(D, P, M, gsl, isl, alpha, s, Xf);
+        float d1f = pair_feature<float>(q.x, Xf).d;
+        load_slots<float>(D, P, M, gsl, isl, 0.0f, s, Xf);
+        float d0f = pair_feature<float>(q.x, Xf).d;
+        float out[3][9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int c = 0; c < 9; ++c) out[a][c] = 0.f;
+        if ((double)d1f <= 2.0 * dh || (double)d0f <= 2.0 * dh) {
+            V3<double> X1[4], X0[4];
+            load_slots<double>(D, P, M, gsl, isl, alpha, s, X1);
+            load_slots<double>(D, P, M, gsl, isl, 0.0f, s, X0);
+            Feature<double> f1 = pair_feature<double>(q.x, X1);
+            Feature<double> f0 = pair_feature<double>(q.x, X0);
+            if (!(f1.d > 0.0)) {
+                badl = 1;
+            } else if (f1.d < dh || f0.d < dh) {
+                V3<double> r = feat_r(f1, X1);
+                double inv = 1.0 / f1.d;
+                V3<double> rh = inv * r;
+                double b1 = kap * barrier_b1(f1.d, dh), b2 = kap * barrier_b2(f1.d, dh);
+                double gdp = 0.0;
+#pragma unroll
+                for (int sl = 0; sl < 3; ++sl)
+                    if (gsl[sl] >= 0) {
+                        int si = P.v_off + gsl[sl];
+                        V3<double> pv = {D.p[si], D.p[D.Vt + si], D.p[2 * D.Vt + si]};
+                        gdp += f1.w[sl] * dot(rh, pv);
+                        double gw = b1 * f1.w[sl], kw = b2 * f1.w[sl] * f1.w[sl];
+                        out[sl][0] = (float)(gw * rh.x);
+                        out[sl][1] = (float)(gw * rh.y);
+                        out[sl][2] = (float)(gw * rh.z);
+                        out[sl][3] = (float)(kw * rh.x * rh.x);
+                        out[sl][4] = (float)(kw * rh.y * rh.y);
+                        out[sl][5] = (float)(kw * rh.z * rh.z);
+                        out[sl][6] = (float)(kw * rh.x * rh.y);
+                        out[sl][7] = (float)(kw * rh.x * rh.z);
+                        out[sl][8] = (float)(kw * rh.y * rh.z);
+                    }
+                acc += kap * (barrier_b(f0.d, dh) - barrier_b(f1.d, dh)) + (double)alpha * b1 * gdp;
+            }
+        }
+#pragma unroll
+        for (int sl = 0; sl < 3; ++sl)
+            if (gsl[sl] >= 0)
+#pragma unroll
+                for (int c = 0; c < 9; ++c) sb[9 * (3 * k + sl) + c] = out[sl][c];
+    }
+    const LagRec* lg = D.lag + P.pair_off;
+    for (int l = threadIdx.x; l < nl; l += kThreads) {
+        const LagRec& L = lg[l];
+        double D1[3] = {-s * L.dY[0], -s * L.dY[1], -s * L.dY[2]}, pd[3] = {0, 0, 0};
+        for (int gs = 0; gs < 3; ++gs)
+            if (L.g[gs] >= 0) {
+                int si = P.v_off + L.g[gs];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    int sc = c * D.Vt + si;
+                    float pv = D.p[sc];
+                    D1[c] += (double)L.w[gs] * (double)((D.uh[sc] - D.u0h[sc]) + (D.ul[sc] - D.u0l[sc]) + alpha * pv);
+                    pd[c] += (double)L.w[gs] * (double)pv;
+                }
+            }
+        double D0[3] = {D1[0] - alpha * pd[0], D1[1] - alpha * pd[1], D1[2] - alpha * pd[2]};
+        double n1 = L.n[0] * D1[0] + L.n[1] * D1[1] + L.n[2] * D1[2];
+        double n0 = L.n[0] * D0[0] + L.n[1] * D0[1] + L.n[2] * D0[2];
+        double t1[3], t0[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            t1[c] = D1[c] - L.n[c] * n1;
+            t0[c] = D0[c] - L.n[c] * n0;
+        }
+        double s1 = sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+        double s0 = sqrt(t0[0] * t0[0] + t0[1] * t0[1] + t0[2] * t0[2]);
+        double eps = P.eps_v, cf = (double)P.mu_f * L.lam;
+        double f1s = moll_f1_over_s(s1, eps), cs = moll_c(s1, eps);
+        double tdp = t1[0] * pd[0] + t1[1] * pd[1] + t1[2] * pd[2];
+        acc += cf * (moll_f(s0, eps) - moll_f(s1, eps) + (double)alpha * f1s * tdp);
+        double uh[3] = {0, 0, 0};
+        if (s1 > 0)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) uh[c] = t1[c] / s1;
+        // tangent-plane Hessian f'/s (I - n n^T) - c(s) u u^T
+        double Hn[6];
+        Hn[0] = f1s * (1.0 - L.n[0] * L.n[0]) - cs * uh[0] * uh[0];
+        Hn[1] = f1s * (1.0 - L.n[1] * L.n[1]) - cs * uh[1] * uh[1];
+        Hn[2] = f1s * (1.0 - L.n[2] * L.n[2]) - cs * uh[2] * uh[2];
+        Hn[3] = -f1s * L.n[0] * L.n[1] - cs * uh[0] * uh[1];
+        Hn[4] = -f1s * L.n[0] * L.n[2] - cs * uh[0] * uh[2];
+        Hn[5] = -f1s * L.n[1] * L.n[2] - cs * uh[1] * uh[2];
+        for (int gs = 0; gs < 3; ++gs)
+            if (L.g[gs] >= 0) {
+                float* e = sb + 9 * (3 * (P.pair_cap + l) + gs);
+                double gw = cf * f1s * L.w[gs], kw = cf * L.w[gs] * L.w[gs];
+                e[0] = (float)(gw * t1[0]);
+                e[1] = (float)(gw * t1[1]);
+                e[2] = (float)(gw * t1[2]);
+                for (int c = 0; c < 6; ++c) e[3 + c] = (float)(kw * Hn[c]);
+            }
+    }
+    double v[1] = {acc};
+    block_sum<1>(v, S);
+    rem = v[0];
+    if (badl) S.flag = 1;
+    __syncthreads();
+    bad = S.flag;
+    __syncthreads();
+    if (threadIdx.x == 0) S.flag = 0;
+    __syncthreads();
+}
+
+// lag records: candidates closer than dhat at the frame start
+__device__ int lag_build(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np, Shared& S) {
+    const int4* pr = D.pairs + P.pair_off;
+    LagRec* lg = D.lag + P.pair_off;
+    const double dh = P.dhat, kap = P.kappa;
+    int run = 0;
+    for (int b0 = 0; b0 < np; b0 += kThreads) {
+        int k = b0 + threadIdx.x;
+        int keep = 0;
+        LagRec L;
+        if (k < np && P.mu_f > 0.f) {
+            int gsl[4], isl[4];
+            int4 q = pr[k];
+            pair_slots(D, M, E, q, gsl, isl);
+            V3<double> X[4];
+            load_slots<double>(D, P, M, gsl, isl, 0.0f, 0.0, X);
+            Feature<double> f = pair_feature<double>(q.x, X);
+            if (f.d < dh && f.d > 0.0) {
+                keep = 1;
+                V3<double> r = feat_r(f, X);
+                double inv = 1.0 / f.d;
+                L.n[0] = (float)(r.x * inv);
+                L.n[1] = (float)(r.y * inv);
+                L.n[2] = (float)(r.z * inv);
+                L.lam = -kap * barrier_b1(f.d, dh);
+                double dY[3] = {0, 0, 0};
+                for (int sl = 0; sl < 4; ++sl) {
+                    if (sl < 3) {
+                        L.g[sl] = gsl[sl];          // mesh-local vertex id or -1
+                        L.w[sl] = gsl[sl] >= 0 ? (float)f.w[sl] : 0.f;
+                    }
+                    if (isl[sl] >= 0)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            dY[c] += -f.w[sl] * ((double)D.Yn[3 * (P.yw_off + isl[sl]) + c] -
+                                                 (double)D.Yt[3 * (P.yw_off + isl[sl]) + c]);
+                }
+                L.dY[0] = (float)dY[0];
+                L.dY[1] = (float)dY[1];
+                L.dY[2] = (float)dY[2];
+            }
+        }
+        int tot;
+        int pos = block_scan(keep, tot, S) + run;
+        if (keep) lg[pos] = L;
+        run += tot;
+    }
+    __syncthreads();
+    return run;
+}
+
+// ---------------------------------------------------------------------------
+// vertex passes
+
+struct Dots {
+    double zy, yPy, pg1, yp;
+    float ginf;
+    int bad;
+};
+
+// Completes g and the blocks at u + alpha p (inertia, Dirichlet), applies
+// the preconditioner and reduces the Dai-Kou dot products.
+__device__ Dots finalize(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, int gb, int go, bool dots,
+                         Shared& S) {
+    double v[4] = {0, 0, 0, 0};
+    float gi[1] = {0.f};
+    int bad = 0;
+    const float rho = P.rho;
+    for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
+        int si = P.v_off + i;
+        float* g = D.g[gb];
+        if (D.fixed[M.xv_off + i]) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                g[c * D.Vt + si] = 0.f;
+                D.z[c * D.Vt + si] = 0.f;
+            }
+            continue;
+        }
+        float m = rho * D.vlump[M.xv_off + i];
+        float g1[3], pv[3], K[6];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            int sc = c * D.Vt + si;
+            pv[c] = D.p[sc];
+            float du = (D.uh[sc] - D.uhat[sc]) + D.ul[sc] + alpha * pv[c];
+            g1[c] = g[sc] + m * du;
+            g[sc] = g1[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) K[c] = D.blk[gb][c * D.Vt + si];
+        K[0] += m; K[1] += m; K[2] += m;
+        float Ki[6];
+        if (P.precond == 0) {
+            if (!sym_inverse(K, Ki)) bad = 1;
+        } else {
+            Ki[0] = 1.f / K[0]; Ki[1] = 1.f / K[1]; Ki[2] = 1.f / K[2];
+            Ki[3] = Ki[4] = Ki[5] = 0.f;
+        }
+        float z[3];
+        sym_apply(Ki, g1, z);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            D.z[c * D.Vt + si] = z[c];
+            gi[0] = fmaxf(gi[0], fabsf(g1[c]));
+        }
+        if (!(isfinite(g1[0]) && isfinite(g1[1]) && isfinite(g1[2]))) bad = 1;
+        if (dots) {
+            float y[3], Py[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) y[c] = g1[c] - D.g[go][c * D.Vt + si];
+            sym_apply(Ki, y, Py);
+            v[0] += (double)(z[0] * y[0]) + (double)(z[1] * y[1]) + (double)(z[2] * y[2]);
+            v[1] += (double)(y[0] * Py[0]) + (double)(y[1] * Py[1]) + (double)(y[2] * Py[2]);
+            v[2] += (double)(pv[0] * g1[0]) + (double)(pv[1] * g1[1]) + (double)(pv[2] * g1[2]);
+            v[3] += (double)(y[0] * pv[0]) + (double)(y[1] * pv[1]) + (double)(y[2] * pv[2]);
+        }
+    }
+    if (bad) S.flag = 1;
+    block_sum<4>(v, S);
+    block_max_f<1>(gi, S);
+    Dots d{v[0], v[1], v[2], v[3], gi[0], 0};
+    d.bad = S.flag;
+    __syncthreads();
+    if (threadIdx.x == 0) S.flag = 0;
+    __syncthreads();
+    return d;
+}
+
+struct DirOut {
+    double gTp, pMp;
+    float pn;
+};
+
+// optionally u += alpha p (double-float), then p = -z + beta p; reduces
+// g^T p, p^T M p and max_i |p_i|
+__device__ DirOut direction(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, bool move, double beta,
+                            int gb, Shared& S) {
+    double v[2] = {0, 0};
+    float pn[1] = {0.f};
+    const float rho = P.rho;
+    const float bf = (float)beta;
+    for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
+        int si = P.v_off + i;
+        bool fx = D.fixed[M.xv_off + i] != 0;
+        float m = rho * D.vlump[M.xv_off + i];
+        float n2 = 0.f;
+        double gp = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            int sc = c * D.Vt + si;
+            float pv = D.p[sc];
+            if (move && !fx) {
+                float t = alpha * pv;
+                float hi = D.uh[sc], lo = D.ul[sc];
+                float s = hi + t;
+                float bb = s - hi;
+                float err = (hi - (s - bb)) + (t - bb);
+                lo += err;
+                float nh = s + lo;
+                D.ul[sc] = lo - (nh - s);
+                D.uh[sc] = nh;
+            }
+            float np = fx ? 0.f : (-D.z[sc] + bf * pv);
+            D.p[sc] = np;
+            n2 += np * np;
+            gp += (double)(D.g[gb][sc] * np);
+        }
+        v[0] += gp;
+        v[1] += (double)(m * n2);
+        pn[0] = fmaxf(pn[0], sqrtf(n2));
+    }
+    block_sum<2>(v, S);
+    block_max_f<1>(pn, S);
+    return DirOut{v[0], v[1], pn[0]};
+}
+
+// ---------------------------------------------------------------------------
+// frame setup: indenter world vertices, u0 = u, uhat = u + h v
+
+__device__ void rotation(const float* pose, double R[9]) {
+    double rx = pose[0], ry = pose[1], rz = pose[2];
+    double th = sqrt(rx * rx + ry * ry + rz * rz);
+    double kx = 0, ky = 0, kz = 0, sn = 0, cs1 = 0;
+    if (th > 1e-300) {
+        kx = rx / th; ky = ry / th; kz = rz / th;
+        sn = sin(th);
+        cs1 = 1.0 - cos(th);
+    }
+    double K[9] = {0, -kz, ky, kz, 0, -kx, -ky, kx, 0};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double kk = 0;
+            for (int k = 0; k < 3; ++k) kk += K[3 * i + k] * K[3 * k + j];
+            R[3 * i + j] = (i == j ? 1.0 : 0.0) + sn * K[3 * i + j] + cs1 * kk;
+        }
+}
+
+__device__ void world_indenter(const Dev& D, const PadDev& P, const EnvDev& E, const float* pose, float* Yw) {
+    double R[9];
+    rotation(pose, R);
+    for (int j = threadIdx.x; j < E.n_v; j += kThreads) {
+        const float* y = D.Y + 3 * (E.y_off + j);
+        for (int c = 0; c < 3; ++c)
+            Yw[3 * (P.yw_off + j) + c] =
+                (float)(R[3 * c] * y[0] + R[3 * c + 1] * y[1] + R[3 * c + 2] * y[2] + (double)pose[3 + c]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the frame solve of one pad
+
+enum { ST_CONVERGED = 0, ST_MAXITER = 1, ST_NONFINITE = 2, ST_LINESEARCH = 3, ST_OVERFLOW = 4 };
+
+struct PadCounters {
+    long long iters, substeps, rebuilds, halvings, tet_passes, vert_passes, pair_evals, peak_pairs;
+};
+
+__device__ void solve_pad(const Dev& D, int pad, Shared& S) {
+    const PadDev P = D.pads[pad];
+    const MeshDev M = D.meshes[P.mesh];
+    const EnvDev E = D.envs[P.env];
+    const int tid = threadIdx.x;
+    PadCounters ctr{0, 0, 0, 0, 0, 0, 0, 0};
+    int status = ST_CONVERGED;
+    unsigned long long t0 = 0;
+    if (tid == 0) t0 = global_ns();
+    const unsigned long long budget = D.budget_ns;
+    // frame setup
+    world_indenter(D, P, E, D.pose_t + 6 * pad, D.Yt);
+    world_indenter(D, P, E, D.pose_n + 6 * pad, D.Yn);
+    for (int i = tid; i < M.n_v; i += kThreads) {
+        int si = P.v_off + i;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            int sc = c * D.Vt + si;
+            float hi = D.uh[sc], lo = D.ul[sc];
+            D.u0h[sc] = hi;
+            D.u0l[sc] = lo;
+            D.uhat[sc] = (hi + lo) + P.h * D.vel[sc];
+        }
+    }
+    __syncthreads();
+    float dyv[1] = {0.f};
+    for (int j = tid; j < E.n_v; j += kThreads) {
+        float a = 0.f;
+        for (int c = 0; c < 3; ++c) {
+            float d = D.Yn[3 * (P.yw_off + j) + c] - D.Yt[3 * (P.yw_off + j) + c];
+            a += d * d;
+        }
+        dyv[0] = fmaxf(dyv[0], sqrtf(a));
+    }
+    block_max_f<1>(dyv, S);
+    const double Dy = (double)dyv[0] * (1.0 + 1e-6);
+    const double dh = P.dhat, margin = P.dhat;
+    const double rbp = (dh + margin) * (1.0 + 1e-6);
+    int4* pairs = D.pairs + P.pair_off;
+    int* il = D.ilist + P.il_off;
+    double s = 0.0, Mb = 0.0;
+    ContactCtl cc{0, 0, 0};
+    {
+        SrcState src{&D, &P, &M, 0.0f};
+        int n = bp_build(src, D, M, E, il, rbp, pairs, P.pair_cap, S);
+        ctr.rebuilds++;
+        ctr.peak_pairs = n;
+        if (n > P.pair_cap) status = ST_OVERFLOW;
+        cc.npairs = min(n, P.pair_cap);
+    }
+    if (status == ST_CONVERGED) {
+        cc.nlag = lag_build(D, P, M, E, cc.npairs, S);
+        csr_build(D, P, M, E, cc, S);
+    }
+    const float tol_abs = P.tol * P.g_ref;
+    const float tol_sub = fmaxf(P.tol, P.tol_adv) * P.g_ref;
+    int gc = 0;          // buffer holding the current gradient
+    float ginf = 0.f;
+    while (status == ST_CONVERGED) {
+        if (s < 1.0) {
+            double ds;
+            if (Dy == 0.0) {
+                ds = 1.0 - s;
+            } else {
+                double dmin = pair_dmin(D, P, M, E, cc.npairs, s, S);
+                ctr.pair_evals += cc.npairs;
+                ds = fmin(1.0 - s, kEta * dmin / Dy);
+                if (Mb + ds * Dy > margin) {
+                    SrcState src{&D, &P, &M, (float)s};
+                    int n = bp_build(src, D, M, E, il, rbp, pairs, P.pair_cap, S);
+                    ctr.rebuilds++;
+                    ctr.peak_pairs = max(ctr.peak_pairs, (long long)n);
+                    if (n > P.pair_cap) { status = ST_OVERFLOW; break; }
+                    cc.npairs = n;
+                    csr_build(D, P, M, E, cc, S);
+                    Mb = 0.0;
+                    dmin = pair_dmin(D, P, M, E, cc.npairs, s, S);
+                    ds = fmin(fmin(1.0 - s, kEta * dmin / Dy), margin / Dy);
+                }
+            }
+            s = (ds >= 1.0 - s) ? 1.0 : s + ds;
+            Mb += ds * Dy;
+            ctr.substeps++;
+        }
+        // gradient and preconditioner at the current point
+        TetOut to = tet_pass<1>(D, P, M, 0.0f, gc, S);
+        ctr.tet_passes++;
+        double rem0;
+        int badp;
+        pair_trial(D, P, M, E, cc.npairs, cc.nlag, s, 0.0f, rem0, badp, S);
+        ctr.pair_evals += cc.npairs;
+        contact_gather(D, P, cc, gc);
+        Dots d0 = finalize(D, P, M, 0.0f, gc, gc, false, S);
+        ctr.vert_passes++;
+        if (to.bad || badp || d0.bad) { status = ST_NONFINITE; break; }
+        ginf = d0.ginf;
+        DirOut dir = direction(D, P, M, 0.0f, false, 0.0, gc, S);
+        ctr.vert_passes++;
+        const float target = (s >= 1.0) ? tol_abs : tol_sub;
+        while (ginf > target && ctr.iters < P.max_iter) {
+            if (over_budget(t0, budget, S)) { status = ST_MAXITER; break; }
+            if (dir.pn == 0.f || dir.gTp >= 0.0) {
+                dir = direction(D, P, M, 0.0f, false, 0.0, gc, S);
+                ctr.vert_passes++;
+                if (dir.pn == 0.f) break;
+            }
+            double a_up = dh / (2.0 * (double)dir.pn);
+            TetOut tp = tet_pass<0>(D, P, M, 0.0f, gc, S);
+            ctr.tet_passes++;
+            double php_c, a_ccd;
+            pair_php(D, P, M, E, cc.npairs, cc.nlag, s, php_c, a_ccd, S);
+            ctr.pair_evals += cc.npairs;
+            double pHp = tp.acc + php_c + dir.pMp;
+            double a_bar = pHp > 0.0 ? -dir.gTp / pHp : 1e300;
+            double alpha = fmin(fmin(a_up, a_ccd), a_bar);
+            if (Mb + alpha * dir.pn > margin) {
+                SrcState src{&D, &P, &M, (float)s};
+                int n = bp_build(src, D, M, E, il, rbp, pairs, P.pair_cap, S);
+                ctr.rebuilds++;
+                ctr.peak_pairs = max(ctr.peak_pairs, (long long)n);
+                if (n > P.pair_cap) { status = ST_OVERFLOW; break; }
+                cc.npairs = n;
+                csr_build(D, P, M, E, cc, S);
+                Mb = 0.0;
+                double dummy;
+                pair_php(D, P, M, E, cc.npairs, cc.nlag, s, dummy, a_ccd, S);
+                ctr.pair_evals += cc.npairs;
+                alpha = fmin(fmin(a_up, a_ccd), a_bar);
+            }
+            const int gn = gc ^ 1;
+            bool accepted = false;
+            Dots dt{};
+            for (int hv = 0; hv <= kMaxHalvings; ++hv) {
+                float af = (float)alpha;
+                TetOut tt = tet_pass<1>(D, P, M, af, gn, S);
+                ctr.tet_passes++;
+                double remc;
+                int bp;
+                pair_trial(D, P, M, E, cc.npairs, cc.nlag, s, af, remc, bp, S);
+                ctr.pair_evals += cc.npairs;
+                contact_gather(D, P, cc, gn);
+                dt = finalize(D, P, M, af, gn, gc, true, S);
+                ctr.vert_passes++;
+                if (!tt.bad && !bp && !dt.bad) {
+                    double a = (double)af;
+                    double R = tt.acc + remc + 0.5 * a * a * dir.pMp;
+                    double dE = a * dt.pg1 - R;
+                    if (dE <= kArmijoC * a * dir.gTp) {
+                        accepted = true;
+                        alpha = a;
+                        break;
+                    }
+                }
+                alpha *= 0.5;
+                ctr.halvings++;
+            }
+            if (!accepted) { status = ST_LINESEARCH; break; }
+            Mb += alpha * dir.pn;
+            ctr.iters++;
+            double beta = 0.0;
+            if (fabs(dt.yp) > 1e-300) beta = dt.zy / dt.yp - (dt.yPy / dt.yp) * (dt.pg1 / dt.yp);
+            dir = direction(D, P, M, (float)alpha, true, beta, gn, S);
+            ctr.vert_passes++;
+            if (dir.gTp >= 0.0) {
+                dir = direction(D, P, M, 0.0f, false, 0.0, gn, S);
+                ctr.vert_passes++;
+            }
+            gc = gn;
+            ginf = dt.ginf;
+        }
+        if (status != ST_CONVERGED) break;
+        if (s >= 1.0) {
+            if (ginf > target) status = ST_MAXITER;
+            break;
+        }
+        if (ctr.substeps >= kMaxSubsteps || ctr.iters >= P.max_iter || over_budget(t0, budget, S)) {
+            status = ST_MAXITER;
+            break;
+        }
+    }
+    // the current gradient must sit in buffer 0 for the next frame's readers
+    // (none today); velocities and pose
+    for (int i = tid; i < M.n_v; i += kThreads) {
+        int si = P.v_off + i;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            int sc = c * D.Vt + si;
+            D.vel[sc] = ((D.uh[sc] - D.u0h[sc]) + (D.ul[sc] - D.u0l[sc])) / P.h;
+        }
+    }
+    if (tid == 0) {
+        if (D.status) D.status[pad] = status;
+        if (D.iters) D.iters[pad] = (int)ctr.iters;
+        long long* st = D.stats + 8 * pad;
+        st[0] = ctr.iters; st[1] = ctr.substeps; st[2] = ctr.rebuilds; st[3] = ctr.halvings;
+        st[4] = ctr.tet_passes; st[5] = ctr.vert_passes; st[6] = ctr.pair_evals; st[7] = ctr.peak_pairs;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) solve_kernel(Dev D) {
+    __shared__ Shared S;
+    if (threadIdx.x == 0) S.flag = 0;
+    for (;;) {
+        if (threadIdx.x == 0) S.pad = atomicAdd(D.queue, 1);
+        __syncthreads();
+        int q = S.pad;
+        __syncthreads();
+        if (q >= D.n_pads) break;
+        solve_pad(D, D.order[q], S);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// verification kernel: one CTA per pad (see tac_debug_eval)
+
+__global__ void __launch_bounds__(kThreads) debug_eval_kernel(Dev D, float alpha, double r, float* grad_out,
+                                                              float* blk_out, double* scal) {
+    __shared__ Shared S;
+    if (threadIdx.x == 0) S.flag = 0;
+    __syncthreads();
+    const int pad = blockIdx.x;
+    const PadDev P = D.pads[pad];
+    const MeshDev M = D.meshes[P.mesh];
+    const EnvDev E = D.envs[P.env];
+    world_indenter(D, P, E, D.pose_t + 6 * pad, D.Yt);
+    world_indenter(D, P, E, D.pose_t + 6 * pad, D.Yn);
+    __syncthreads();
+    SrcState src{&D, &P, &M, 1.0f};
+    int n = bp_build(src, D, M, E, D.ilist + P.il_off, r, D.pairs + P.pair_off, P.pair_cap, S);
+    ContactCtl cc{min(n, P.pair_cap), 0, 0};
+    csr_build(D, P, M, E, cc, S);
+    // u0 = uhat = u (no inertia offset, no friction lag)
+    for (int i = threadIdx.x; i < M.n_v; i += kThreads)
+        for (int c = 0; c < 3; ++c) {
+            int sc = c * D.Vt + P.v_off + i;
+            D.u0h[sc] = D.uh[sc];
+            D.u0l[sc] = D.ul[sc];
+            D.uhat[sc] = D.uh[sc] + D.ul[sc];
+        }
+    __syncthreads();
+    double dmin = pair_dmin(D, P, M, E, cc.npairs, 1.0, S);
+    TetOut tp = tet_pass<0>(D, P, M, 0.0f, 0, S);
+    double php_c, a_ccd;
+    pair_php(D, P, M, E, cc.npairs, 0, 1.0, php_c, a_ccd, S);
+    double pMp = 0.0;
+    {
+        double v[1] = {0.0};
+        for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
+            if (D.fixed[M.xv_off + i]) continue;
+            float m = P.rho * D.vlump[M.xv_off + i];
+            for (int c = 0; c < 3; ++c) {
+                float pv = D.p[c * D.Vt + P.v_off + i];
+                v[0] += (double)(m * pv * pv);
+            }
+        }
+        block_sum<1>(v, S);
+        pMp = v[0];
+    }
+    TetOut tt = tet_pass<1>(D, P, M, alpha, 0, S);
+    double remc;
+    int bp;
+    pair_trial(D, P, M, E, cc.npairs, 0, 1.0, alpha, remc, bp, S);
+    contact_gather(D, P, cc, 0);
+    // outputs before inertia / inversion: gradient with inertia m alpha p
+    double gp[1] = {0.0};
+    float gi[1] = {0.f};
+    for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
+        int si = P.v_off + i;
+        bool fx = D.fixed[M.xv_off + i] != 0;
+        float m = P.rho * D.vlump[M.xv_off + i];
+        for (int c = 0; c < 3; ++c) {
+            int sc = c * D.Vt + si;
+            float gv = fx ? 0.f : D.g[0][sc] + m * alpha * D.p[sc];
+            if (grad_out) grad_out[3 * si + c] = gv;
+            gp[0] += (double)(gv * D.p[sc]);
+            gi[0] = fmaxf(gi[0], fabsf(gv));
+        }
+        if (blk_out)
+            for (int c = 0; c < 6; ++c) blk_out[6 * si + c] = D.blk[0][c * D.Vt + si] + (c < 3 ? m : 0.f);
+    }
+    block_sum<1>(gp, S);
+    block_max_f<1>(gi, S);
+    if (threadIdx.x == 0 && scal) {
+        double a = alpha;
+        double R = tt.acc + remc + 0.5 * a * a * pMp;
+        double* o = scal + 8 * pad;
+        o[0] = tp.acc;
+        o[1] = php_c;
+        o[2] = pMp;
+        o[3] = a * gp[0] - R;
+        o[4] = a_ccd;
+        o[5] = dmin;
+        o[6] = (double)n;
+        o[7] = (double)gi[0];
+    }
+}
+
+// candidate set of one pad for caller positions (see tac_broadphase)
+__global__ void __launch_bounds__(kThreads) broadphase_kernel(Dev D, int pad, const float* x, const float* y,
+                                                              double r, int* out, int cap, int* count) {
+    __shared__ Shared S;
+    const PadDev P = D.pads[pad];
+    const MeshDev M = D.meshes[P.mesh];
+    const EnvDev E = D.envs[P.env];
+    SrcArrays src{x, y};
+    int n = bp_build(src, D, M, E, D.ilist + P.il_off, r, D.pairs + P.pair_off, P.pair_cap, S);
+    for (int k = threadIdx.x; k < min(n, min(cap, P.pair_cap)); k += kThreads) {
+        int4 q = D.pairs[P.pair_off + k];
+        out[3 * k] = q.x;
+        out[3 * k + 1] = q.y;
+        out[3 * k + 2] = q.z;
+    }
+    if (threadIdx.x == 0) *count = n;
+}
+
+// marker readout: u_m = sum_k w_k u_{v_k}, first two components
+__global__ void markers_kernel(Dev D, float* out) {
+    int pad = blockIdx.y;
+    const PadDev P = D.pads[pad];
+    const MeshDev M = D.meshes[P.mesh];
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M.n_mk) return;
+    const int* id = D.mk_ids + 3 * (M.mk_off + m);
+    const float* w = D.mk_w + 3 * (M.mk_off + m);
+    for (int c = 0; c < 2; ++c) {
+        float a = 0.f;
+        for (int k = 0; k < 3; ++k) {
+            int sc = c * D.Vt + P.v_off + id[k];
+            a += w[k] * (D.uh[sc] + D.ul[sc]);
+        }
+        out[2 * (P.mk_out + m) + c] = a;
+    }
+}
+
+}  // namespace tac

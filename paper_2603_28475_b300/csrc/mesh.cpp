@@ -1,0 +1,340 @@
+// Host-side mesh preprocessing (see mesh.h).
+#include "mesh.h"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <numeric>
+
+namespace tac {
+
+namespace {
+
+uint32_t spread10(uint32_t v) {
+    v &= 0x3ff;
+    v = (v | (v << 16)) & 0x030000ff;
+    v = (v | (v << 8)) & 0x0300f00f;
+    v = (v | (v << 4)) & 0x030c30c3;
+    v = (v | (v << 2)) & 0x09249249;
+    return v;
+}
+
+double det3(const double m[9]) {
+    return m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
+           m[2] * (m[3] * m[7] - m[4] * m[6]);
+}
+
+void inv3(const double m[9], double o[9]) {
+    double d = det3(m);
+    o[0] = (m[4] * m[8] - m[5] * m[7]) / d;
+    o[1] = (m[2] * m[7] - m[1] * m[8]) / d;
+    o[2] = (m[1] * m[5] - m[2] * m[4]) / d;
+    o[3] = (m[5] * m[6] - m[3] * m[8]) / d;
+    o[4] = (m[0] * m[8] - m[2] * m[6]) / d;
+    o[5] = (m[2] * m[3] - m[0] * m[5]) / d;
+    o[6] = (m[3] * m[7] - m[4] * m[6]) / d;
+    o[7] = (m[1] * m[6] - m[0] * m[7]) / d;
+    o[8] = (m[0] * m[4] - m[1] * m[3]) / d;
+}
+
+char msgbuf[256];
+
+}  // namespace
+
+bool build_pad_mesh(int nv, int nt, int nf, int nm, const float* rest, const int* tets,
+                    const int* fixed, const float* markers, PadMesh& M, std::string& err) {
+    if (nv <= 0 || nt <= 0 || nf < 0 || nm < 0 || !rest || !tets || (nf && !fixed) || (nm && !markers)) {
+        err = "pad descriptor has a non-positive size or a null array";
+        return false;
+    }
+    if (nv > kVertMask) {
+        err = "pad has too many vertices";
+        return false;
+    }
+    M.n_v = nv;
+    M.n_t = nt;
+    M.n_mk = nm;
+    M.X.assign(rest, rest + 3 * static_cast<size_t>(nv));
+    M.fixed.assign(nv, 0);
+    for (int i = 0; i < nf; ++i) {
+        if (fixed[i] < 0 || fixed[i] >= nv) {
+            err = "fixed vertex id out of range";
+            return false;
+        }
+        M.fixed[fixed[i]] = 1;
+    }
+    // rest shape per input tet
+    std::vector<double> Binv(9 * static_cast<size_t>(nt));
+    std::vector<double> vol(nt);
+    M.vlump.assign(nv, 0.0f);
+    std::vector<double> vl(nv, 0.0);
+    for (int t = 0; t < nt; ++t) {
+        const int* c = tets + 4 * static_cast<size_t>(t);
+        for (int k = 0; k < 4; ++k)
+            if (c[k] < 0 || c[k] >= nv) {
+                std::snprintf(msgbuf, sizeof msgbuf, "tet %d has a vertex id out of range", t);
+                err = msgbuf;
+                return false;
+            }
+        double Dm[9];
+        for (int col = 0; col < 3; ++col)
+            for (int r = 0; r < 3; ++r)
+                Dm[3 * r + col] = static_cast<double>(rest[3 * c[col + 1] + r]) - static_cast<double>(rest[3 * c[0] + r]);
+        double d = det3(Dm);
+        if (!(d > 0.0)) {
+            std::snprintf(msgbuf, sizeof msgbuf, "tet %d has non-positive rest volume", t);
+            err = msgbuf;
+            return false;
+        }
+        inv3(Dm, &Binv[9 * static_cast<size_t>(t)]);
+        vol[t] = d / 6.0;
+        for (int k = 0; k < 4; ++k) vl[c[k]] += vol[t] / 4.0;
+    }
+    for (int i = 0; i < nv; ++i) M.vlump[i] = static_cast<float>(vl[i]);
+
+    // canonical surface: boundary faces (sorted ids), sorted lexicographically
+    std::vector<std::array<int, 3>> faces;
+    faces.reserve(4 * static_cast<size_t>(nt));
+    static const int fidx[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
+    for (int t = 0; t < nt; ++t) {
+        const int* c = tets + 4 * static_cast<size_t>(t);
+        for (auto& f : fidx) {
+            std::array<int, 3> a = {c[f[0]], c[f[1]], c[f[2]]};
+            std::sort(a.begin(), a.end());
+            faces.push_back(a);
+        }
+    }
+    std::sort(faces.begin(), faces.end());
+    std::vector<std::array<int, 3>> surf;
+    for (size_t i = 0; i < faces.size();) {
+        size_t j = i;
+        while (j < faces.size() && faces[j] == faces[i]) ++j;
+        if (j - i == 1) surf.push_back(faces[i]);
+        i = j;
+    }
+    M.st.clear();
+    std::vector<std::array<int, 2>> edges;
+    for (auto& f : surf) {
+        M.st.insert(M.st.end(), f.begin(), f.end());
+        edges.push_back({f[0], f[1]});
+        edges.push_back({f[1], f[2]});
+        edges.push_back({f[0], f[2]});
+    }
+    std::sort(edges.begin(), edges.end());
+    edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
+    M.se.clear();
+    double lsum = 0.0;
+    for (auto& e : edges) {
+        M.se.push_back(e[0]);
+        M.se.push_back(e[1]);
+        double l2 = 0.0;
+        for (int r = 0; r < 3; ++r) {
+            double dd = static_cast<double>(rest[3 * e[1] + r]) - rest[3 * e[0] + r];
+            l2 += dd * dd;
+        }
+        lsum += std::sqrt(l2);
+    }
+    M.lbar = edges.empty() ? 0.0 : lsum / edges.size();
+    M.sv.clear();
+    for (int v : M.st) M.sv.push_back(v);
+    std::sort(M.sv.begin(), M.sv.end());
+    M.sv.erase(std::unique(M.sv.begin(), M.sv.end()), M.sv.end());
+
+    // markers: top-face triangle maximising the smallest barycentric coordinate
+    float ztop = rest[2];
+    for (int i = 0; i < nv; ++i) ztop = std::max(ztop, rest[3 * i + 2]);
+    std::vector<int> top;
+    for (size_t k = 0; k < surf.size(); ++k) {
+        const auto& f = surf[k];
+        if (rest[3 * f[0] + 2] == ztop && rest[3 * f[1] + 2] == ztop && rest[3 * f[2] + 2] == ztop)
+            top.push_back(static_cast<int>(k));
+    }
+    M.mk_ids.assign(3 * static_cast<size_t>(nm), 0);
+    M.mk_w.assign(3 * static_cast<size_t>(nm), 0.0f);
+    for (int m = 0; m < nm; ++m) {
+        double qx = markers[2 * m], qy = markers[2 * m + 1];
+        double best = -1e300, bw[3] = {0, 0, 0};
+        int bk = -1;
+        for (int k : top) {
+            const auto& f = surf[k];
+            double ax = rest[3 * f[0]], ay = rest[3 * f[0] + 1];
+            double v0x = rest[3 * f[1]] - ax, v0y = rest[3 * f[1] + 1] - ay;
+            double v1x = rest[3 * f[2]] - ax, v1y = rest[3 * f[2] + 1] - ay;
+            double v2x = qx - ax, v2y = qy - ay;
+            double den = v0x * v1y - v1x * v0y;
+            double l1 = (v2x * v1y - v1x * v2y) / den;
+            double l2 = (v0x * v2y - v2x * v0y) / den;
+            double l0 = 1.0 - l1 - l2;
+            double sc = std::min(l0, std::min(l1, l2));
+            if (sc > best) {
+                best = sc;
+                bk = k;
+                bw[0] = l0;
+                bw[1] = l1;
+                bw[2] = l2;
+            }
+        }
+        if (bk < 0 || best < -1e-9) {
+            std::snprintf(msgbuf, sizeof msgbuf, "marker %d is not on the top face", m);
+            err = msgbuf;
+            return false;
+        }
+        for (int r = 0; r < 3; ++r) {
+            M.mk_ids[3 * m + r] = surf[bk][r];
+            M.mk_w[3 * m + r] = static_cast<float>(bw[r]);
+        }
+    }
+
+    // patches: tets in Morton order of their centroids, cut greedily so that a
+    // patch has at most kPatchTets tets and kPatchVerts distinct vertices
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int i = 0; i < nv; ++i)
+        for (int r = 0; r < 3; ++r) {
+            lo[r] = std::min(lo[r], static_cast<double>(rest[3 * i + r]));
+            hi[r] = std::max(hi[r], static_cast<double>(rest[3 * i + r]));
+        }
+    double span = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+    std::vector<uint32_t> code(nt);
+    for (int t = 0; t < nt; ++t) {
+        const int* c = tets + 4 * static_cast<size_t>(t);
+        uint32_t q[3];
+        for (int r = 0; r < 3; ++r) {
+            double s = 0.25 * (rest[3 * c[0] + r] + rest[3 * c[1] + r] + rest[3 * c[2] + r] + rest[3 * c[3] + r]);
+            double u = span > 0 ? (s - lo[r]) / span : 0.0;
+            q[r] = static_cast<uint32_t>(std::min(1023.0, std::max(0.0, u * 1023.0)));
+        }
+        code[t] = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+    }
+    M.tet_order.resize(nt);
+    std::iota(M.tet_order.begin(), M.tet_order.end(), 0);
+    std::stable_sort(M.tet_order.begin(), M.tet_order.end(), [&](int a, int b) { return code[a] < code[b]; });
+
+    M.B.assign(9 * static_cast<size_t>(nt), 0.0f);
+    M.lconn.assign(nt, 0);
+    M.slot.assign(nt, 0);
+    M.patch.clear();
+    M.pvert.clear();
+    M.pcsr.clear();
+    std::vector<int> local(nv, -1);
+    std::vector<int> first_patch(nv, -1), last_patch(nv, -1);
+    std::vector<int> cur_verts;
+    int begin = 0;
+    auto flush = [&](int end) {
+        // local vertex list sorted by mesh id, local ids remapped accordingly
+        std::vector<int> verts = cur_verts;
+        std::sort(verts.begin(), verts.end());
+        int pidx = static_cast<int>(M.patch.size() / 4);
+        for (size_t l = 0; l < verts.size(); ++l) local[verts[l]] = static_cast<int>(l);
+        int nloc = static_cast<int>(verts.size());
+        int ntl = end - begin;
+        // corner slots: for each local vertex, its (tet, corner) pairs in (tet, corner) order
+        std::vector<int> count(nloc + 1, 0);
+        for (int k = begin; k < end; ++k) {
+            const int* c = tets + 4 * static_cast<size_t>(M.tet_order[k]);
+            for (int j = 0; j < 4; ++j) count[local[c[j]] + 1]++;
+        }
+        for (int l = 0; l < nloc; ++l) count[l + 1] += count[l];
+        std::vector<int> cursor(count.begin(), count.end() - 1);
+        int csr_begin = static_cast<int>(M.pcsr.size());
+        for (int l = 0; l <= nloc; ++l) M.pcsr.push_back(static_cast<uint16_t>(count[l]));
+        for (int k = begin; k < end; ++k) {
+            int t = M.tet_order[k];
+            const int* c = tets + 4 * static_cast<size_t>(t);
+            uint32_t lc = 0;
+            uint64_t sl = 0;
+            for (int j = 0; j < 4; ++j) {
+                int l = local[c[j]];
+                lc |= static_cast<uint32_t>(l) << (8 * j);
+                sl |= static_cast<uint64_t>(cursor[l]++) << (16 * j);
+            }
+            M.lconn[k] = lc;
+            M.slot[k] = sl;
+            for (int e = 0; e < 9; ++e) M.B[static_cast<size_t>(e) * nt + k] = static_cast<float>(Binv[9 * static_cast<size_t>(t) + e]);
+        }
+        int vert_begin = static_cast<int>(M.pvert.size());
+        for (int v : verts) {
+            M.pvert.push_back(v);
+            if (first_patch[v] < 0) first_patch[v] = pidx;
+            last_patch[v] = pidx;
+            local[v] = -1;
+        }
+        M.patch.push_back(begin);
+        M.patch.push_back(vert_begin);
+        M.patch.push_back(ntl | (nloc << 16));
+        M.patch.push_back(csr_begin);
+        cur_verts.clear();
+        begin = end;
+    };
+    for (int k = 0; k < nt; ++k) {
+        const int* c = tets + 4 * static_cast<size_t>(M.tet_order[k]);
+        int add = 0;
+        for (int j = 0; j < 4; ++j) {
+            bool seen = local[c[j]] >= 0;
+            for (int jj = 0; jj < j; ++jj) seen = seen || (c[jj] == c[j]);
+            add += seen ? 0 : 1;
+        }
+        if (k - begin >= kPatchTets || static_cast<int>(cur_verts.size()) + add > kPatchVerts) {
+            for (int v : cur_verts) local[v] = -1;
+            flush(k);
+        }
+        for (int j = 0; j < 4; ++j)
+            if (local[c[j]] < 0) {
+                local[c[j]] = 1;
+                cur_verts.push_back(c[j]);
+            }
+    }
+    for (int v : cur_verts) local[v] = -1;
+    flush(nt);
+    // first / last flags
+    int np = M.n_patch();
+    for (int p = 0; p < np; ++p) {
+        int vb = M.patch[4 * p + 1], nl = M.patch[4 * p + 2] >> 16;
+        for (int l = 0; l < nl; ++l) {
+            int v = M.pvert[vb + l];
+            if (first_patch[v] == p) M.pvert[vb + l] |= kFirstFlag;
+            if (last_patch[v] == p) M.pvert[vb + l] |= kLastFlag;
+        }
+    }
+    for (int v = 0; v < nv; ++v)
+        if (first_patch[v] < 0) {
+            std::snprintf(msgbuf, sizeof msgbuf, "vertex %d belongs to no tet", v);
+            err = msgbuf;
+            return false;
+        }
+    return true;
+}
+
+bool build_indenter_mesh(int nv, int nt, const float* verts, const int* tris, IndenterMesh& I,
+                         std::string& err) {
+    if (nv <= 0 || nt <= 0 || !verts || !tris) {
+        err = "indenter descriptor has a non-positive size or a null array";
+        return false;
+    }
+    I.n_v = nv;
+    I.n_t = nt;
+    I.Y.assign(verts, verts + 3 * static_cast<size_t>(nv));
+    I.tris.assign(tris, tris + 3 * static_cast<size_t>(nt));
+    std::vector<std::array<int, 2>> e;
+    for (int t = 0; t < nt; ++t) {
+        int a = tris[3 * t], b = tris[3 * t + 1], c = tris[3 * t + 2];
+        if (a < 0 || b < 0 || c < 0 || a >= nv || b >= nv || c >= nv) {
+            err = "indenter triangle has a vertex id out of range";
+            return false;
+        }
+        e.push_back({std::min(a, b), std::max(a, b)});
+        e.push_back({std::min(b, c), std::max(b, c)});
+        e.push_back({std::min(a, c), std::max(a, c)});
+    }
+    std::sort(e.begin(), e.end());
+    e.erase(std::unique(e.begin(), e.end()), e.end());
+    I.n_e = static_cast<int>(e.size());
+    I.edges.clear();
+    for (auto& x : e) {
+        I.edges.push_back(x[0]);
+        I.edges.push_back(x[1]);
+    }
+    return true;
+}
+
+}  // namespace tac

@@ -1,0 +1,64 @@
+// Host-side preprocessing of one gel pad mesh and one indenter mesh.
+//
+// Everything here runs once per distinct mesh at batch creation: validation,
+// rest shape (Dm^-1 and lumped volume), canonical surface primitives, marker
+// barycentric weights, and the spatial tet patches that the device kernels
+// stream through shared memory.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace tac {
+
+// Limits of one tet patch: its tets are processed one per thread of a CTA and
+// its vertices are addressed with 8-bit local indices.
+constexpr int kPatchTets = 256;
+constexpr int kPatchVerts = 256;
+
+// Flags carried in the high bits of a patch's vertex list entry.
+constexpr int kFirstFlag = 1 << 30;   // first patch (in processing order) touching the vertex
+constexpr int kLastFlag = 1 << 29;    // last patch touching the vertex
+constexpr int kVertMask = (1 << 29) - 1;
+
+struct PadMesh {
+    int n_v = 0, n_t = 0, n_mk = 0;
+    std::vector<float> X;             // [n_v*3] rest positions
+    std::vector<float> vlump;         // [n_v] lumped rest volume (sum of V/4); mass = rho * vlump
+    std::vector<uint8_t> fixed;       // [n_v] 1 = Dirichlet
+    // tets in patch order
+    std::vector<float> B;             // [9][n_t] Dm^-1 (row-major entries), SoA
+    std::vector<uint32_t> lconn;      // [n_t] 4 x 8-bit local vertex ids
+    std::vector<uint64_t> slot;       // [n_t] 4 x 16-bit corner slots in the patch CSR
+    std::vector<int> patch;           // [n_patch*4] tet_begin, vert_begin, n_t | n_v << 16, csr_begin
+    std::vector<int> pvert;           // per patch local vertex -> mesh vertex id | flags
+    std::vector<uint16_t> pcsr;       // per patch CSR offsets (n_v + 1 entries)
+    std::vector<int> tet_order;       // patch-order position -> input tet id
+    // canonical surface
+    std::vector<int> sv;              // surface vertex ids, sorted
+    std::vector<int> st;              // [n_st*3] surface triangles (sorted ids), sorted
+    std::vector<int> se;              // [n_se*2] surface edges (lo, hi), sorted
+    double lbar = 0.0;                // mean rest surface edge length
+    // markers
+    std::vector<int> mk_ids;          // [n_mk*3]
+    std::vector<float> mk_w;          // [n_mk*3]
+    int n_patch() const { return static_cast<int>(patch.size() / 4); }
+};
+
+struct IndenterMesh {
+    int n_v = 0, n_t = 0, n_e = 0;
+    std::vector<float> Y;             // [n_v*3] local frame
+    std::vector<int> tris;            // [n_t*3]
+    std::vector<int> edges;           // [n_e*2] distinct (lo, hi), sorted
+};
+
+// Builds a pad; returns false with a message on invalid input.
+bool build_pad_mesh(int n_verts, int n_tets, int n_fixed, int n_markers, const float* rest,
+                    const int* tets, const int* fixed, const float* markers, PadMesh& out,
+                    std::string& err);
+
+bool build_indenter_mesh(int n_verts, int n_tris, const float* verts, const int* tris,
+                         IndenterMesh& out, std::string& err);
+
+}  // namespace tac

@@ -1,0 +1,106 @@
+// Device-side data of a batch and the per-pad PNCG-IPC frame solve.
+//
+// One CTA owns one pad for a whole frame: it moves the indenter along its
+// path in CCD-bounded substeps, keeps the contact candidate set valid, and
+// runs the preconditioned nonlinear CG (Supp. A, Eq. dk_direction and
+// Eq. step_size) to convergence with only CTA-level barriers. The tet passes
+// stream spatial patches of <= 256 tets through shared memory; per-corner
+// contributions are summed per vertex through the patch's corner CSR
+// (a deterministic segmented reduction, no atomics).
+#pragma once
+
+#include <cstdint>
+
+#include "device_math.cuh"
+
+namespace tac {
+
+constexpr int kThreads = 256;
+constexpr int kStage = 4 * 256;      // corner slots of one patch
+
+struct MeshDev {
+    int xv_off, n_v;          // static per-vertex arrays (X, vlump, fixed)
+    int tet_off, n_t;         // tet arrays (B, lconn, slot)
+    int patch_off, n_patch;
+    int pvert_off, pcsr_off;
+    int sv_off, n_sv, st_off, n_st, se_off, n_se;
+    int mk_off, n_mk;
+};
+
+struct EnvDev {
+    int y_off, n_v, t_off, n_t, e_off, n_e;
+};
+
+struct PadDev {
+    int mesh, env;
+    int v_off;                // state vertex offset
+    int yw_off;               // per-pad world indenter vertex slots
+    int pair_off, pair_cap;   // candidate pairs (and lag records, entries)
+    int il_off;               // per-pad culled indenter primitive list
+    int mk_out;               // marker output offset (markers)
+    float mu, lam, rho, h, dhat, kappa, mu_f, eps_v, g_ref, tol, tol_adv;
+    int max_iter, precond;
+};
+
+struct LagRec {
+    int g[3];                 // gel vertex (mesh-local id) of each gel slot, -1 if none
+    float w[3];               // gel slot weights
+    float n[3];               // lagged contact normal
+    float dY[3];              // indenter closest-point displacement over the frame
+    double lam;               // lagged normal force magnitude -kappa b'(d)
+};
+
+// All device arrays of a batch (SoA with strides noted).
+struct Dev {
+    int n_pads, Vt;           // pads, state vertices
+    const MeshDev* meshes;
+    const EnvDev* envs;
+    const PadDev* pads;
+    const int* order;         // pads in processing order
+    // static mesh data
+    const float* X;           // [3][XVt] rest positions
+    int XVt;
+    const float* vlump;       // [XVt]
+    const uint8_t* fixed;     // [XVt]
+    const float* B;           // [9][Tt]
+    int Tt;
+    const uint32_t* lconn;    // [Tt]
+    const uint64_t* slot;     // [Tt]
+    const int4* patch;
+    const int* pvert;
+    const uint16_t* pcsr;
+    const int* sv;
+    const int* st;            // [n*3]
+    const int* se;            // [n*2]
+    const int* mk_ids;        // [n*3]
+    const float* mk_w;        // [n*3]
+    // indenters
+    const float* Y;           // [n*3] local
+    const int* it;            // [n*3]
+    const int* ie;            // [n*2]
+    float* Yt;                // [n*3] world at the frame start (per pad slots)
+    float* Yn;                // [n*3] world at the frame end
+    const float* pose_t;      // [n_pads*6]
+    const float* pose_n;      // [n_pads*6]
+    // state [c][Vt]
+    float *uh, *ul, *u0h, *u0l, *vel, *uhat, *p, *z;
+    float* g[2];              // [3][Vt]
+    float* blk[2];            // [6][Vt]
+    // contact scratch (per pad regions of pair_cap)
+    int4* pairs;
+    LagRec* lag;
+    float* slotbuf;           // [6 * pair_cap][9] per pad region (pairs then lag, 3 slots each)
+    int* ent;                 // [6 * pair_cap]
+    int* cvl;                 // [6 * pair_cap + 1] contact vertex list / offsets
+    int* cvo;                 // [6 * pair_cap + 1]
+    int* cnt;                 // [Vt] zero between uses
+    int* ilist;               // culled indenter primitives
+    // outputs
+    int* status;
+    int* iters;
+    long long* stats;         // [n_pads][8]
+    int* queue;
+    unsigned long long budget_ns;   // wall-clock cap of one pad's frame solve
+};
+
+}  // namespace tac

@@ -1,0 +1,252 @@
+"""Thin Python binding of the C ABI in include/tac.h (ctypes + torch tensors).
+
+Only argument marshalling lives here: every step of the solve runs in the
+CUDA kernels of ``libtac.so``. Device memory and streams come from PyTorch.
+Importing this module without a built library raises immediately, and every
+call needs a CUDA device; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtac.so")
+
+TAC_OK = 0
+PAD_STATUS = {0: "converged", 1: "maxiter", 2: "nonfinite", 3: "linesearch", 4: "pair_overflow"}
+
+SYMBOLS = ("tac_create_batch", "tac_destroy_batch", "tac_reset", "tac_set_indenter", "tac_step", "tac_markers",
+           "tac_get_state", "tac_set_state", "tac_set_params", "tac_broadphase", "tac_debug_eval", "tac_stats",
+           "tac_sizes", "tac_last_error")
+
+
+class PadDesc(ctypes.Structure):
+    _fields_ = [("n_verts", ctypes.c_int), ("n_tets", ctypes.c_int), ("n_fixed", ctypes.c_int),
+                ("n_markers", ctypes.c_int), ("rest_xyz", ctypes.c_void_p), ("tets", ctypes.c_void_p),
+                ("fixed_idx", ctypes.c_void_p), ("marker_xy", ctypes.c_void_p)]
+
+
+class IndenterDesc(ctypes.Structure):
+    _fields_ = [("n_verts", ctypes.c_int), ("n_tris", ctypes.c_int), ("verts", ctypes.c_void_p),
+                ("tris", ctypes.c_void_p)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_float), ("nu", ctypes.c_float), ("rho", ctypes.c_float), ("h", ctypes.c_float),
+                ("dhat", ctypes.c_float), ("kappa", ctypes.c_float), ("mu_f", ctypes.c_float),
+                ("eps_v", ctypes.c_float), ("tol_rel_grad", ctypes.c_float), ("tol_advance", ctypes.c_float),
+                ("max_iter", ctypes.c_int), ("precond_mode", ctypes.c_int)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("pair_capacity", ctypes.c_int), ("share_meshes", ctypes.c_int)]
+
+
+def load_library(path=_LIB_PATH):
+    """Load libtac.so and declare the C signatures."""
+    if not os.path.exists(path):
+        raise ImportError(f"libtac.so not built ({path}); run python -m paper_2603_28475_b300.build")
+    lib = ctypes.CDLL(path)
+    vp, i, f, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_double
+    sig = {
+        "tac_create_batch": [ctypes.POINTER(PadDesc), ctypes.POINTER(Params), i, ctypes.POINTER(IndenterDesc), i, i,
+                             ctypes.POINTER(Options), vp, ctypes.POINTER(vp)],
+        "tac_destroy_batch": [vp],
+        "tac_reset": [vp, vp, vp],
+        "tac_set_indenter": [vp, vp, vp, vp],
+        "tac_step": [vp, vp, vp, vp],
+        "tac_markers": [vp, vp, vp],
+        "tac_get_state": [vp, vp, vp, vp],
+        "tac_set_state": [vp, vp, vp, vp],
+        "tac_set_params": [vp, ctypes.POINTER(Params), i],
+        "tac_broadphase": [vp, i, vp, vp, d, vp, i, vp, vp],
+        "tac_debug_eval": [vp, vp, vp, f, vp, vp, vp, vp],
+        "tac_stats": [vp, vp, vp],
+        "tac_sizes": [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.tac_last_error.argtypes = []
+    lib.tac_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+class TacError(RuntimeError):
+    pass
+
+
+def _check(rc):
+    if rc != TAC_OK:
+        raise TacError(f"tac error {rc}: {lib().tac_last_error().decode()}")
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_params(mat, tol=1e-6, tol_advance=1e-2, max_iter=10000, precond=0, kappa=0.0, eps_v=0.0):
+    return Params(E=mat.E, nu=mat.nu, rho=mat.rho, h=mat.h, dhat=mat.dhat, kappa=kappa, mu_f=mat.mu_f,
+                  eps_v=eps_v, tol_rel_grad=tol, tol_advance=tol_advance, max_iter=max_iter, precond_mode=precond)
+
+
+class TacBatch:
+    """A batch of gel pads on the current CUDA device.
+
+    ``pads``: list of objects with rest/tets/fixed/markers arrays (one per
+    pad; pads that share the same numpy arrays share device mesh data);
+    ``params``: list of ``Params``; ``indenters``: list of objects with
+    verts/tris (one per environment)."""
+
+    def __init__(self, pads, params, indenters, pads_per_env=1, pair_capacity=0, share_meshes=True, stream=None):
+        if not torch.cuda.is_available():
+            raise TacError("TacBatch needs a CUDA device")
+        self._keep = []
+        n = len(pads)
+        pd = (PadDesc * n)()
+        for k, p in enumerate(pads):
+            rest = np.ascontiguousarray(p.rest, dtype=np.float32)
+            tets = np.ascontiguousarray(p.tets, dtype=np.int32)
+            fixed = np.ascontiguousarray(p.fixed, dtype=np.int32)
+            mk = np.ascontiguousarray(p.markers, dtype=np.float32)
+            # keep identical host arrays identical so that the library can share them
+            key = id(p)
+            cached = getattr(p, "_tac_cache", None)
+            if cached is None:
+                cached = (rest, tets, fixed, mk)
+                try:
+                    p._tac_cache = cached
+                except AttributeError:
+                    self._keep.append(cached)
+            rest, tets, fixed, mk = cached
+            self._keep.append(cached)
+            pd[k] = PadDesc(rest.shape[0], tets.shape[0], fixed.shape[0], mk.shape[0], rest.ctypes.data,
+                            tets.ctypes.data, fixed.ctypes.data if fixed.size else 0, mk.ctypes.data if mk.size else 0)
+            del key
+        ne = len(indenters)
+        idesc = (IndenterDesc * ne)()
+        for e, ind in enumerate(indenters):
+            cached = getattr(ind, "_tac_cache", None)
+            if cached is None:
+                cached = (np.ascontiguousarray(ind.verts, dtype=np.float32), np.ascontiguousarray(ind.tris, dtype=np.int32))
+                try:
+                    ind._tac_cache = cached
+                except AttributeError:
+                    pass
+            self._keep.append(cached)
+            idesc[e] = IndenterDesc(cached[0].shape[0], cached[1].shape[0], cached[0].ctypes.data, cached[1].ctypes.data)
+        prm = (Params * n)(*params)
+        opts = Options(pair_capacity, 1 if share_meshes else 0)
+        h = ctypes.c_void_p()
+        _check(lib().tac_create_batch(pd, prm, n, idesc, ne, pads_per_env, ctypes.byref(opts), _stream(stream),
+                                      ctypes.byref(h)))
+        self._h = h
+        self.n_pads = n
+        tv, tm, cap = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().tac_sizes(h, ctypes.byref(tv), ctypes.byref(tm), ctypes.byref(cap)))
+        self.total_verts, self.total_markers, self.pair_capacity = tv.value, tm.value, cap.value
+        self.vert_offsets = np.cumsum([0] + [int(np.asarray(p.rest).shape[0]) for p in pads])
+        self.marker_offsets = np.cumsum([0] + [int(np.asarray(p.markers).shape[0]) for p in pads])
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tac_destroy_batch(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _f32(self, a):
+        t = torch.as_tensor(a, dtype=torch.float32, device=self.device)
+        return t.contiguous()
+
+    def reset(self, poses, stream=None):
+        p = self._f32(poses).reshape(self.n_pads, 6)
+        _check(lib().tac_reset(self._h, _ptr(p), _stream(stream)))
+        self._hold = p
+
+    def set_indenter(self, poses=None, twists=None, stream=None):
+        p = self._f32(poses).reshape(self.n_pads, 6) if poses is not None else None
+        w = self._f32(twists).reshape(self.n_pads, 6) if twists is not None else None
+        _check(lib().tac_set_indenter(self._h, _ptr(p), _ptr(w), _stream(stream)))
+        self._hold = (p, w)
+
+    def step(self, status=None, iters=None, stream=None):
+        status = status if status is not None else torch.empty(self.n_pads, dtype=torch.int32, device=self.device)
+        iters = iters if iters is not None else torch.empty(self.n_pads, dtype=torch.int32, device=self.device)
+        _check(lib().tac_step(self._h, _ptr(status), _ptr(iters), _stream(stream)))
+        return status, iters
+
+    def markers(self, out=None, stream=None):
+        out = out if out is not None else torch.empty(self.total_markers, 2, dtype=torch.float32, device=self.device)
+        _check(lib().tac_markers(self._h, _ptr(out), _stream(stream)))
+        return out
+
+    def get_state(self, stream=None):
+        x = torch.empty(self.total_verts, 3, dtype=torch.float32, device=self.device)
+        v = torch.empty_like(x)
+        _check(lib().tac_get_state(self._h, _ptr(x), _ptr(v), _stream(stream)))
+        return x, v
+
+    def set_state(self, x, v, stream=None):
+        x, v = self._f32(x).reshape(-1, 3), self._f32(v).reshape(-1, 3)
+        _check(lib().tac_set_state(self._h, _ptr(x), _ptr(v), _stream(stream)))
+        self._hold = (x, v)
+
+    def set_params(self, params):
+        prm = (Params * self.n_pads)(*params)
+        _check(lib().tac_set_params(self._h, prm, self.n_pads))
+
+    def broadphase(self, pad, x, y, r, capacity=1 << 16, stream=None):
+        x, y = self._f32(x).reshape(-1, 3), self._f32(y).reshape(-1, 3)
+        out = torch.zeros(capacity, 3, dtype=torch.int32, device=self.device)
+        cnt = torch.zeros(1, dtype=torch.int32, device=self.device)
+        _check(lib().tac_broadphase(self._h, pad, _ptr(x), _ptr(y), float(r), _ptr(out), capacity, _ptr(cnt),
+                                    _stream(stream)))
+        n = int(cnt.item())
+        return out[:min(n, capacity)], n
+
+    def debug_eval(self, u, p, alpha, stream=None):
+        u, p = self._f32(u).reshape(-1, 3), self._f32(p).reshape(-1, 3)
+        g = torch.empty(self.total_verts, 3, dtype=torch.float32, device=self.device)
+        k = torch.empty(self.total_verts, 6, dtype=torch.float32, device=self.device)
+        sc = torch.empty(self.n_pads, 8, dtype=torch.float64, device=self.device)
+        _check(lib().tac_debug_eval(self._h, _ptr(u), _ptr(p), float(alpha), _ptr(g), _ptr(k), _ptr(sc),
+                                    _stream(stream)))
+        return g, k, sc
+
+    def stats(self, stream=None):
+        out = torch.empty(self.n_pads, 8, dtype=torch.int64, device=self.device)
+        _check(lib().tac_stats(self._h, _ptr(out), _stream(stream)))
+        return out
+
+
+def batch_from_workload(w, tol=1e-6, tol_advance=1e-2, max_iter=10000, precond=0, pair_capacity=0,
+                        share_meshes=True, stream=None):
+    params = [make_params(m, tol=tol, tol_advance=tol_advance, max_iter=max_iter, precond=precond)
+              for m in w.materials]
+    return TacBatch(w.pads, params, w.indenters, w.pads_per_env, pair_capacity=pair_capacity,
+                    share_meshes=share_meshes, stream=stream)
