@@ -1,0 +1,367 @@
+"""Benchmark: converged tactile env-frames per second of the batched PNCG-IPC
+frame solve, with the roofline of the solve kernel and the FP64 oracle timed
+on the host cores beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--envs E] [--impl ours|reference]
+
+Workload (the batched RL step): E environments x 2 gel pads, each env's pads
+drawn from the 2k / 5k / 10k-vertex size classes, a cylinder peg per env
+(r ~ U[2, 4] mm) pressed into each pad at 0.05 mm per frame from a dhat gap
+with a random pose (+-15 deg, +-1 mm) up to a depth ~ U[0, 1.2] mm, friction
+0.5. One step = one frame for every pad: set the target poses, solve
+(tac_step), read the markers. W warm-up frames, then K timed frames.
+Under torchrun every rank solves its own E environments (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "converged tactile frames/s (PNCG-IPC) at 4096 envs; % of HBM roofline"
+UNIT = "env-frames/s"
+
+# algorithmic bytes per unit of work of the solve kernel:
+# a tet pass reads each tet's Dm^-1 (36 B), local connectivity (4 B) and
+# corner slots (8 B) once, and per patch vertex the displacement (hi, lo) and
+# the direction (36 B) and, averaged over the two pass kinds, writes the
+# gradient and diagonal block (36 B / 2); a vertex pass moves ~120 B per
+# vertex; a pair evaluation ~64 B per candidate pair.
+B_TET = 48.0
+B_TET_VERT = 36.0 + 18.0
+B_VERT_PASS = 120.0
+B_PAIR = 64.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--envs", type=int, default=4096)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--pair-capacity", type=int, default=8192)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- helpers
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(envs, frames, seed):
+    from paper_2603_28475_b300 import scenes as S
+    return S.config_batched(n_envs=envs, frames=frames, seed=seed)
+
+
+def algorithmic_bytes(stats, w):
+    """Counted bytes of one solve launch from the per-pad counters."""
+    tot = 0.0
+    for k, pad in enumerate(w.pads):
+        it, sub, reb, hal, tp, vp, pe, peak = [float(v) for v in stats[k]]
+        tot += tp * (B_TET * pad.n_tets + B_TET_VERT * pad.n_verts) + vp * B_VERT_PASS * pad.n_verts + pe * B_PAIR
+    return tot
+
+
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "device_math.cuh", "solve.cuh"):
+        with open(os.path.join(ROOT, "paper_2603_28475_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(bytes_alg_per_launch):
+    """DRAM bytes per launch from the committed ncu summary, scaled from the
+    captured case by the counted bytes, or None when the kernel changed."""
+    path = os.path.join(ROOT, "profiles", "solve_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    if rec.get("kernel_hash") != kernel_hash():
+        return None
+    ratio = float(rec["dram_bytes"]) / float(rec["algorithmic_bytes"])
+    return ratio * bytes_alg_per_launch
+
+
+# --------------------------------------------------------------------------- oracle sample
+
+def class_mean_tets():
+    """Expected tet count of a pad when classes are drawn uniformly."""
+    from paper_2603_28475_b300 import scenes as S
+    return float(np.mean([6 * a * b * c for a, b, c in S.SIZE_CLASSES.values()]))
+
+
+def oracle_sample(w, frame_pose_idx=1):
+    """The oracle as it stands on one pad of the smallest size class for one
+    frame (contact from rest). Returns (seconds, pad index, scale) where scale
+    converts one such pad-frame into one average env-frame of the workload
+    (2 pads, tet count averaged over the workload's pads)."""
+    from threadpoolctl import threadpool_limits
+    from oracle import geometry as G
+    from oracle import solver as SV
+    f32 = lambda v: float(np.float32(v))
+    k = int(np.argmin([p.n_tets for p in w.pads]))
+    pd, m = w.pads[k], w.materials[k]
+    pad = G.build_pad(pd.rest, pd.tets, pd.fixed, pd.markers, f32(m.E), f32(m.nu), f32(m.rho), f32(m.h),
+                      f32(m.dhat), f32(m.mu_f))
+    e = k // w.pads_per_env
+    ind = G.build_indenter(w.indenters[e].verts, w.indenters[e].tris)
+    st = SV.rest_state(pad, w.poses[0, k].astype(np.float64))
+    with threadpool_limits(1):
+        t = time.perf_counter()
+        st, info = SV.solve_frame(pad, ind, st, w.poses[frame_pose_idx, k].astype(np.float64))
+        dt = time.perf_counter() - t
+    scale = w.pads_per_env * class_mean_tets() / pd.n_tets
+    return dt, k, scale, info
+
+
+# --------------------------------------------------------------------------- arms
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = workload(min(args.envs, 8), 2, args.seed)
+    times = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        dt, k, scale, info = oracle_sample(w)
+        if i >= args.warmup:
+            times.append(dt * scale)
+    t_env = float(np.mean(times))
+    value = 1.0 / t_env
+    sample = (f"oracle (numpy FP64, 1 thread) on one {w.pads[k].n_verts}-vert pad for its first contact frame "
+              f"({info.iters} iterations), scaled by {scale:.2f} to one average env-frame of the workload "
+              "(2 pads, mean tet count of the size classes)")
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_env * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": f"batched_{args.envs}env_x2pads", "envs": args.envs},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2603_28475_b300 import tac
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    frames = args.warmup + args.steps
+    w = workload(args.envs, 2 * frames + 1, args.seed + 1000 * rank)
+    n_pads = w.n_pads
+    t0 = time.time()
+    b = tac.batch_from_workload(w, pair_capacity=args.pair_capacity)
+    t_create = time.time() - t0
+    stream = torch.cuda.current_stream()
+    poses = torch.tensor(w.poses, dtype=torch.float32, device=dev)      # [F+1, n_pads, 6]
+    b.reset(poses[0])
+    status = torch.empty(n_pads, dtype=torch.int32, device=dev)
+    iters = torch.empty(n_pads, dtype=torch.int32, device=dev)
+    mk = torch.empty(b.total_markers, 2, dtype=torch.float32, device=dev)
+    for f in range(1, args.warmup + 1):
+        b.set_indenter(poses[f])
+        b.step(status, iters)
+        b.markers(mk)
+    torch.cuda.synchronize()
+    # timed frames: inputs resident in HBM
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    conv, iter_hist, stats_all = 0, [], []
+    bytes_alg = 0.0
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for s in range(args.steps):
+            f = args.warmup + 1 + s
+            b.set_indenter(poses[f])
+            ev[s][0].record(stream)
+            b.step(status, iters)
+            ev[s][1].record(stream)
+            b.markers(mk)
+            st = b.stats()
+            stats_all.append((status.clone(), iters.clone(), st))
+        stop.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = start.elapsed_time(stop)
+    solve_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    for stt, it, st in stats_all:
+        s_np = stt.cpu().numpy().reshape(-1, w.pads_per_env)
+        conv += int(np.all(s_np == 0, axis=1).sum())
+        iter_hist.append(it.cpu().numpy())
+        bytes_alg += algorithmic_bytes(st.cpu().numpy(), w)
+    if world > 1:
+        t = torch.tensor([total_ms, float(conv)], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+        sm = t.clone()
+        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+        total_ms_job, conv_job = float(mx[0]), float(sm[1])
+    else:
+        total_ms_job, conv_job = total_ms, float(conv)
+    value = conv_job / (total_ms_job / 1e3)
+    its = np.concatenate(iter_hist)
+    bytes_per_launch = bytes_alg / args.steps
+    launch_ms = float(np.mean(solve_ms))
+    peak, peak_kind = load_peaks()
+    achieved = bytes_per_launch / (launch_ms / 1e3) / 1e9
+    traffic = committed_traffic(bytes_per_launch)
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_poses = poses.cpu().pin_memory()
+        host_mk = torch.empty(b.total_markers, 2, dtype=torch.float32).pin_memory()
+        host_st = torch.empty(n_pads, dtype=torch.int32).pin_memory()
+        dev_pose = torch.empty(n_pads, 6, dtype=torch.float32, device=dev)
+        n_e2e = args.steps
+        conv_e = 0
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for s in range(n_e2e):
+            f = args.warmup + args.steps + 1 + s
+            dev_pose.copy_(host_poses[f], non_blocking=True)
+            b.set_indenter(dev_pose)
+            b.step(status, iters)
+            b.markers(mk)
+            host_mk.copy_(mk, non_blocking=True)
+            host_st.copy_(status, non_blocking=True)
+            torch.cuda.synchronize()
+            conv_e += int(np.all(host_st.numpy().reshape(-1, w.pads_per_env) == 0, axis=1).sum())
+        dt_e = time.perf_counter() - t1
+        e2e = {"value": conv_e / dt_e * world, "unit": UNIT, "h2d_bytes_per_step": n_pads * 6 * 4,
+               "d2h_bytes_per_step": b.total_markers * 2 * 4 + n_pads * 4}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        dt, k, scale, info = oracle_sample(w)
+        cpu = {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"oracle (numpy FP64, 1 thread) on one {w.pads[k].n_verts}-vert pad, first contact frame "
+                         f"({info.iters} iterations, {dt:.1f} s), scaled by {scale:.2f} to an average env-frame "
+                         "(2 pads, mean tet count of the workload)"}
+    if rank == 0:
+        v_state = b.total_verts * 168 / 1e9
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": total_ms_job / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32 (double-float displacements; f64 pair distance, barrier, CCD and reductions)",
+               "data": "synthetic",
+               "config": {"workload": f"batched_{args.envs}env_x2pads", "envs": args.envs, "pads": n_pads,
+                          "pads_per_env": 2, "size_classes_verts": [2070, 4830, 9918],
+                          "total_verts": b.total_verts, "total_tets": int(sum(p.n_tets for p in w.pads)),
+                          "frames": f"{args.warmup + 1}..{args.warmup + args.steps} of a 0.05 mm/frame press",
+                          "tol_rel_grad": 1e-6, "friction": 0.5,
+                          "l2": f"inputs larger than L2 (solver state {v_state:.1f} GB)",
+                          "parallelism": f"{world} rank(s), env-sharded"},
+               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                            "kernel": "tac::solve_kernel", "bytes_per_launch": bytes_per_launch,
+                            "launch_ms": launch_ms},
+               "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
+               "clocks": clk.summary(),
+               "converged_fraction": conv_job / (args.steps * args.envs * world),
+               "iters_per_pad_frame": {"p50": float(np.percentile(its, 50)), "p99": float(np.percentile(its, 99)),
+                                       "max": int(its.max())},
+               "frame_ms": {"p50": float(np.percentile(solve_ms, 50)), "p99": float(np.percentile(solve_ms, 99))},
+               "setup_s": t_create}
+        print(json.dumps(out), flush=True)
+    b.close()
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    run_ours(args, rank, world)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

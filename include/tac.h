@@ -87,7 +87,9 @@ typedef struct {
  *  kappa          barrier stiffness; <= 0 selects h^2 * E * (mean surface edge)
  *  mu_f, eps_v    friction coefficient and mollifier width [m]; eps_v <= 0
  *                 selects 1e-3 m/s * h
- *  tol_rel_grad   stop when max |g_i| <= tol_rel_grad * kappa * dhat
+ *  tol_rel_grad   stop when max |g_i| <= tol_rel_grad * h^2 * E * (mean
+ *                 surface edge) * dhat (the elastic gradient of a
+ *                 dhat-sized displacement over one element)
  *  tol_advance    looser tolerance of the intermediate indenter substeps
  *  max_iter       PNCG iteration cap per frame
  *  precond_mode   0 = 3x3 block Jacobi, 1 = scalar Jacobi diag(H)^-1 */

@@ -138,11 +138,12 @@ class IndenterModel:
     edges: np.ndarray
 
 
-def build_pad(rest, tets, fixed, markers_xy, E, nu, rho, h, dhat, mu_f):
-    """Precompute a pad. Conventions: kappa = h^2 E l-bar (barrier
-    stiffness), eps_v = 1e-3 m/s * h (friction mollifier width, a
-    displacement), g_ref = kappa * dhat (gradient scale of the stopping
-    rule)."""
+def build_pad(rest, tets, fixed, markers_xy, E, nu, rho, h, dhat, mu_f, kappa=None, eps_v=None):
+    """Precompute a pad. Conventions: kappa (barrier stiffness) defaults to
+    KAPPA_SCALE * h^2 E l-bar, eps_v (friction mollifier width, a
+    displacement) to 1e-3 m/s * h, and the gradient scale of the stopping
+    rule is g_ref = h^2 E l-bar dhat (the elastic gradient of a dhat-sized
+    displacement over one element)."""
     rest = np.asarray(rest, dtype=np.float64)
     tets = np.asarray(tets, dtype=np.int64)
     Dm_inv, vol = rest_shape(rest, tets)
@@ -155,11 +156,17 @@ def build_pad(rest, tets, fixed, markers_xy, E, nu, rho, h, dhat, mu_f):
     mids, mw = marker_map(rest, st, markers_xy)
     mu, lam = lame(E, nu)
     lbar = mean_surface_edge(rest, se)
-    kappa = h * h * E * lbar
+    if kappa is None or kappa <= 0:
+        kappa = KAPPA_SCALE * h * h * E * lbar
+    if eps_v is None or eps_v <= 0:
+        eps_v = 1e-3 * h
     return PadModel(rest=rest, tets=tets, Dm_inv=Dm_inv, vol=vol, mass=mass, free=free,
                     surf_tris=st, surf_edges=se, surf_verts=sv, marker_ids=mids, marker_w=mw,
                     mu=mu, lam=lam, rho=rho, h=h, dhat=dhat, kappa=kappa, mu_f=mu_f,
-                    eps_v=1e-3 * h, g_ref=kappa * dhat, lbar=lbar)
+                    eps_v=eps_v, g_ref=h * h * E * lbar * dhat, lbar=lbar)
+
+
+KAPPA_SCALE = 1.0
 
 
 def build_indenter(verts, tris):

@@ -24,7 +24,11 @@ with the step rule of Eq. (step_size). Readings where the paper is silent:
     last build would exceed the margin m (= dhat), so pairs outside the set
     stay farther than dhat;
   * friction lag (lambda_n, normal, closest-point weights) from x^t with the
-    indenter at y^t, once per frame.
+    indenter at y^t, once per frame;
+  * initial guess: x^t + a0 (xhat - x^t) with a0 = min(1, alpha_ccd,
+    m / max_i |xhat_i - x^t_i|) against the candidates at (x^t, y^t),
+    halved while a tet would invert (the inertial prediction of Eq. varopt,
+    made collision-free).
 """
 from __future__ import annotations
 
@@ -110,6 +114,23 @@ def dk_beta(g_new, yv, p, P_new):
         return 0.0
     Py = apply_P(P_new, yv)
     return float(np.sum(g_new * Py)) / yp - (float(np.sum(yv * Py)) / yp) * (float(np.sum(p * g_new)) / yp)
+
+
+def predictor(fr, x_t, xhat, pairs, eta, margin, max_halvings=20):
+    """Collision-free, inversion-free start of the frame on the segment from
+    x^t to xhat (see the module docstring)."""
+    p0 = xhat - x_t
+    p0[~fr.pad.free] = 0.0
+    pn = vnorm_max(p0)
+    if pn == 0.0:
+        return x_t.copy()
+    a0 = min(1.0, ccd_bound(fr, x_t, p0, 0.0, pairs, eta), margin / pn)
+    for _ in range(max_halvings + 1):
+        F = En.deformation_gradient(x_t + a0 * p0, fr.pad)
+        if np.all(np.linalg.det(F) > 0):
+            return x_t + a0 * p0
+        a0 *= 0.5
+    return x_t.copy()
 
 
 def min_distance(fr, x, s, pairs):
@@ -206,7 +227,10 @@ def solve_frame(pad, ind, state, pose_next, prm=Params(), trace=None):
     fr = En.Frame(pad, ind, x_t, xhat, y_t, y_n, lag)
     Dy = float(np.sqrt(((y_n - y_t) ** 2).sum(axis=1)).max())
     free = pad.free
-    x = x_t.copy()
+    x = predictor(fr, x_t, xhat, cand, prm.eta, margin)
+    if not np.array_equal(x, x_t):
+        cand = BP.candidates(x, y_t, pad, ind, r_inf)
+        info.rebuilds += 1
     s, M = 0.0, 0.0
     info.min_gap = min_distance(fr, x, s, cand)
     tol_abs = prm.tol * pad.g_ref

@@ -176,7 +176,7 @@ void fill_pad_params(tac_batch* b, int p) {
     P.kappa = q.kappa > 0 ? q.kappa : (float)((double)q.h * q.h * q.E * M.lbar);
     P.mu_f = q.mu_f;
     P.eps_v = q.eps_v > 0 ? q.eps_v : (float)(1e-3 * q.h);
-    P.g_ref = (float)((double)P.kappa * q.dhat);
+    P.g_ref = (float)((double)q.h * q.h * q.E * M.lbar * q.dhat);
     P.tol = q.tol_rel_grad;
     P.tol_adv = q.tol_advance;
     P.max_iter = q.max_iter;

@@ -1120,6 +1120,48 @@ __device__ DirOut direction(const Dev& D, const PadDev& P, const MeshDev& M, flo
     return DirOut{v[0], v[1], pn[0]};
 }
 
+// p = xhat - x^t = h v (zero on Dirichlet vertices); returns max_i |p_i|
+__device__ float predictor_direction(const Dev& D, const PadDev& P, const MeshDev& M, Shared& S) {
+    float pn[1] = {0.f};
+    for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
+        int si = P.v_off + i;
+        bool fx = D.fixed[M.xv_off + i] != 0;
+        float n2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            int sc = c * D.Vt + si;
+            float v = fx ? 0.f : P.h * D.vel[sc];
+            D.p[sc] = v;
+            n2 += v * v;
+        }
+        pn[0] = fmaxf(pn[0], sqrtf(n2));
+    }
+    block_max_f<1>(pn, S);
+    return pn[0];
+}
+
+// u += alpha p (double-float), p untouched
+__device__ void move_state(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, Shared& S) {
+    for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
+        int si = P.v_off + i;
+        if (D.fixed[M.xv_off + i]) continue;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            int sc = c * D.Vt + si;
+            float t = alpha * D.p[sc];
+            float hi = D.uh[sc], lo = D.ul[sc];
+            float s = hi + t;
+            float bb = s - hi;
+            float err = (hi - (s - bb)) + (t - bb);
+            lo += err;
+            float nh = s + lo;
+            D.ul[sc] = lo - (nh - s);
+            D.uh[sc] = nh;
+        }
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // frame setup: indenter world vertices, u0 = u, uhat = u + h v
 
@@ -1214,6 +1256,31 @@ __device__ void solve_pad(const Dev& D, int pad, Shared& S) {
     if (status == ST_CONVERGED) {
         cc.nlag = lag_build(D, P, M, E, cc.npairs, S);
         csr_build(D, P, M, E, cc, S);
+        // initial guess on the segment x^t -> xhat: collision-free by the
+        // per-pair bound, inside the broad-phase margin, no inverted tet
+        float pn0 = predictor_direction(D, P, M, S);
+        if (pn0 > 0.f) {
+            double php_d, accd;
+            pair_php(D, P, M, E, cc.npairs, 0, 0.0, php_d, accd, S);
+            ctr.pair_evals += cc.npairs;
+            double a0 = fmin(1.0, fmin(accd, margin / (double)pn0));
+            for (int k = 0; k <= kMaxHalvings; ++k) {
+                TetOut t = tet_pass<1>(D, P, M, (float)a0, 0, S);
+                ctr.tet_passes++;
+                if (!t.bad) break;
+                a0 = (k == kMaxHalvings) ? 0.0 : 0.5 * a0;
+            }
+            if (a0 > 0.0) {
+                move_state(D, P, M, (float)a0, S);
+                SrcState src{&D, &P, &M, 0.0f};
+                int n = bp_build(src, D, M, E, il, rbp, pairs, P.pair_cap, S);
+                ctr.rebuilds++;
+                ctr.peak_pairs = max(ctr.peak_pairs, (long long)n);
+                if (n > P.pair_cap) status = ST_OVERFLOW;
+                cc.npairs = min(n, P.pair_cap);
+                if (status == ST_CONVERGED) csr_build(D, P, M, E, cc, S);
+            }
+        }
     }
     const float tol_abs = P.tol * P.g_ref;
     const float tol_sub = fmaxf(P.tol, P.tol_adv) * P.g_ref;

@@ -303,6 +303,54 @@ def lowest_z(verts, rotvec):
     return float((verts.astype(np.float64) @ R.T)[:, 2].min())
 
 
+def _box_dist(P, size):
+    d = np.maximum(np.maximum(-P, P - np.asarray(size, dtype=np.float64)), 0.0)
+    return np.sqrt(np.einsum("...c,...c->...", d, d))
+
+
+def place_above_box(verts, rotvec, xy, size, gap, tris=None, n=4):
+    """Height z of the translation (xy[0], xy[1], z) that puts the rotated
+    indenter at minimum distance ``gap`` from the solid pad box
+    [0, Lx] x [0, Ly] x [0, Lz] (scene placement only).
+
+    Vertices alone fix a first height by bisection. With ``tris`` given,
+    points sampled on the triangles that can reach the box (a triangle's
+    points are within its diameter of its vertices) then raise it until the
+    sampled surface is ``gap`` away."""
+    R = _rotation(np.asarray(rotvec, dtype=np.float64))
+    V = np.asarray(verts, dtype=np.float64) @ R.T
+    V[:, 0] += xy[0]
+    V[:, 1] += xy[1]
+    over = (V[:, 0] > 0) & (V[:, 0] < size[0]) & (V[:, 1] > 0) & (V[:, 1] < size[1])
+    if not np.any(over):
+        raise ValueError("no indenter vertex lies over the pad")
+    lo = 0.5 * size[2] - V[over, 2].min()   # a vertex inside the box: distance 0
+    hi = size[2] - V[:, 2].min() + gap      # every vertex above the top: distance >= gap
+    for _ in range(44):
+        mid = 0.5 * (lo + hi)
+        if _box_dist(V + np.array([0.0, 0.0, mid]), size).min() < gap:
+            lo = mid
+        else:
+            hi = mid
+    z = hi
+    if tris is None:
+        return z
+    T = np.asarray(tris, dtype=np.int64)
+    dv = _box_dist(V + np.array([0.0, 0.0, z]), size)[T]              # [K, 3]
+    e = V[T]
+    diam = np.max(np.linalg.norm(e[:, [1, 2, 0]] - e, axis=2), axis=1)
+    near = dv.min(axis=1) < gap + diam
+    ij = [(i, j) for i in range(n + 1) for j in range(n + 1 - i)]
+    w = np.array([(1 - (i + j) / n, i / n, j / n) for i, j in ij])
+    Ps = np.einsum("sk,tkc->tsc", w, e[near]).reshape(-1, 3)
+    for _ in range(50):
+        dm = _box_dist(Ps + np.array([0.0, 0.0, z]), size).min()
+        if dm >= gap * (1.0 - 1e-6):
+            break
+        z += gap - dm            # the distance grows at most as fast as z
+    return z
+
+
 def _rotation(rv):
     th = float(np.linalg.norm(rv))
     if th < 1e-300:
@@ -416,7 +464,8 @@ def config_batched(n_envs=4096, frames=12, seed=0, step=0.05 * MM, classes=(2000
     """``n_envs`` environments x 2 pads. Per env: size class drawn uniformly,
     cylinder peg r ~ U[2, 4] mm (64 x 8 side quads). Per pad: rotation vector
     components ~ U(+-15 deg), xy offset ~ U(+-1 mm), press depth
-    ~ U[0, 1.2] mm reached at ``step`` per frame from a d-hat gap, then held."""
+    ~ U[0, 1.2] mm reached at ``step`` per frame from a d-hat gap to the pad
+    (the indenter surface starts dhat from the solid pad box), then held."""
     rng = np.random.default_rng(np.random.PCG64(20260 + 3000 + seed))
     pads, mats, inds = [], [], []
     n_pads = 2 * n_envs
@@ -439,9 +488,10 @@ def config_batched(n_envs=4096, frames=12, seed=0, step=0.05 * MM, classes=(2000
             off = rng.uniform(-1 * MM, 1 * MM, size=2)
             depth = float(rng.uniform(0, 1.2 * MM))
             lx, ly, lz = pad.size
-            z0 = lz + DHAT - lowest_z(ind.verts, rot)
+            cx, cy = lx / 2 + off[0], ly / 2 + off[1]
+            z0 = place_above_box(ind.verts, rot, (cx, cy), pad.size, DHAT, ind.tris)
             poses[:, i, :3] = rot
-            poses[:, i, 3] = lx / 2 + off[0]
-            poses[:, i, 4] = ly / 2 + off[1]
+            poses[:, i, 3] = cx
+            poses[:, i, 4] = cy
             poses[:, i, 5] = z0 - np.minimum(step * np.arange(frames + 1), depth + DHAT)
     return Workload(f"batched_{n_envs}env_x2pads", pads, mats, inds, 2, poses.astype(np.float32))
