@@ -87,9 +87,10 @@ typedef struct {
  *  kappa          barrier stiffness; <= 0 selects h^2 * E * (mean surface edge)
  *  mu_f, eps_v    friction coefficient and mollifier width [m]; eps_v <= 0
  *                 selects 1e-3 m/s * h
- *  tol_rel_grad   stop when max |g_i| <= tol_rel_grad * h^2 * E * (mean
- *                 surface edge) * dhat (the elastic gradient of a
- *                 dhat-sized displacement over one element)
+ *  tol_rel_grad   stop when max |g_i| <= tol_rel_grad * g_ref with
+ *                 g_ref = max(h^2 E (mean surface edge) dhat, max |g_i| at
+ *                 the frame's first evaluation after the first indenter
+ *                 substep); see tac_pad_norms for the float32 floor
  *  tol_advance    looser tolerance of the intermediate indenter substeps
  *  max_iter       PNCG iteration cap per frame
  *  precond_mode   0 = 3x3 block Jacobi, 1 = scalar Jacobi diag(H)^-1 */
@@ -186,6 +187,13 @@ int tac_debug_eval(tac_handle h, const float* u_dev, const float* p_dev, float a
  * iterations, substeps, broad-phase rebuilds, Armijo halvings, tet passes,
  * vertex passes, pair evaluations, peak candidate count. */
 int tac_stats(tac_handle h, long long* stats_dev, void* stream);
+
+/* Convergence record of the last tac_step per pad (device [n_pads*4]
+ * double): final max |g_i|, the stopping target, g_ref of the frame, and the
+ * largest per-corner force component F. The target is
+ * max(tol * g_ref, 256 * 2^-24 * F): a float32 gradient is not resolved
+ * below a few hundred ulps of the forces summed into it. */
+int tac_pad_norms(tac_handle h, double* norms_dev, void* stream);
 
 /* Sizes: total vertices, total markers, candidate capacity per pad. */
 int tac_sizes(tac_handle h, int* total_verts, int* total_markers, int* pair_capacity);

@@ -15,7 +15,9 @@ with the step rule of Eq. (step_size). Readings where the paper is silent:
     R(a) = E(x + a p) - E(x) - a g^T p summed element by element;
   * direction restart (beta = 0) when |y^T p| is negligible or the new p
     is not a descent direction;
-  * stopping: max_i |g_i| (free DOFs) <= tol * g_ref, g_ref = kappa * dhat;
+  * stopping: max_i |g_i| (free DOFs) <= tol * g_ref, g_ref = max(h^2 E
+    l-bar dhat, max_i |g_i| at the frame's first evaluation after the first
+    indenter substep);
   * indenter motion: the indenter vertices move on the straight path
     y(s) = (1 - s) y^t + s y^{t+1}; s advances in substeps of at most
     eta * min_k d_k / max_j |y_j^{t+1} - y_j^t| (the gel held fixed), each
@@ -233,8 +235,7 @@ def solve_frame(pad, ind, state, pose_next, prm=Params(), trace=None):
         info.rebuilds += 1
     s, M = 0.0, 0.0
     info.min_gap = min_distance(fr, x, s, cand)
-    tol_abs = prm.tol * pad.g_ref
-    tol_sub = max(prm.tol, prm.tol_advance) * pad.g_ref
+    g_ref = None
     while True:
         if s < 1.0:
             if Dy == 0.0:
@@ -257,7 +258,10 @@ def solve_frame(pad, ind, state, pose_next, prm=Params(), trace=None):
             break
         P = precondition(blk, free, prm.precond)
         p = -apply_P(P, g)
-        target = tol_abs if s >= 1.0 else tol_sub
+        if g_ref is None:
+            g_ref = max(pad.g_ref, float(np.abs(g[free]).max(initial=0.0)))
+            info.g_ref = g_ref
+        target = (prm.tol if s >= 1.0 else max(prm.tol, prm.tol_advance)) * g_ref
         while np.abs(g[free]).max(initial=0.0) > target and info.iters < prm.max_iter:
             pn = vnorm_max(p)
             gTp = float(np.sum(g * p))

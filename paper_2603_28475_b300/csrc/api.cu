@@ -358,6 +358,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     int* cnt = dalloc<int>(K, Vt, rc);
     int* ilist = dalloc<int>(K, il, rc);
     long long* stats = dalloc<long long>(K, 8 * (size_t)n_pads, rc);
+    double* norms = dalloc<double>(K, 4 * (size_t)n_pads, rc);
     int* queue = dalloc<int>(K, 1, rc);
     int* order_d = dalloc<int>(K, n_pads, rc);
     b->d_meshes = dalloc<MeshDev>(K, b->hmesh.size(), rc);
@@ -446,6 +447,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     CUDA_TRY(cudaMemsetAsync(k1, 0, 6 * (size_t)Vt * 4, st));
     CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)Vt * 4, st));
     CUDA_TRY(cudaMemsetAsync(stats, 0, 8 * (size_t)n_pads * 8, st));
+    CUDA_TRY(cudaMemsetAsync(norms, 0, 4 * (size_t)n_pads * 8, st));
     CUDA_TRY(cudaMemsetAsync(b->d_pose_t, 0, 6 * (size_t)n_pads * 4, st));
     CUDA_TRY(cudaMemsetAsync(b->d_pose_n, 0, 6 * (size_t)n_pads * 4, st));
     D.meshes = b->d_meshes;
@@ -460,7 +462,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     D.p = st3[6]; D.z = st3[7];
     D.g[0] = g0; D.g[1] = g1; D.blk[0] = k0; D.blk[1] = k1;
     D.pairs = pairs; D.lag = lag; D.slotbuf = slotbuf; D.ent = ent; D.cvl = cvl; D.cvo = cvo; D.cnt = cnt;
-    D.ilist = ilist; D.stats = stats; D.queue = queue;
+    D.ilist = ilist; D.stats = stats; D.norms = norms; D.queue = queue;
     D.status = nullptr; D.iters = nullptr;
     D.budget_ns = 20ull * 1000000000ull;
     int nsm = 0, occ = 0;
@@ -589,6 +591,13 @@ int tac_debug_eval(tac_handle h, const float* u_dev, const float* p_dev, float a
 int tac_stats(tac_handle h, long long* stats_dev, void* stream) {
     if (!h || !stats_dev) return fail(TAC_ERR_INVALID_ARG, "null argument");
     CUDA_TRY(cudaMemcpyAsync(stats_dev, h->dev.stats, 8 * (size_t)h->n_pads * 8, cudaMemcpyDeviceToDevice,
+                             static_cast<cudaStream_t>(stream)));
+    return TAC_OK;
+}
+
+int tac_pad_norms(tac_handle h, double* norms_dev, void* stream) {
+    if (!h || !norms_dev) return fail(TAC_ERR_INVALID_ARG, "null argument");
+    CUDA_TRY(cudaMemcpyAsync(norms_dev, h->dev.norms, 4 * (size_t)h->n_pads * 8, cudaMemcpyDeviceToDevice,
                              static_cast<cudaStream_t>(stream)));
     return TAC_OK;
 }

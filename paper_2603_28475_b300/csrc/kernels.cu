@@ -26,6 +26,9 @@ constexpr double kArmijoC = 1e-4;
 constexpr int kMaxHalvings = 20;
 constexpr int kMaxSubsteps = 1000;
 constexpr int kWarps = kThreads / 32;
+// a float32 gradient is resolved only down to a few hundred ulps of the
+// largest per-corner force that enters it: 256 * 2^-24
+constexpr float kFloat32Floor = 256.0f / 16777216.0f;
 
 // ---------------------------------------------------------------------------
 // shared memory of one CTA
@@ -275,6 +278,7 @@ __device__ __forceinline__ double pair_distance(const Dev& D, const PadDev& P, c
 struct TetOut {
     double acc;       // p^T H_e p (pass 0) or remainder R' (pass 1)
     int bad;          // trial state inverted a tet
+    float fmax;       // largest per-corner force component (pass 1)
 };
 
 // Loads the patch's local vertices: su = patch-relative displacement at
@@ -299,7 +303,7 @@ __device__ __forceinline__ void load_patch(const Dev& D, const PadDev& P, const 
 // u + alpha p, scattered into g[gb], blk[gb].
 template <int PASS>
 __device__ TetOut tet_pass(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, int gb, Shared& S) {
-    TetOut out{0.0, 0};
+    TetOut out{0.0, 0, 0.f};
     const int tid = threadIdx.x;
     const float mu = P.mu, lam = P.lam, h2 = P.h * P.h;
     for (int pi = 0; pi < M.n_patch; ++pi) {
@@ -388,6 +392,7 @@ __device__ TetOut tet_pass(const Dev& D, const PadDev& P, const MeshDev& M, floa
                     float bb = mu * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
                     float cf = coef;
                     int slot = (int)((sl >> (16 * k)) & 0xffff);
+                    out.fmax = fmaxf(out.fmax, fmaxf(fabsf(fo[0]), fmaxf(fabsf(fo[1]), fabsf(fo[2]))));
                     S.stg[0][slot] = fo[0];
                     S.stg[1][slot] = fo[1];
                     S.stg[2][slot] = fo[2];
@@ -436,6 +441,9 @@ __device__ TetOut tet_pass(const Dev& D, const PadDev& P, const MeshDev& M, floa
     block_sum<2>(v, S);
     out.acc = v[0];
     out.bad = v[1] > 0.0 ? 1 : 0;
+    float fm[1] = {out.fmax};
+    block_max_f<1>(fm, S);
+    out.fmax = fm[0];
     return out;
 }
 
@@ -1282,9 +1290,11 @@ __device__ void solve_pad(const Dev& D, int pad, Shared& S) {
             }
         }
     }
-    const float tol_abs = P.tol * P.g_ref;
-    const float tol_sub = fmaxf(P.tol, P.tol_adv) * P.g_ref;
-    int gc = 0;          // buffer holding the current gradient
+    float g_ref = P.g_ref;   // becomes max(floor, |g| after the first substep)
+    bool have_ref = false;
+    float fmax = 0.f;        // force scale of the float32 resolution floor
+    float target = 0.f;
+    int gc = 0;              // buffer holding the current gradient
     float ginf = 0.f;
     while (status == ST_CONVERGED) {
         if (s < 1.0) {
@@ -1324,9 +1334,15 @@ __device__ void solve_pad(const Dev& D, int pad, Shared& S) {
         ctr.vert_passes++;
         if (to.bad || badp || d0.bad) { status = ST_NONFINITE; break; }
         ginf = d0.ginf;
+        fmax = to.fmax;
+        if (!have_ref) {
+            g_ref = fmaxf(g_ref, ginf);
+            have_ref = true;
+        }
         DirOut dir = direction(D, P, M, 0.0f, false, 0.0, gc, S);
         ctr.vert_passes++;
-        const float target = (s >= 1.0) ? tol_abs : tol_sub;
+        const float rel = (s >= 1.0) ? P.tol : fmaxf(P.tol, P.tol_adv);
+        target = fmaxf(rel * g_ref, kFloat32Floor * fmax);
         while (ginf > target && ctr.iters < P.max_iter) {
             if (over_budget(t0, budget, S)) { status = ST_MAXITER; break; }
             if (dir.pn == 0.f || dir.gTp >= 0.0) {
@@ -1378,6 +1394,7 @@ __device__ void solve_pad(const Dev& D, int pad, Shared& S) {
                     if (dE <= kArmijoC * a * dir.gTp) {
                         accepted = true;
                         alpha = a;
+                        fmax = tt.fmax;
                         break;
                     }
                 }
@@ -1397,6 +1414,7 @@ __device__ void solve_pad(const Dev& D, int pad, Shared& S) {
             }
             gc = gn;
             ginf = dt.ginf;
+            target = fmaxf(rel * g_ref, kFloat32Floor * fmax);
         }
         if (status != ST_CONVERGED) break;
         if (s >= 1.0) {
@@ -1424,6 +1442,8 @@ __device__ void solve_pad(const Dev& D, int pad, Shared& S) {
         long long* st = D.stats + 8 * pad;
         st[0] = ctr.iters; st[1] = ctr.substeps; st[2] = ctr.rebuilds; st[3] = ctr.halvings;
         st[4] = ctr.tet_passes; st[5] = ctr.vert_passes; st[6] = ctr.pair_evals; st[7] = ctr.peak_pairs;
+        double* nr = D.norms + 4 * pad;
+        nr[0] = ginf; nr[1] = target; nr[2] = g_ref; nr[3] = fmax;
     }
     __syncthreads();
 }

@@ -99,6 +99,7 @@ struct Dev {
     int* status;
     int* iters;
     long long* stats;         // [n_pads][8]
+    double* norms;            // [n_pads][4] final |g|_inf, stopping target, g_ref, force scale
     int* queue;
     unsigned long long budget_ns;   // wall-clock cap of one pad's frame solve
 };

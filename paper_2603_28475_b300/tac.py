@@ -20,7 +20,7 @@ PAD_STATUS = {0: "converged", 1: "maxiter", 2: "nonfinite", 3: "linesearch", 4: 
 
 SYMBOLS = ("tac_create_batch", "tac_destroy_batch", "tac_reset", "tac_set_indenter", "tac_step", "tac_markers",
            "tac_get_state", "tac_set_state", "tac_set_params", "tac_broadphase", "tac_debug_eval", "tac_stats",
-           "tac_sizes", "tac_last_error")
+           "tac_pad_norms", "tac_sizes", "tac_last_error")
 
 
 class PadDesc(ctypes.Structure):
@@ -65,6 +65,7 @@ def load_library(path=_LIB_PATH):
         "tac_broadphase": [vp, i, vp, vp, d, vp, i, vp, vp],
         "tac_debug_eval": [vp, vp, vp, f, vp, vp, vp, vp],
         "tac_stats": [vp, vp, vp],
+        "tac_pad_norms": [vp, vp, vp],
         "tac_sizes": [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)],
     }
     for name, args in sig.items():
@@ -237,6 +238,11 @@ class TacBatch:
         _check(lib().tac_debug_eval(self._h, _ptr(u), _ptr(p), float(alpha), _ptr(g), _ptr(k), _ptr(sc),
                                     _stream(stream)))
         return g, k, sc
+
+    def norms(self, stream=None):
+        out = torch.empty(self.n_pads, 4, dtype=torch.float64, device=self.device)
+        _check(lib().tac_pad_norms(self._h, _ptr(out), _stream(stream)))
+        return out
 
     def stats(self, stream=None):
         out = torch.empty(self.n_pads, 8, dtype=torch.int64, device=self.device)
