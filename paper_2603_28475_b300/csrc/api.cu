@@ -14,11 +14,11 @@
 #include "tac.h"
 
 namespace tac {
-__global__ void solve_kernel(Dev D);
-__global__ void debug_eval_kernel(Dev D, float alpha, double r, float* grad_out, float* blk_out, double* scal);
-__global__ void broadphase_kernel(Dev D, int pad, const float* x, const float* y, double r, int* out, int cap,
+__global__ void solve_kernel(const __grid_constant__ Dev D);
+__global__ void debug_eval_kernel(const __grid_constant__ Dev D, float alpha, double r, float* grad_out, float* blk_out, double* scal);
+__global__ void broadphase_kernel(const __grid_constant__ Dev D, int pad, const float* x, const float* y, double r, int* out, int cap,
                                   int* count);
-__global__ void markers_kernel(Dev D, float* out);
+__global__ void markers_kernel(const __grid_constant__ Dev D, float* out);
 }  // namespace tac
 
 using namespace tac;

@@ -47,6 +47,9 @@ struct Shared {
     int expired;
 };
 
+// one CTA-wide scratch object, visible to every device function of the file
+__shared__ Shared S;
+
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -55,7 +58,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // true (in every thread) once the pad's solve has run longer than budget_ns;
 // thread 0 reads the clock and broadcasts so that the decision is uniform
-__device__ __forceinline__ bool over_budget(unsigned long long t0, unsigned long long budget_ns, Shared& S) {
+__device__ __forceinline__ bool over_budget(unsigned long long t0, unsigned long long budget_ns) {
     if (threadIdx.x == 0) S.expired = (global_ns() - t0) > budget_ns ? 1 : 0;
     __syncthreads();
     bool e = S.expired != 0;
@@ -73,7 +76,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 template <int K>
-__device__ __forceinline__ void block_sum(double (&v)[K], Shared& S) {
+__device__ __forceinline__ void block_sum(double (&v)[K]) {
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
@@ -91,7 +94,7 @@ __device__ __forceinline__ void block_sum(double (&v)[K], Shared& S) {
     __syncthreads();
 }
 
-__device__ __forceinline__ double block_min_d(double v, Shared& S) {
+__device__ __forceinline__ double block_min_d(double v) {
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -106,7 +109,7 @@ __device__ __forceinline__ double block_min_d(double v, Shared& S) {
 
 // max of up to 4 floats
 template <int K>
-__device__ __forceinline__ void block_max_f(float (&v)[K], Shared& S) {
+__device__ __forceinline__ void block_max_f(float (&v)[K]) {
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k)
@@ -127,7 +130,7 @@ __device__ __forceinline__ void block_max_f(float (&v)[K], Shared& S) {
 }
 
 // exclusive scan of one int per thread; total to every thread
-__device__ __forceinline__ int block_scan(int v, int& total, Shared& S) {
+__device__ __forceinline__ int block_scan(int v, int& total) {
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int x = v;
 #pragma unroll
@@ -284,7 +287,7 @@ struct TetOut {
 // Loads the patch's local vertices: su = patch-relative displacement at
 // u + alpha p, sp = p.
 __device__ __forceinline__ void load_patch(const Dev& D, const PadDev& P, const MeshDev& M, int vb, int nv,
-                                           float alpha, Shared& S) {
+                                           float alpha) {
     int ref = D.pvert[M.pvert_off + vb] & ((1 << 29) - 1);
     int tid = threadIdx.x;
     if (tid < nv) {
@@ -302,14 +305,14 @@ __device__ __forceinline__ void load_patch(const Dev& D, const PadDev& P, const 
 // pass 0: p^T H_e p at u; pass 1: gradient, diagonal blocks and remainder at
 // u + alpha p, scattered into g[gb], blk[gb].
 template <int PASS>
-__device__ TetOut tet_pass(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, int gb, Shared& S) {
+__device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, int gb) {
     TetOut out{0.0, 0, 0.f};
     const int tid = threadIdx.x;
     const float mu = P.mu, lam = P.lam, h2 = P.h * P.h;
     for (int pi = 0; pi < M.n_patch; ++pi) {
         int4 ph = D.patch[M.patch_off + pi];
         int tb = ph.x, vb = ph.y, nt = ph.z & 0xffff, nv = ph.z >> 16, cb = ph.w;
-        load_patch(D, P, M, vb, nv, alpha, S);
+        load_patch(D, P, M, vb, nv, alpha);
         __syncthreads();
         if (tid < nt) {
             int t = M.tet_off + tb + tid;
@@ -438,11 +441,11 @@ __device__ TetOut tet_pass(const Dev& D, const PadDev& P, const MeshDev& M, floa
     }
     // every thread must see the same totals: the caller branches on them
     double v[2] = {out.acc, (double)out.bad};
-    block_sum<2>(v, S);
+    block_sum<2>(v);
     out.acc = v[0];
     out.bad = v[1] > 0.0 ? 1 : 0;
     float fm[1] = {out.fmax};
-    block_max_f<1>(fm, S);
+    block_max_f<1>(fm);
     out.fmax = fm[0];
     return out;
 }
@@ -537,8 +540,8 @@ __device__ __forceinline__ BoxF ind_box(const Src& src, const Dev& D, const EnvD
 // Builds the candidate list of one pad into out[0 .. cap); returns the full
 // count (> cap means overflow; entries beyond cap are not written).
 template <class Src>
-__device__ int bp_build(const Src& src, const Dev& D, const MeshDev& M, const EnvDev& E, int* ilist, double r,
-                        int4* out, int cap, Shared& S) {
+__device__ __noinline__ int bp_build(const Src& src, const Dev& D, const MeshDev& M, const EnvDev& E, int* ilist, double r,
+                        int4* out, int cap) {
     const int tid = threadIdx.x;
     const float rlo = (float)(r * (1.0 - 1e-5)), rhi = (float)(r * (1.0 + 1e-5));
     const float rc = (float)(r * (1.0 + 1e-4)) + 1e-12f;     // conservative culling radius
@@ -551,8 +554,8 @@ __device__ int bp_build(const Src& src, const Dev& D, const MeshDev& M, const En
             mx[c] = fmaxf(mx[c], y);
             mn[c] = fmaxf(mn[c], -y);
         }
-    block_max_f<4>(mx, S);
-    block_max_f<4>(mn, S);
+    block_max_f<4>(mx);
+    block_max_f<4>(mn);
     float ibox[6] = {-mn[0] - rc, -mn[1] - rc, -mn[2] - rc, mx[0] + rc, mx[1] + rc, mx[2] + rc};
     // 2. union box of gel surface triangles near the indenter box
     float gx[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX}, gn[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
@@ -565,8 +568,8 @@ __device__ int bp_build(const Src& src, const Dev& D, const MeshDev& M, const En
                 gn[c] = fmaxf(gn[c], -b.lo[c]);
             }
     }
-    block_max_f<4>(gx, S);
-    block_max_f<4>(gn, S);
+    block_max_f<4>(gx);
+    block_max_f<4>(gn);
     float gbox[6] = {-gn[0] - rc, -gn[1] - rc, -gn[2] - rc, gx[0] + rc, gx[1] + rc, gx[2] + rc};
     bool any_gel = gx[0] > -FLT_MAX;
     // 3. cull indenter primitives of each type against the gel box (order kept)
@@ -582,7 +585,7 @@ __device__ int bp_build(const Src& src, const Dev& D, const MeshDev& M, const En
             int keep = 0;
             if (any_gel && j < nprim[ty]) keep = box_near(ind_box(src, D, E, ty, j), gbox) ? 1 : 0;
             int tot;
-            int pos = block_scan(keep, tot, S);
+            int pos = block_scan(keep, tot);
             if (keep) ilist[lbase + run + pos] = j;
             run += tot;
         }
@@ -607,7 +610,7 @@ __device__ int bp_build(const Src& src, const Dev& D, const MeshDev& M, const En
                     for (int q = 0; q < nil; ++q) c += bp_overlap(gb, ind_box(src, D, E, ty, il[q]), r, rlo, rhi) ? 1 : 0;
             }
             int tot;
-            int pos = block_scan(c, tot, S) + total;
+            int pos = block_scan(c, tot) + total;
             if (c > 0) {
                 int gi = ty == 0 ? D.sv[M.sv_off + i] : i;
                 for (int q = 0; q < nil; ++q) {
@@ -632,8 +635,7 @@ struct ContactCtl {
     int npairs, nlag, ncv;
 };
 
-__device__ void csr_build(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, ContactCtl& cc,
-                          Shared& S) {
+__device__ __noinline__ void csr_build(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, ContactCtl& cc) {
     const int tid = threadIdx.x;
     int* cnt = D.cnt + P.v_off;
     int* cvl = D.cvl + 6 * P.pair_off;
@@ -667,7 +669,7 @@ __device__ void csr_build(const Dev& D, const PadDev& P, const MeshDev& M, const
         int i = b0 + tid;
         int c = i < ncv ? cnt[cvl[i]] : 0;
         int tot;
-        int pos = block_scan(c, tot, S) + run;
+        int pos = block_scan(c, tot) + run;
         if (i < ncv) cvo[i] = pos;
         run += tot;
     }
@@ -708,7 +710,7 @@ __device__ void csr_build(const Dev& D, const PadDev& P, const MeshDev& M, const
 }
 
 // adds the slot values of every contact vertex into g[gb], blk[gb]
-__device__ void contact_gather(const Dev& D, const PadDev& P, const ContactCtl& cc, int gb) {
+__device__ __noinline__ void contact_gather(const Dev& D, const PadDev& P, const ContactCtl& cc, int gb) {
     const int* cvl = D.cvl + 6 * P.pair_off;
     const int* cvo = D.cvo + 6 * P.pair_off;
     const int* ent = D.ent + 6 * P.pair_off;
@@ -735,8 +737,7 @@ __device__ void contact_gather(const Dev& D, const PadDev& P, const ContactCtl& 
 // pair passes
 
 // minimum distance over the candidates at (u, s)
-__device__ double pair_dmin(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np, double s,
-                            Shared& S) {
+__device__ __noinline__ double pair_dmin(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np, double s) {
     double dm = 1e300;
     const int4* pr = D.pairs + P.pair_off;
     for (int k = threadIdx.x; k < np; k += kThreads) {
@@ -745,12 +746,12 @@ __device__ double pair_dmin(const Dev& D, const PadDev& P, const MeshDev& M, con
         pair_slots(D, M, E, q, gsl, isl);
         dm = fmin(dm, pair_distance(D, P, M, q.x, gsl, isl, 0.0f, s, 2.0 * P.dhat));
     }
-    return block_min_d(dm, S);
+    return block_min_d(dm);
 }
 
 // p^T H p of the barrier and friction terms and the per-pair step bound
-__device__ void pair_php(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np, int nl, double s,
-                         double& php, double& accd, Shared& S) {
+__device__ __noinline__ void pair_php(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np, int nl, double s,
+                         double& php, double& accd) {
     double acc = 0.0, amin = 1e300;
     const int4* pr = D.pairs + P.pair_off;
     const double dh = P.dhat, kap = P.kappa;
@@ -821,14 +822,14 @@ __device__ void pair_php(const Dev& D, const PadDev& P, const MeshDev& M, const 
             acc += cf * (moll_f1_over_s(sv, eps) * tp2 - moll_c(sv, eps) * up * up);
         }
     double v[1] = {acc};
-    block_sum<1>(v, S);
+    block_sum<1>(v);
     php = v[0];
-    accd = block_min_d(amin, S);
+    accd = block_min_d(amin);
 }
 
 // trial pass over pairs at u + alpha p: slot contributions and remainders
-__device__ void pair_trial(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np, int nl, double s,
-                           float alpha, double& rem, int& bad, Shared& S) {
+__device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np, int nl, double s,
+                           float alpha, double& rem, int& bad) {
     double acc = 0.0;
     int badl = 0;
     const int4* pr = D.pairs + P.pair_off;
@@ -941,7 +942,7 @@ __device__ void pair_trial(const Dev& D, const PadDev& P, const MeshDev& M, cons
             }
     }
     double v[1] = {acc};
-    block_sum<1>(v, S);
+    block_sum<1>(v);
     rem = v[0];
     if (badl) S.flag = 1;
     __syncthreads();
@@ -952,7 +953,7 @@ __device__ void pair_trial(const Dev& D, const PadDev& P, const MeshDev& M, cons
 }
 
 // lag records: candidates closer than dhat at the frame start
-__device__ int lag_build(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np, Shared& S) {
+__device__ __noinline__ int lag_build(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np) {
     const int4* pr = D.pairs + P.pair_off;
     LagRec* lg = D.lag + P.pair_off;
     const double dh = P.dhat, kap = P.kappa;
@@ -994,7 +995,7 @@ __device__ int lag_build(const Dev& D, const PadDev& P, const MeshDev& M, const 
             }
         }
         int tot;
-        int pos = block_scan(keep, tot, S) + run;
+        int pos = block_scan(keep, tot) + run;
         if (keep) lg[pos] = L;
         run += tot;
     }
@@ -1013,8 +1014,7 @@ struct Dots {
 
 // Completes g and the blocks at u + alpha p (inertia, Dirichlet), applies
 // the preconditioner and reduces the Dai-Kou dot products.
-__device__ Dots finalize(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, int gb, int go, bool dots,
-                         Shared& S) {
+__device__ __noinline__ Dots finalize(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, int gb, int go, bool dots) {
     double v[4] = {0, 0, 0, 0};
     float gi[1] = {0.f};
     int bad = 0;
@@ -1070,8 +1070,8 @@ __device__ Dots finalize(const Dev& D, const PadDev& P, const MeshDev& M, float 
         }
     }
     if (bad) S.flag = 1;
-    block_sum<4>(v, S);
-    block_max_f<1>(gi, S);
+    block_sum<4>(v);
+    block_max_f<1>(gi);
     Dots d{v[0], v[1], v[2], v[3], gi[0], 0};
     d.bad = S.flag;
     __syncthreads();
@@ -1087,8 +1087,8 @@ struct DirOut {
 
 // optionally u += alpha p (double-float), then p = -z + beta p; reduces
 // g^T p, p^T M p and max_i |p_i|
-__device__ DirOut direction(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, bool move, double beta,
-                            int gb, Shared& S) {
+__device__ __noinline__ DirOut direction(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, bool move, double beta,
+                            int gb) {
     double v[2] = {0, 0};
     float pn[1] = {0.f};
     const float rho = P.rho;
@@ -1123,13 +1123,13 @@ __device__ DirOut direction(const Dev& D, const PadDev& P, const MeshDev& M, flo
         v[1] += (double)(m * n2);
         pn[0] = fmaxf(pn[0], sqrtf(n2));
     }
-    block_sum<2>(v, S);
-    block_max_f<1>(pn, S);
+    block_sum<2>(v);
+    block_max_f<1>(pn);
     return DirOut{v[0], v[1], pn[0]};
 }
 
 // p = xhat - x^t = h v (zero on Dirichlet vertices); returns max_i |p_i|
-__device__ float predictor_direction(const Dev& D, const PadDev& P, const MeshDev& M, Shared& S) {
+__device__ __noinline__ float predictor_direction(const Dev& D, const PadDev& P, const MeshDev& M) {
     float pn[1] = {0.f};
     for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
         int si = P.v_off + i;
@@ -1144,12 +1144,12 @@ __device__ float predictor_direction(const Dev& D, const PadDev& P, const MeshDe
         }
         pn[0] = fmaxf(pn[0], sqrtf(n2));
     }
-    block_max_f<1>(pn, S);
+    block_max_f<1>(pn);
     return pn[0];
 }
 
 // u += alpha p (double-float), p untouched
-__device__ void move_state(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, Shared& S) {
+__device__ __noinline__ void move_state(const Dev& D, const PadDev& P, const MeshDev& M, float alpha) {
     for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
         int si = P.v_off + i;
         if (D.fixed[M.xv_off + i]) continue;
@@ -1191,7 +1191,7 @@ __device__ void rotation(const float* pose, double R[9]) {
         }
 }
 
-__device__ void world_indenter(const Dev& D, const PadDev& P, const EnvDev& E, const float* pose, float* Yw) {
+__device__ __noinline__ void world_indenter(const Dev& D, const PadDev& P, const EnvDev& E, const float* pose, float* Yw) {
     double R[9];
     rotation(pose, R);
     for (int j = threadIdx.x; j < E.n_v; j += kThreads) {
@@ -1211,7 +1211,7 @@ struct PadCounters {
     long long iters, substeps, rebuilds, halvings, tet_passes, vert_passes, pair_evals, peak_pairs;
 };
 
-__device__ void solve_pad(const Dev& D, int pad, Shared& S) {
+__device__ void solve_pad(const Dev& D, int pad) {
     const PadDev P = D.pads[pad];
     const MeshDev M = D.meshes[P.mesh];
     const EnvDev E = D.envs[P.env];
@@ -1245,7 +1245,7 @@ __device__ void solve_pad(const Dev& D, int pad, Shared& S) {
         }
         dyv[0] = fmaxf(dyv[0], sqrtf(a));
     }
-    block_max_f<1>(dyv, S);
+    block_max_f<1>(dyv);
     const double Dy = (double)dyv[0] * (1.0 + 1e-6);
     const double dh = P.dhat, margin = P.dhat;
     const double rbp = (dh + margin) * (1.0 + 1e-6);
@@ -1255,38 +1255,38 @@ __device__ void solve_pad(const Dev& D, int pad, Shared& S) {
     ContactCtl cc{0, 0, 0};
     {
         SrcState src{&D, &P, &M, 0.0f};
-        int n = bp_build(src, D, M, E, il, rbp, pairs, P.pair_cap, S);
+        int n = bp_build(src, D, M, E, il, rbp, pairs, P.pair_cap);
         ctr.rebuilds++;
         ctr.peak_pairs = n;
         if (n > P.pair_cap) status = ST_OVERFLOW;
         cc.npairs = min(n, P.pair_cap);
     }
     if (status == ST_CONVERGED) {
-        cc.nlag = lag_build(D, P, M, E, cc.npairs, S);
-        csr_build(D, P, M, E, cc, S);
+        cc.nlag = lag_build(D, P, M, E, cc.npairs);
+        csr_build(D, P, M, E, cc);
         // initial guess on the segment x^t -> xhat: collision-free by the
         // per-pair bound, inside the broad-phase margin, no inverted tet
-        float pn0 = predictor_direction(D, P, M, S);
+        float pn0 = predictor_direction(D, P, M);
         if (pn0 > 0.f) {
             double php_d, accd;
-            pair_php(D, P, M, E, cc.npairs, 0, 0.0, php_d, accd, S);
+            pair_php(D, P, M, E, cc.npairs, 0, 0.0, php_d, accd);
             ctr.pair_evals += cc.npairs;
             double a0 = fmin(1.0, fmin(accd, margin / (double)pn0));
             for (int k = 0; k <= kMaxHalvings; ++k) {
-                TetOut t = tet_pass<1>(D, P, M, (float)a0, 0, S);
+                TetOut t = tet_pass<1>(D, P, M, (float)a0, 0);
                 ctr.tet_passes++;
                 if (!t.bad) break;
                 a0 = (k == kMaxHalvings) ? 0.0 : 0.5 * a0;
             }
             if (a0 > 0.0) {
-                move_state(D, P, M, (float)a0, S);
+                move_state(D, P, M, (float)a0);
                 SrcState src{&D, &P, &M, 0.0f};
-                int n = bp_build(src, D, M, E, il, rbp, pairs, P.pair_cap, S);
+                int n = bp_build(src, D, M, E, il, rbp, pairs, P.pair_cap);
                 ctr.rebuilds++;
                 ctr.peak_pairs = max(ctr.peak_pairs, (long long)n);
                 if (n > P.pair_cap) status = ST_OVERFLOW;
                 cc.npairs = min(n, P.pair_cap);
-                if (status == ST_CONVERGED) csr_build(D, P, M, E, cc, S);
+                if (status == ST_CONVERGED) csr_build(D, P, M, E, cc);
             }
         }
     }
@@ -1302,19 +1302,19 @@ __device__ void solve_pad(const Dev& D, int pad, Shared& S) {
             if (Dy == 0.0) {
                 ds = 1.0 - s;
             } else {
-                double dmin = pair_dmin(D, P, M, E, cc.npairs, s, S);
+                double dmin = pair_dmin(D, P, M, E, cc.npairs, s);
                 ctr.pair_evals += cc.npairs;
                 ds = fmin(1.0 - s, kEta * dmin / Dy);
                 if (Mb + ds * Dy > margin) {
                     SrcState src{&D, &P, &M, (float)s};
-                    int n = bp_build(src, D, M, E, il, rbp, pairs, P.pair_cap, S);
+                    int n = bp_build(src, D, M, E, il, rbp, pairs, P.pair_cap);
                     ctr.rebuilds++;
                     ctr.peak_pairs = max(ctr.peak_pairs, (long long)n);
                     if (n > P.pair_cap) { status = ST_OVERFLOW; break; }
                     cc.npairs = n;
-                    csr_build(D, P, M, E, cc, S);
+                    csr_build(D, P, M, E, cc);
                     Mb = 0.0;
-                    dmin = pair_dmin(D, P, M, E, cc.npairs, s, S);
+                    dmin = pair_dmin(D, P, M, E, cc.npairs, s);
                     ds = fmin(fmin(1.0 - s, kEta * dmin / Dy), margin / Dy);
                 }
             }
@@ -1323,14 +1323,14 @@ __device__ void solve_pad(const Dev& D, int pad, Shared& S) {
             ctr.substeps++;
         }
         // gradient and preconditioner at the current point
-        TetOut to = tet_pass<1>(D, P, M, 0.0f, gc, S);
+        TetOut to = tet_pass<1>(D, P, M, 0.0f, gc);
         ctr.tet_passes++;
         double rem0;
         int badp;
-        pair_trial(D, P, M, E, cc.npairs, cc.nlag, s, 0.0f, rem0, badp, S);
+        pair_trial(D, P, M, E, cc.npairs, cc.nlag, s, 0.0f, rem0, badp);
         ctr.pair_evals += cc.npairs;
         contact_gather(D, P, cc, gc);
-        Dots d0 = finalize(D, P, M, 0.0f, gc, gc, false, S);
+        Dots d0 = finalize(D, P, M, 0.0f, gc, gc, false);
         ctr.vert_passes++;
         if (to.bad || badp || d0.bad) { status = ST_NONFINITE; break; }
         ginf = d0.ginf;
@@ -1339,37 +1339,37 @@ __device__ void solve_pad(const Dev& D, int pad, Shared& S) {
             g_ref = fmaxf(g_ref, ginf);
             have_ref = true;
         }
-        DirOut dir = direction(D, P, M, 0.0f, false, 0.0, gc, S);
+        DirOut dir = direction(D, P, M, 0.0f, false, 0.0, gc);
         ctr.vert_passes++;
         const float rel = (s >= 1.0) ? P.tol : fmaxf(P.tol, P.tol_adv);
         target = fmaxf(rel * g_ref, kFloat32Floor * fmax);
         while (ginf > target && ctr.iters < P.max_iter) {
-            if (over_budget(t0, budget, S)) { status = ST_MAXITER; break; }
+            if (over_budget(t0, budget)) { status = ST_MAXITER; break; }
             if (dir.pn == 0.f || dir.gTp >= 0.0) {
-                dir = direction(D, P, M, 0.0f, false, 0.0, gc, S);
+                dir = direction(D, P, M, 0.0f, false, 0.0, gc);
                 ctr.vert_passes++;
                 if (dir.pn == 0.f) break;
             }
             double a_up = dh / (2.0 * (double)dir.pn);
-            TetOut tp = tet_pass<0>(D, P, M, 0.0f, gc, S);
+            TetOut tp = tet_pass<0>(D, P, M, 0.0f, gc);
             ctr.tet_passes++;
             double php_c, a_ccd;
-            pair_php(D, P, M, E, cc.npairs, cc.nlag, s, php_c, a_ccd, S);
+            pair_php(D, P, M, E, cc.npairs, cc.nlag, s, php_c, a_ccd);
             ctr.pair_evals += cc.npairs;
             double pHp = tp.acc + php_c + dir.pMp;
             double a_bar = pHp > 0.0 ? -dir.gTp / pHp : 1e300;
             double alpha = fmin(fmin(a_up, a_ccd), a_bar);
             if (Mb + alpha * dir.pn > margin) {
                 SrcState src{&D, &P, &M, (float)s};
-                int n = bp_build(src, D, M, E, il, rbp, pairs, P.pair_cap, S);
+                int n = bp_build(src, D, M, E, il, rbp, pairs, P.pair_cap);
                 ctr.rebuilds++;
                 ctr.peak_pairs = max(ctr.peak_pairs, (long long)n);
                 if (n > P.pair_cap) { status = ST_OVERFLOW; break; }
                 cc.npairs = n;
-                csr_build(D, P, M, E, cc, S);
+                csr_build(D, P, M, E, cc);
                 Mb = 0.0;
                 double dummy;
-                pair_php(D, P, M, E, cc.npairs, cc.nlag, s, dummy, a_ccd, S);
+                pair_php(D, P, M, E, cc.npairs, cc.nlag, s, dummy, a_ccd);
                 ctr.pair_evals += cc.npairs;
                 alpha = fmin(fmin(a_up, a_ccd), a_bar);
             }
@@ -1378,14 +1378,14 @@ __device__ void solve_pad(const Dev& D, int pad, Shared& S) {
             Dots dt{};
             for (int hv = 0; hv <= kMaxHalvings; ++hv) {
                 float af = (float)alpha;
-                TetOut tt = tet_pass<1>(D, P, M, af, gn, S);
+                TetOut tt = tet_pass<1>(D, P, M, af, gn);
                 ctr.tet_passes++;
                 double remc;
                 int bp;
-                pair_trial(D, P, M, E, cc.npairs, cc.nlag, s, af, remc, bp, S);
+                pair_trial(D, P, M, E, cc.npairs, cc.nlag, s, af, remc, bp);
                 ctr.pair_evals += cc.npairs;
                 contact_gather(D, P, cc, gn);
-                dt = finalize(D, P, M, af, gn, gc, true, S);
+                dt = finalize(D, P, M, af, gn, gc, true);
                 ctr.vert_passes++;
                 if (!tt.bad && !bp && !dt.bad) {
                     double a = (double)af;
@@ -1406,10 +1406,10 @@ __device__ void solve_pad(const Dev& D, int pad, Shared& S) {
             ctr.iters++;
             double beta = 0.0;
             if (fabs(dt.yp) > 1e-300) beta = dt.zy / dt.yp - (dt.yPy / dt.yp) * (dt.pg1 / dt.yp);
-            dir = direction(D, P, M, (float)alpha, true, beta, gn, S);
+            dir = direction(D, P, M, (float)alpha, true, beta, gn);
             ctr.vert_passes++;
             if (dir.gTp >= 0.0) {
-                dir = direction(D, P, M, 0.0f, false, 0.0, gn, S);
+                dir = direction(D, P, M, 0.0f, false, 0.0, gn);
                 ctr.vert_passes++;
             }
             gc = gn;
@@ -1421,7 +1421,7 @@ __device__ void solve_pad(const Dev& D, int pad, Shared& S) {
             if (ginf > target) status = ST_MAXITER;
             break;
         }
-        if (ctr.substeps >= kMaxSubsteps || ctr.iters >= P.max_iter || over_budget(t0, budget, S)) {
+        if (ctr.substeps >= kMaxSubsteps || ctr.iters >= P.max_iter || over_budget(t0, budget)) {
             status = ST_MAXITER;
             break;
         }
@@ -1448,8 +1448,7 @@ __device__ void solve_pad(const Dev& D, int pad, Shared& S) {
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads) solve_kernel(Dev D) {
-    __shared__ Shared S;
+__global__ void __launch_bounds__(kThreads, 2) solve_kernel(const __grid_constant__ Dev D) {
     if (threadIdx.x == 0) S.flag = 0;
     for (;;) {
         if (threadIdx.x == 0) S.pad = atomicAdd(D.queue, 1);
@@ -1457,16 +1456,15 @@ __global__ void __launch_bounds__(kThreads) solve_kernel(Dev D) {
         int q = S.pad;
         __syncthreads();
         if (q >= D.n_pads) break;
-        solve_pad(D, D.order[q], S);
+        solve_pad(D, D.order[q]);
     }
 }
 
 // ---------------------------------------------------------------------------
 // verification kernel: one CTA per pad (see tac_debug_eval)
 
-__global__ void __launch_bounds__(kThreads) debug_eval_kernel(Dev D, float alpha, double r, float* grad_out,
+__global__ void __launch_bounds__(kThreads) debug_eval_kernel(const __grid_constant__ Dev D, float alpha, double r, float* grad_out,
                                                               float* blk_out, double* scal) {
-    __shared__ Shared S;
     if (threadIdx.x == 0) S.flag = 0;
     __syncthreads();
     const int pad = blockIdx.x;
@@ -1477,9 +1475,9 @@ __global__ void __launch_bounds__(kThreads) debug_eval_kernel(Dev D, float alpha
     world_indenter(D, P, E, D.pose_t + 6 * pad, D.Yn);
     __syncthreads();
     SrcState src{&D, &P, &M, 1.0f};
-    int n = bp_build(src, D, M, E, D.ilist + P.il_off, r, D.pairs + P.pair_off, P.pair_cap, S);
+    int n = bp_build(src, D, M, E, D.ilist + P.il_off, r, D.pairs + P.pair_off, P.pair_cap);
     ContactCtl cc{min(n, P.pair_cap), 0, 0};
-    csr_build(D, P, M, E, cc, S);
+    csr_build(D, P, M, E, cc);
     // u0 = uhat = u (no inertia offset, no friction lag)
     for (int i = threadIdx.x; i < M.n_v; i += kThreads)
         for (int c = 0; c < 3; ++c) {
@@ -1489,10 +1487,10 @@ __global__ void __launch_bounds__(kThreads) debug_eval_kernel(Dev D, float alpha
             D.uhat[sc] = D.uh[sc] + D.ul[sc];
         }
     __syncthreads();
-    double dmin = pair_dmin(D, P, M, E, cc.npairs, 1.0, S);
-    TetOut tp = tet_pass<0>(D, P, M, 0.0f, 0, S);
+    double dmin = pair_dmin(D, P, M, E, cc.npairs, 1.0);
+    TetOut tp = tet_pass<0>(D, P, M, 0.0f, 0);
     double php_c, a_ccd;
-    pair_php(D, P, M, E, cc.npairs, 0, 1.0, php_c, a_ccd, S);
+    pair_php(D, P, M, E, cc.npairs, 0, 1.0, php_c, a_ccd);
     double pMp = 0.0;
     {
         double v[1] = {0.0};
@@ -1504,13 +1502,13 @@ __global__ void __launch_bounds__(kThreads) debug_eval_kernel(Dev D, float alpha
                 v[0] += (double)(m * pv * pv);
             }
         }
-        block_sum<1>(v, S);
+        block_sum<1>(v);
         pMp = v[0];
     }
-    TetOut tt = tet_pass<1>(D, P, M, alpha, 0, S);
+    TetOut tt = tet_pass<1>(D, P, M, alpha, 0);
     double remc;
     int bp;
-    pair_trial(D, P, M, E, cc.npairs, 0, 1.0, alpha, remc, bp, S);
+    pair_trial(D, P, M, E, cc.npairs, 0, 1.0, alpha, remc, bp);
     contact_gather(D, P, cc, 0);
     // outputs before inertia / inversion: gradient with inertia m alpha p
     double gp[1] = {0.0};
@@ -1529,8 +1527,8 @@ __global__ void __launch_bounds__(kThreads) debug_eval_kernel(Dev D, float alpha
         if (blk_out)
             for (int c = 0; c < 6; ++c) blk_out[6 * si + c] = D.blk[0][c * D.Vt + si] + (c < 3 ? m : 0.f);
     }
-    block_sum<1>(gp, S);
-    block_max_f<1>(gi, S);
+    block_sum<1>(gp);
+    block_max_f<1>(gi);
     if (threadIdx.x == 0 && scal) {
         double a = alpha;
         double R = tt.acc + remc + 0.5 * a * a * pMp;
@@ -1547,14 +1545,13 @@ __global__ void __launch_bounds__(kThreads) debug_eval_kernel(Dev D, float alpha
 }
 
 // candidate set of one pad for caller positions (see tac_broadphase)
-__global__ void __launch_bounds__(kThreads) broadphase_kernel(Dev D, int pad, const float* x, const float* y,
+__global__ void __launch_bounds__(kThreads) broadphase_kernel(const __grid_constant__ Dev D, int pad, const float* x, const float* y,
                                                               double r, int* out, int cap, int* count) {
-    __shared__ Shared S;
     const PadDev P = D.pads[pad];
     const MeshDev M = D.meshes[P.mesh];
     const EnvDev E = D.envs[P.env];
     SrcArrays src{x, y};
-    int n = bp_build(src, D, M, E, D.ilist + P.il_off, r, D.pairs + P.pair_off, P.pair_cap, S);
+    int n = bp_build(src, D, M, E, D.ilist + P.il_off, r, D.pairs + P.pair_off, P.pair_cap);
     for (int k = threadIdx.x; k < min(n, min(cap, P.pair_cap)); k += kThreads) {
         int4 q = D.pairs[P.pair_off + k];
         out[3 * k] = q.x;
@@ -1565,7 +1562,7 @@ __global__ void __launch_bounds__(kThreads) broadphase_kernel(Dev D, int pad, co
 }
 
 // marker readout: u_m = sum_k w_k u_{v_k}, first two components
-__global__ void markers_kernel(Dev D, float* out) {
+__global__ void markers_kernel(const __grid_constant__ Dev D, float* out) {
     int pad = blockIdx.y;
     const PadDev P = D.pads[pad];
     const MeshDev M = D.meshes[P.mesh];
