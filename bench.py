@@ -135,7 +135,7 @@ def algorithmic_bytes(stats, w):
     """Counted bytes of one solve launch from the per-pad counters."""
     tot = 0.0
     for k, pad in enumerate(w.pads):
-        it, sub, reb, hal, tp, vp, pe, peak = [float(v) for v in stats[k]]
+        it, sub, reb, hal, tp, vp, pe, peak = [float(v) for v in stats[k][:8]]
         tot += tp * (B_TET * pad.n_tets + B_TET_VERT * pad.n_verts) + vp * B_VERT_PASS * pad.n_verts + pe * B_PAIR
     return tot
 
@@ -268,11 +268,16 @@ def run_ours(args, rank, world):
         torch.distributed.barrier()
     total_ms = start.elapsed_time(stop)
     solve_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    phase = np.zeros(8)
     for stt, it, st in stats_all:
         s_np = stt.cpu().numpy().reshape(-1, w.pads_per_env)
         conv += int(np.all(s_np == 0, axis=1).sum())
         iter_hist.append(it.cpu().numpy())
-        bytes_alg += algorithmic_bytes(st.cpu().numpy(), w)
+        st_np = st.cpu().numpy()
+        bytes_alg += algorithmic_bytes(st_np, w)
+        phase += st_np[:, 8:16].sum(axis=0)
+    names = ["tet_pHp", "tet_grad", "pair_pHp", "pair_grad", "vertex", "advance_rebuild", "setup"]
+    phase_share = {n: float(phase[i] / phase[7]) for i, n in enumerate(names)} if phase[7] > 0 else None
     if world > 1:
         t = torch.tensor([total_ms, float(conv)], dtype=torch.float64, device=dev)
         mx = t.clone()
@@ -347,7 +352,7 @@ def run_ours(args, rank, world):
                "iters_per_pad_frame": {"p50": float(np.percentile(its, 50)), "p99": float(np.percentile(its, 99)),
                                        "max": int(its.max())},
                "frame_ms": {"p50": float(np.percentile(solve_ms, 50)), "p99": float(np.percentile(solve_ms, 99))},
-               "setup_s": t_create}
+               "setup_s": t_create, "phase_share": phase_share}
         print(json.dumps(out), flush=True)
     b.close()
 

@@ -183,9 +183,12 @@ int tac_broadphase(tac_handle h, int pad, const float* x_dev, const float* y_dev
 int tac_debug_eval(tac_handle h, const float* u_dev, const float* p_dev, float alpha,
                    float* grad_dev, float* blk_dev, double* scal_dev, void* stream);
 
-/* Per-pad counters of the last tac_step (device [n_pads*8] long long):
+/* Per-pad counters of the last tac_step (device [n_pads*16] long long):
  * iterations, substeps, broad-phase rebuilds, Armijo halvings, tet passes,
- * vertex passes, pair evaluations, peak candidate count. */
+ * vertex passes, pair evaluations, peak candidate count, then nanoseconds
+ * spent in: p^T H p tet passes, gradient tet passes, contact p^T H p and
+ * step bound, contact gradient passes, vertex passes, indenter advance and
+ * rebuilds, frame setup, and the whole pad solve. */
 int tac_stats(tac_handle h, long long* stats_dev, void* stream);
 
 /* Convergence record of the last tac_step per pad (device [n_pads*4]

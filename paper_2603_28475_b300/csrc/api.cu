@@ -357,7 +357,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     int* cvo = dalloc<int>(K, 6 * pc + 1, rc);
     int* cnt = dalloc<int>(K, Vt, rc);
     int* ilist = dalloc<int>(K, il, rc);
-    long long* stats = dalloc<long long>(K, 8 * (size_t)n_pads, rc);
+    long long* stats = dalloc<long long>(K, 16 * (size_t)n_pads, rc);
     double* norms = dalloc<double>(K, 4 * (size_t)n_pads, rc);
     int* queue = dalloc<int>(K, 1, rc);
     int* order_d = dalloc<int>(K, n_pads, rc);
@@ -446,7 +446,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     CUDA_TRY(cudaMemsetAsync(k0, 0, 6 * (size_t)Vt * 4, st));
     CUDA_TRY(cudaMemsetAsync(k1, 0, 6 * (size_t)Vt * 4, st));
     CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)Vt * 4, st));
-    CUDA_TRY(cudaMemsetAsync(stats, 0, 8 * (size_t)n_pads * 8, st));
+    CUDA_TRY(cudaMemsetAsync(stats, 0, 16 * (size_t)n_pads * 8, st));
     CUDA_TRY(cudaMemsetAsync(norms, 0, 4 * (size_t)n_pads * 8, st));
     CUDA_TRY(cudaMemsetAsync(b->d_pose_t, 0, 6 * (size_t)n_pads * 4, st));
     CUDA_TRY(cudaMemsetAsync(b->d_pose_n, 0, 6 * (size_t)n_pads * 4, st));
@@ -590,7 +590,7 @@ int tac_debug_eval(tac_handle h, const float* u_dev, const float* p_dev, float a
 
 int tac_stats(tac_handle h, long long* stats_dev, void* stream) {
     if (!h || !stats_dev) return fail(TAC_ERR_INVALID_ARG, "null argument");
-    CUDA_TRY(cudaMemcpyAsync(stats_dev, h->dev.stats, 8 * (size_t)h->n_pads * 8, cudaMemcpyDeviceToDevice,
+    CUDA_TRY(cudaMemcpyAsync(stats_dev, h->dev.stats, 16 * (size_t)h->n_pads * 8, cudaMemcpyDeviceToDevice,
                              static_cast<cudaStream_t>(stream)));
     return TAC_OK;
 }

@@ -56,6 +56,25 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
+// per-phase wall time of one pad's solve, accumulated by thread 0 at points
+// where the CTA is already synchronised
+enum { PH_TET0 = 0, PH_TET1, PH_PAIR_PHP, PH_PAIR_TRIAL, PH_VERTEX, PH_BROAD, PH_SETUP, PH_COUNT };
+
+struct PhaseClock {
+    unsigned long long last = 0;
+    unsigned long long acc[PH_COUNT] = {0, 0, 0, 0, 0, 0, 0};
+    __device__ __forceinline__ void start() {
+        if (threadIdx.x == 0) last = global_ns();
+    }
+    __device__ __forceinline__ void lap(int ph) {
+        if (threadIdx.x == 0) {
+            unsigned long long t = global_ns();
+            acc[ph] += t - last;
+            last = t;
+        }
+    }
+};
+
 // true (in every thread) once the pad's solve has run longer than budget_ns;
 // thread 0 reads the clock and broadcasts so that the decision is uniform
 __device__ __forceinline__ bool over_budget(unsigned long long t0, unsigned long long budget_ns) {
@@ -1221,6 +1240,8 @@ __device__ void solve_pad(const Dev& D, int pad) {
     unsigned long long t0 = 0;
     if (tid == 0) t0 = global_ns();
     const unsigned long long budget = D.budget_ns;
+    PhaseClock clk;
+    clk.start();
     // frame setup
     world_indenter(D, P, E, D.pose_t + 6 * pad, D.Yt);
     world_indenter(D, P, E, D.pose_n + 6 * pad, D.Yn);
@@ -1290,6 +1311,7 @@ __device__ void solve_pad(const Dev& D, int pad) {
             }
         }
     }
+    clk.lap(PH_SETUP);
     float g_ref = P.g_ref;   // becomes max(floor, |g| after the first substep)
     bool have_ref = false;
     float fmax = 0.f;        // force scale of the float32 resolution floor
@@ -1321,15 +1343,18 @@ __device__ void solve_pad(const Dev& D, int pad) {
             s = (ds >= 1.0 - s) ? 1.0 : s + ds;
             Mb += ds * Dy;
             ctr.substeps++;
+            clk.lap(PH_BROAD);
         }
         // gradient and preconditioner at the current point
         TetOut to = tet_pass<1>(D, P, M, 0.0f, gc);
         ctr.tet_passes++;
+        clk.lap(PH_TET1);
         double rem0;
         int badp;
         pair_trial(D, P, M, E, cc.npairs, cc.nlag, s, 0.0f, rem0, badp);
         ctr.pair_evals += cc.npairs;
         contact_gather(D, P, cc, gc);
+        clk.lap(PH_PAIR_TRIAL);
         Dots d0 = finalize(D, P, M, 0.0f, gc, gc, false);
         ctr.vert_passes++;
         if (to.bad || badp || d0.bad) { status = ST_NONFINITE; break; }
@@ -1341,6 +1366,7 @@ __device__ void solve_pad(const Dev& D, int pad) {
         }
         DirOut dir = direction(D, P, M, 0.0f, false, 0.0, gc);
         ctr.vert_passes++;
+        clk.lap(PH_VERTEX);
         const float rel = (s >= 1.0) ? P.tol : fmaxf(P.tol, P.tol_adv);
         target = fmaxf(rel * g_ref, kFloat32Floor * fmax);
         while (ginf > target && ctr.iters < P.max_iter) {
@@ -1351,11 +1377,14 @@ __device__ void solve_pad(const Dev& D, int pad) {
                 if (dir.pn == 0.f) break;
             }
             double a_up = dh / (2.0 * (double)dir.pn);
+            clk.lap(PH_VERTEX);
             TetOut tp = tet_pass<0>(D, P, M, 0.0f, gc);
             ctr.tet_passes++;
+            clk.lap(PH_TET0);
             double php_c, a_ccd;
             pair_php(D, P, M, E, cc.npairs, cc.nlag, s, php_c, a_ccd);
             ctr.pair_evals += cc.npairs;
+            clk.lap(PH_PAIR_PHP);
             double pHp = tp.acc + php_c + dir.pMp;
             double a_bar = pHp > 0.0 ? -dir.gTp / pHp : 1e300;
             double alpha = fmin(fmin(a_up, a_ccd), a_bar);
@@ -1372,6 +1401,7 @@ __device__ void solve_pad(const Dev& D, int pad) {
                 pair_php(D, P, M, E, cc.npairs, cc.nlag, s, dummy, a_ccd);
                 ctr.pair_evals += cc.npairs;
                 alpha = fmin(fmin(a_up, a_ccd), a_bar);
+                clk.lap(PH_BROAD);
             }
             const int gn = gc ^ 1;
             bool accepted = false;
@@ -1380,13 +1410,16 @@ __device__ void solve_pad(const Dev& D, int pad) {
                 float af = (float)alpha;
                 TetOut tt = tet_pass<1>(D, P, M, af, gn);
                 ctr.tet_passes++;
+                clk.lap(PH_TET1);
                 double remc;
                 int bp;
                 pair_trial(D, P, M, E, cc.npairs, cc.nlag, s, af, remc, bp);
                 ctr.pair_evals += cc.npairs;
                 contact_gather(D, P, cc, gn);
+                clk.lap(PH_PAIR_TRIAL);
                 dt = finalize(D, P, M, af, gn, gc, true);
                 ctr.vert_passes++;
+                clk.lap(PH_VERTEX);
                 if (!tt.bad && !bp && !dt.bad) {
                     double a = (double)af;
                     double R = tt.acc + remc + 0.5 * a * a * dir.pMp;
@@ -1412,6 +1445,7 @@ __device__ void solve_pad(const Dev& D, int pad) {
                 dir = direction(D, P, M, 0.0f, false, 0.0, gn);
                 ctr.vert_passes++;
             }
+            clk.lap(PH_VERTEX);
             gc = gn;
             ginf = dt.ginf;
             target = fmaxf(rel * g_ref, kFloat32Floor * fmax);
@@ -1439,9 +1473,12 @@ __device__ void solve_pad(const Dev& D, int pad) {
     if (tid == 0) {
         if (D.status) D.status[pad] = status;
         if (D.iters) D.iters[pad] = (int)ctr.iters;
-        long long* st = D.stats + 8 * pad;
+        long long* st = D.stats + 16 * pad;
         st[0] = ctr.iters; st[1] = ctr.substeps; st[2] = ctr.rebuilds; st[3] = ctr.halvings;
         st[4] = ctr.tet_passes; st[5] = ctr.vert_passes; st[6] = ctr.pair_evals; st[7] = ctr.peak_pairs;
+        clk.lap(PH_VERTEX);
+        for (int q = 0; q < PH_COUNT; ++q) st[8 + q] = (long long)clk.acc[q];
+        st[15] = (long long)(global_ns() - t0);
         double* nr = D.norms + 4 * pad;
         nr[0] = ginf; nr[1] = target; nr[2] = g_ref; nr[3] = fmax;
     }

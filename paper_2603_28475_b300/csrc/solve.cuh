@@ -98,7 +98,7 @@ struct Dev {
     // outputs
     int* status;
     int* iters;
-    long long* stats;         // [n_pads][8]
+    long long* stats;         // [n_pads][16] counters and per-phase nanoseconds
     double* norms;            // [n_pads][4] final |g|_inf, stopping target, g_ref, force scale
     int* queue;
     unsigned long long budget_ns;   // wall-clock cap of one pad's frame solve

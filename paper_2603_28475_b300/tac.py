@@ -245,7 +245,7 @@ class TacBatch:
         return out
 
     def stats(self, stream=None):
-        out = torch.empty(self.n_pads, 8, dtype=torch.int64, device=self.device)
+        out = torch.empty(self.n_pads, 16, dtype=torch.int64, device=self.device)
         _check(lib().tac_stats(self._h, _ptr(out), _stream(stream)))
         return out
 
