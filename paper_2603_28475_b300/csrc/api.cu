@@ -19,6 +19,8 @@ __global__ void debug_eval_kernel(const __grid_constant__ Dev D, float alpha, do
 __global__ void broadphase_kernel(const __grid_constant__ Dev D, int pad, const float* x, const float* y, double r, int* out, int cap,
                                   int* count);
 __global__ void markers_kernel(const __grid_constant__ Dev D, float* out);
+size_t shared_bytes();
+cudaError_t configure_kernels();
 }  // namespace tac
 
 using namespace tac;
@@ -466,8 +468,9 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     D.status = nullptr; D.iters = nullptr;
     D.budget_ns = 20ull * 1000000000ull;
     int nsm = 0, occ = 0;
+    CUDA_TRY(configure_kernels());
     CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device));
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, solve_kernel, kThreads, 0));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, solve_kernel, kThreads, shared_bytes()));
     b->grid = std::max(1, std::min(n_pads, nsm * std::max(1, occ)));
     CUDA_TRY(cudaStreamSynchronize(st));
     *out = b;
@@ -514,7 +517,7 @@ int tac_step(tac_handle h, int* pad_status_dev, int* iters_dev, void* stream) {
     D.status = pad_status_dev;
     D.iters = iters_dev;
     CUDA_TRY(cudaMemsetAsync(D.queue, 0, sizeof(int), st));
-    solve_kernel<<<h->grid, kThreads, 0, st>>>(D);
+    solve_kernel<<<h->grid, kThreads, shared_bytes(), st>>>(D);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaMemcpyAsync(h->d_pose_t, h->d_pose_n, 6 * (size_t)h->n_pads * 4, cudaMemcpyDeviceToDevice, st));
     return TAC_OK;
@@ -568,7 +571,7 @@ int tac_broadphase(tac_handle h, int pad, const float* x_dev, const float* y_dev
     if (!h || pad < 0 || pad >= h->n_pads || !x_dev || !y_dev || !pairs_out_dev || !count_dev || capacity < 0 ||
         !(r >= 0))
         return fail(TAC_ERR_INVALID_ARG, "invalid argument");
-    broadphase_kernel<<<1, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(h->dev, pad, x_dev, y_dev, r,
+    broadphase_kernel<<<1, kThreads, shared_bytes(), static_cast<cudaStream_t>(stream)>>>(h->dev, pad, x_dev, y_dev, r,
                                                                              pairs_out_dev, capacity, count_dev);
     CUDA_TRY(cudaGetLastError());
     return TAC_OK;
@@ -583,7 +586,7 @@ int tac_debug_eval(tac_handle h, const float* u_dev, const float* p_dev, float a
     copy_aos_to_soa<<<nb, 256, 0, st>>>(p_dev, h->dev.p, h->Vt);
     CUDA_TRY(cudaMemsetAsync(h->dev.vel, 0, 3 * (size_t)h->Vt * 4, st));
     double r = 2.0 * (double)h->hpad[0].dhat;
-    debug_eval_kernel<<<h->n_pads, kThreads, 0, st>>>(h->dev, alpha, r, grad_dev, blk_dev, scal_dev);
+    debug_eval_kernel<<<h->n_pads, kThreads, shared_bytes(), st>>>(h->dev, alpha, r, grad_dev, blk_dev, scal_dev);
     CUDA_TRY(cudaGetLastError());
     return TAC_OK;
 }

@@ -33,9 +33,18 @@ constexpr float kFloat32Floor = 256.0f / 16777216.0f;
 // ---------------------------------------------------------------------------
 // shared memory of one CTA
 
+// raw data of one tet patch, copied asynchronously from global memory
+struct PatchStage {
+    float B[9][kThreads];       // Dm^-1 entries of the patch's tets
+    uint32_t lc[kThreads];      // 4 x 8-bit local vertex ids
+    uint2 sl[kThreads];         // 4 x 16-bit corner slots
+    float uh[3][kThreads];      // displacement (hi) of the patch's vertices
+    float ul[3][kThreads];      // displacement (lo)
+    float p[3][kThreads];       // direction
+};
+
 struct Shared {
-    float su[3][kThreads];
-    float sp[3][kThreads];
+    PatchStage st[2];           // double buffer: patch k+1 loads while k computes
     float stg[9][kStage];
     double rd[kWarps][8];
     float rf[kWarps][4];
@@ -47,8 +56,21 @@ struct Shared {
     int expired;
 };
 
-// one CTA-wide scratch object, visible to every device function of the file
-__shared__ Shared S;
+// one CTA-wide scratch object (dynamic shared memory, sizeof(Shared) bytes at
+// every launch), visible to every device function of the file
+extern __shared__ __align__(16) unsigned char tac_smem[];
+#define S (*reinterpret_cast<Shared*>(tac_smem))
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -303,53 +325,90 @@ struct TetOut {
     float fmax;       // largest per-corner force component (pass 1)
 };
 
-// Loads the patch's local vertices: su = patch-relative displacement at
-// u + alpha p, sp = p.
-__device__ __forceinline__ void load_patch(const Dev& D, const PadDev& P, const MeshDev& M, int vb, int nv,
-                                           float alpha) {
-    int ref = D.pvert[M.pvert_off + vb] & ((1 << 29) - 1);
-    int tid = threadIdx.x;
-    if (tid < nv) {
-        int gv = D.pvert[M.pvert_off + vb + tid] & ((1 << 29) - 1);
+struct PatchHdr {
+    int tb, vb, nt, nv, cb;
+};
+
+__device__ __forceinline__ PatchHdr patch_hdr(const Dev& D, const MeshDev& M, int pi) {
+    int4 ph = __ldg(D.patch + M.patch_off + pi);
+    return PatchHdr{ph.x, ph.y, ph.z & 0xffff, ph.z >> 16, ph.w};
+}
+
+// this thread's entry of the patch's vertex list (mesh vertex id | flags)
+__device__ __forceinline__ int patch_vertex(const Dev& D, const MeshDev& M, const PatchHdr& h) {
+    return threadIdx.x < h.nv ? __ldg(D.pvert + M.pvert_off + h.vb + threadIdx.x) : 0;
+}
+
+// asynchronous copy of one patch (tet data and raw vertex data) into a stage
+__device__ __forceinline__ void issue_patch(const Dev& D, const PadDev& P, const MeshDev& M, const PatchHdr& h,
+                                            int gvf, PatchStage& st) {
+    const int tid = threadIdx.x;
+    if (tid < h.nt) {
+        size_t t = (size_t)M.tet_off + h.tb + tid;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) cp_async4(&st.B[e][tid], D.B + (size_t)e * D.Tt + t);
+        cp_async4(&st.lc[tid], D.lconn + t);
+        cp_async8(&st.sl[tid], D.slot + t);
+    }
+    if (tid < h.nv) {
+        int si = P.v_off + (gvf & ((1 << 29) - 1));
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            int si = c * D.Vt + P.v_off + gv, sr = c * D.Vt + P.v_off + ref;
-            float pv = D.p[si];
-            S.su[c][tid] = ((D.uh[si] - D.uh[sr]) + (D.ul[si] - D.ul[sr])) + alpha * pv;
-            S.sp[c][tid] = pv;
+            cp_async4(&st.uh[c][tid], D.uh + (size_t)c * D.Vt + si);
+            cp_async4(&st.ul[c][tid], D.ul + (size_t)c * D.Vt + si);
+            cp_async4(&st.p[c][tid], D.p + (size_t)c * D.Vt + si);
         }
     }
+    cp_async_commit();
 }
 
 // pass 0: p^T H_e p at u; pass 1: gradient, diagonal blocks and remainder at
-// u + alpha p, scattered into g[gb], blk[gb].
+// u + alpha p, scattered into g[gb], blk[gb]. Patches stream through a
+// double-buffered stage: the copies of patch k+1 are in flight while patch k
+// is computed and its vertices are reduced.
 template <int PASS>
 __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, int gb) {
     TetOut out{0.0, 0, 0.f};
     const int tid = threadIdx.x;
     const float mu = P.mu, lam = P.lam, h2 = P.h * P.h;
-    for (int pi = 0; pi < M.n_patch; ++pi) {
-        int4 ph = D.patch[M.patch_off + pi];
-        int tb = ph.x, vb = ph.y, nt = ph.z & 0xffff, nv = ph.z >> 16, cb = ph.w;
-        load_patch(D, P, M, vb, nv, alpha);
-        __syncthreads();
-        if (tid < nt) {
-            int t = M.tet_off + tb + tid;
-            uint32_t lc = D.lconn[t];
+    const int np = M.n_patch;
+    PatchHdr hc = patch_hdr(D, M, 0);
+    int gvf_c = patch_vertex(D, M, hc);
+    issue_patch(D, P, M, hc, gvf_c, S.st[0]);
+    int gvf_n = 0;
+    if (np > 1) gvf_n = patch_vertex(D, M, patch_hdr(D, M, 1));
+    for (int pi = 0; pi < np; ++pi) {
+        const int b = pi & 1;
+        cp_async_wait_all();
+        __syncthreads();     // stage b complete; every thread is done with patch pi-1
+        int s0 = 0, s1 = 0;
+        if (PASS == 1 && tid < hc.nv) {
+            s0 = __ldg(D.pcsr + M.pcsr_off + hc.cb + tid);
+            s1 = __ldg(D.pcsr + M.pcsr_off + hc.cb + tid + 1);
+        }
+        int gvf_a = 0;
+        if (pi + 1 < np) {
+            issue_patch(D, P, M, patch_hdr(D, M, pi + 1), gvf_n, S.st[b ^ 1]);
+            if (pi + 2 < np) gvf_a = patch_vertex(D, M, patch_hdr(D, M, pi + 2));
+        }
+        const PatchStage& st = S.st[b];
+        if (tid < hc.nt) {
+            uint32_t lc = st.lc[tid];
             int l0 = lc & 255, l1 = (lc >> 8) & 255, l2 = (lc >> 16) & 255, l3 = lc >> 24;
             float Bm[9];
 #pragma unroll
-            for (int e = 0; e < 9; ++e) Bm[e] = D.B[(size_t)e * D.Tt + t];
+            for (int e = 0; e < 9; ++e) Bm[e] = st.B[e][tid];
             float Du[9], Dp[9];
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
-                float a0 = S.su[r][l0], p0 = S.sp[r][l0];
-                Du[3 * r + 0] = S.su[r][l1] - a0;
-                Du[3 * r + 1] = S.su[r][l2] - a0;
-                Du[3 * r + 2] = S.su[r][l3] - a0;
-                Dp[3 * r + 0] = S.sp[r][l1] - p0;
-                Dp[3 * r + 1] = S.sp[r][l2] - p0;
-                Dp[3 * r + 2] = S.sp[r][l3] - p0;
+                float h0 = st.uh[r][l0], o0 = st.ul[r][l0], p0 = st.p[r][l0];
+                float p1 = st.p[r][l1] - p0, p2 = st.p[r][l2] - p0, p3 = st.p[r][l3] - p0;
+                Dp[3 * r + 0] = p1;
+                Dp[3 * r + 1] = p2;
+                Dp[3 * r + 2] = p3;
+                Du[3 * r + 0] = ((st.uh[r][l1] - h0) + (st.ul[r][l1] - o0)) + alpha * p1;
+                Du[3 * r + 1] = ((st.uh[r][l2] - h0) + (st.ul[r][l2] - o0)) + alpha * p2;
+                Du[3 * r + 2] = ((st.uh[r][l3] - h0) + (st.ul[r][l3] - o0)) + alpha * p3;
             }
             float G[9], dF[9];
 #pragma unroll
@@ -391,55 +450,53 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
                     for (int r = 0; r < 3; ++r)
                         Hc[k][r] = hV * (Pm[3 * r] * Bm[3 * k] + Pm[3 * r + 1] * Bm[3 * k + 1] + Pm[3 * r + 2] * Bm[3 * k + 2]);
                 float coef = fmaxf(mu + lam * (1.0f - f.lnJ), 0.0f) * f.invJ * f.invJ;
-                uint64_t sl = D.slot[t];
+                uint2 slw = st.sl[tid];
+                uint64_t sl = (uint64_t)slw.x | ((uint64_t)slw.y << 32);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    float b[3], fo[3];
+                    float bv[3], fo[3];
                     if (k == 0) {
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
-                            b[c] = -(Bm[c] + Bm[3 + c] + Bm[6 + c]);
+                            bv[c] = -(Bm[c] + Bm[3 + c] + Bm[6 + c]);
                             fo[c] = -(Hc[0][c] + Hc[1][c] + Hc[2][c]);
                         }
                     } else {
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
-                            b[c] = Bm[3 * (k - 1) + c];
+                            bv[c] = Bm[3 * (k - 1) + c];
                             fo[c] = Hc[k - 1][c];
                         }
                     }
                     float cc[3];
 #pragma unroll
-                    for (int r = 0; r < 3; ++r) cc[r] = f.cof[3 * r] * b[0] + f.cof[3 * r + 1] * b[1] + f.cof[3 * r + 2] * b[2];
-                    float bb = mu * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
-                    float cf = coef;
+                    for (int r = 0; r < 3; ++r) cc[r] = f.cof[3 * r] * bv[0] + f.cof[3 * r + 1] * bv[1] + f.cof[3 * r + 2] * bv[2];
+                    float bb = mu * (bv[0] * bv[0] + bv[1] * bv[1] + bv[2] * bv[2]);
                     int slot = (int)((sl >> (16 * k)) & 0xffff);
                     out.fmax = fmaxf(out.fmax, fmaxf(fabsf(fo[0]), fmaxf(fabsf(fo[1]), fabsf(fo[2]))));
                     S.stg[0][slot] = fo[0];
                     S.stg[1][slot] = fo[1];
                     S.stg[2][slot] = fo[2];
-                    S.stg[3][slot] = hV * (bb + cf * cc[0] * cc[0]);
-                    S.stg[4][slot] = hV * (bb + cf * cc[1] * cc[1]);
-                    S.stg[5][slot] = hV * (bb + cf * cc[2] * cc[2]);
-                    S.stg[6][slot] = hV * (cf * cc[0] * cc[1]);
-                    S.stg[7][slot] = hV * (cf * cc[0] * cc[2]);
-                    S.stg[8][slot] = hV * (cf * cc[1] * cc[2]);
+                    S.stg[3][slot] = hV * (bb + coef * cc[0] * cc[0]);
+                    S.stg[4][slot] = hV * (bb + coef * cc[1] * cc[1]);
+                    S.stg[5][slot] = hV * (bb + coef * cc[2] * cc[2]);
+                    S.stg[6][slot] = hV * (coef * cc[0] * cc[1]);
+                    S.stg[7][slot] = hV * (coef * cc[0] * cc[2]);
+                    S.stg[8][slot] = hV * (coef * cc[1] * cc[2]);
                 }
             }
         }
-        __syncthreads();
         if (PASS == 1) {
-            if (tid < nv) {
-                int pv = D.pvert[M.pvert_off + vb + tid];
-                int gv = pv & ((1 << 29) - 1);
-                bool first = (pv & (1 << 30)) != 0;
-                int s0 = D.pcsr[M.pcsr_off + cb + tid], s1 = D.pcsr[M.pcsr_off + cb + tid + 1];
+            __syncthreads();     // every corner of patch pi staged
+            if (tid < hc.nv) {
+                int gv = gvf_c & ((1 << 29) - 1);
+                bool first = (gvf_c & (1 << 30)) != 0;
                 float acc[9];
 #pragma unroll
                 for (int c = 0; c < 9; ++c) acc[c] = 0.f;
-                for (int s = s0; s < s1; ++s)
+                for (int q = s0; q < s1; ++q)
 #pragma unroll
-                    for (int c = 0; c < 9; ++c) acc[c] += S.stg[c][s];
+                    for (int c = 0; c < 9; ++c) acc[c] += S.stg[c][q];
                 int si = P.v_off + gv;
                 float* g = D.g[gb];
                 float* k = D.blk[gb];
@@ -455,9 +512,12 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
                     for (int c = 0; c < 6; ++c) k[c * D.Vt + si] += acc[3 + c];
                 }
             }
-            __syncthreads();
         }
+        if (pi + 1 < np) hc = patch_hdr(D, M, pi + 1);
+        gvf_c = gvf_n;
+        gvf_n = gvf_a;
     }
+    __syncthreads();
     // every thread must see the same totals: the caller branches on them
     double v[2] = {out.acc, (double)out.bad};
     block_sum<2>(v);
@@ -1615,6 +1675,20 @@ __global__ void markers_kernel(const __grid_constant__ Dev D, float* out) {
         }
         out[2 * (P.mk_out + m) + c] = a;
     }
+}
+
+// ---------------------------------------------------------------------------
+// host side: dynamic shared memory of the kernels that use the CTA scratch
+
+size_t shared_bytes() { return sizeof(Shared); }
+
+cudaError_t configure_kernels() {
+    int bytes = (int)sizeof(Shared);
+    cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(debug_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(broadphase_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 }  // namespace tac
