@@ -169,6 +169,38 @@ int tac_set_params(tac_handle h, const tac_params* per_pad, int n);
 int tac_broadphase(tac_handle h, int pad, const float* x_dev, const float* y_dev, double r,
                    int* pairs_out_dev, int capacity, int* count_dev, void* stream);
 
+/* Allocation-free candidate search (the paper has no counterpart; this is
+ * a service for callers of the library). It returns the same candidate set
+ * as tac_broadphase, for callers that cannot allocate device memory: code
+ * running while a stream is being captured into a CUDA graph, real-time or
+ * embedded loops whose memory is fixed before they start, and hosts that
+ * give the library no allocator. It takes no batch handle; the caller
+ * passes every input and output as device arrays, and the call allocates and
+ * frees nothing (no cudaMalloc, cudaFree or library allocator).
+ * Inputs: x_dev gel positions [n*3]; the gel surface primitives in the
+ * canonical order described at tac_broadphase (vertex ids [n_surf_verts],
+ * triangles [n_surf_tris*3], edges [n_surf_edges*2]); y_dev indenter world
+ * vertices [n_ind_verts*3], indenter triangles [n_ind_tris*3] and distinct
+ * sorted edges [n_ind_edges*2]; the inflation radius r. Outputs:
+ * pairs_out_dev [capacity*3] (type, i, j) triples sorted lexicographically,
+ * count_dev the full count (entries beyond capacity are not written).
+ * Scratch: one fixed array of 65536 16-byte slots (1 MiB) built into the
+ * library; every GPU that loads the library holds it until the process
+ * exits. A call needs ceil((n_ind_tris + n_ind_verts + n_ind_edges) / 4) +
+ * capacity slots; a larger request fails with TAC_ERR_INVALID_ARG before any
+ * device work. Each scratch entry a call reads is written earlier by the
+ * same call, so the contents left by the previous call need no clearing.
+ * The first call on a device looks up the device address of the array and
+ * sets the kernel's shared-memory limit: make that first call before any
+ * stream capture. All calls share the one array, so calls whose GPU work
+ * overlaps (different streams or threads on one device) race on it and must
+ * be serialised by the caller. */
+int tac_broadphase_static(const float* x_dev, const int* surf_verts_dev, int n_surf_verts,
+                          const int* surf_tris_dev, int n_surf_tris, const int* surf_edges_dev,
+                          int n_surf_edges, const float* y_dev, int n_ind_verts, const int* ind_tris_dev,
+                          int n_ind_tris, const int* ind_edges_dev, int n_ind_edges, double r,
+                          int* pairs_out_dev, int capacity, int* count_dev, void* stream);
+
 /* Verification entry point: evaluate the pieces of one PNCG iteration for
  * every pad at displacement u (x = X + u) along direction p with the
  * indenter at its current pose, inertia centred at u (xhat = x) and no

@@ -21,6 +21,7 @@ __global__ void broadphase_kernel(const __grid_constant__ Dev D, int pad, const 
 __global__ void markers_kernel(const __grid_constant__ Dev D, float* out);
 size_t shared_bytes();
 cudaError_t configure_kernels();
+void set_last_error(const std::string& msg);
 }  // namespace tac
 
 using namespace tac;
@@ -33,6 +34,12 @@ int fail(int code, const std::string& msg) {
     g_err = msg;
     return code;
 }
+
+}  // namespace
+
+void tac::set_last_error(const std::string& msg) { g_err = msg; }
+
+namespace {
 
 #define CUDA_TRY(call)                                                                         \
     do {                                                                                       \

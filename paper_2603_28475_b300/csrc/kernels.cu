@@ -1678,6 +1678,34 @@ __global__ void markers_kernel(const __grid_constant__ Dev D, float* out) {
 }
 
 // ---------------------------------------------------------------------------
+// allocation-free broad phase: the same candidate search as broadphase_kernel
+// on caller arrays, with its scratch (culled indenter primitives and the
+// staged candidate list) in one fixed array of this file instead of the
+// batch's device memory.
+
+constexpr int kStaticScratchInt4 = 1 << 16;        // 1 MiB per device
+static __device__ __align__(256) int4 g_static_scratch[kStaticScratchInt4];
+
+__global__ void __launch_bounds__(kThreads) broadphase_static_kernel2(const __grid_constant__ Dev D,
+                                                                      const __grid_constant__ MeshDev M,
+                                                                      const __grid_constant__ EnvDev E,
+                                                                      const float* x, const float* y, double r,
+                                                                      int4* scratch, int n_list_int4, int* out,
+                                                                      int cap, int* count) {
+    SrcArrays src{x, y};
+    int* ilist = reinterpret_cast<int*>(scratch);
+    int4* staged = scratch + n_list_int4;
+    int n = bp_build(src, D, M, E, ilist, r, staged, cap);
+    for (int k = threadIdx.x; k < min(n, cap); k += kThreads) {
+        int4 q = staged[k];
+        out[3 * k] = q.x;
+        out[3 * k + 1] = q.y;
+        out[3 * k + 2] = q.z;
+    }
+    if (threadIdx.x == 0) *count = n;
+}
+
+// ---------------------------------------------------------------------------
 // host side: dynamic shared memory of the kernels that use the CTA scratch
 
 size_t shared_bytes() { return sizeof(Shared); }
@@ -1692,3 +1720,94 @@ cudaError_t configure_kernels() {
 }
 
 }  // namespace tac
+
+// ---------------------------------------------------------------------------
+// allocation-free entry point (declared in include/tac.h)
+
+#include <mutex>
+#include <string>
+
+#include "tac.h"
+
+namespace tac {
+void set_last_error(const std::string& msg);   // message returned by tac_last_error (api.cu)
+}
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+void* g_static_ptr[kMaxDevices] = {};      // device address of g_static_scratch, per device
+
+int static_fail(int code, const std::string& m) {
+    tac::set_last_error(m);
+    return code;
+}
+
+}  // namespace
+
+extern "C" int tac_broadphase_static(const float* x_dev, const int* surf_verts_dev, int n_surf_verts,
+                                     const int* surf_tris_dev, int n_surf_tris, const int* surf_edges_dev,
+                                     int n_surf_edges, const float* y_dev, int n_ind_verts,
+                                     const int* ind_tris_dev, int n_ind_tris, const int* ind_edges_dev,
+                                     int n_ind_edges, double r, int* pairs_out_dev, int capacity, int* count_dev,
+                                     void* stream) {
+    using namespace tac;
+    if (!x_dev || !y_dev || !pairs_out_dev || !count_dev || n_surf_verts < 0 || n_surf_tris < 0 ||
+        n_surf_edges < 0 || n_ind_verts <= 0 || n_ind_tris < 0 || n_ind_edges < 0 || capacity < 0 || !(r >= 0) ||
+        (n_surf_verts && !surf_verts_dev) || (n_surf_tris && !surf_tris_dev) || (n_surf_edges && !surf_edges_dev) ||
+        (n_ind_tris && !ind_tris_dev) || (n_ind_edges && !ind_edges_dev))
+        return static_fail(TAC_ERR_INVALID_ARG, "tac_broadphase_static: null pointer or negative size");
+    // scratch: culled indenter primitive ids (rounded up to int4) + staged candidates
+    long long n_list = (long long)n_ind_tris + n_ind_verts + n_ind_edges;
+    long long n_list_int4 = (n_list + 3) / 4;
+    if (n_list_int4 + capacity > kStaticScratchInt4)
+        return static_fail(TAC_ERR_INVALID_ARG,
+                           "tac_broadphase_static: indenter primitives + 4 x capacity exceed the fixed scratch of " +
+                               std::to_string(4 * kStaticScratchInt4) + " ints (1 MiB)");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return static_fail(TAC_ERR_CUDA, "tac_broadphase_static: no usable current device");
+    void* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mutex);
+        if (!g_static_ptr[dev]) {
+            // first call on this device: look up the device address of the
+            // fixed array (the host-side symbol is only a stand-in for it)
+            void* ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+            if (e != cudaSuccess)
+                return static_fail(TAC_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            e = configure_kernels();
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(broadphase_static_kernel2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)shared_bytes());
+            if (e != cudaSuccess)
+                return static_fail(TAC_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+            g_static_ptr[dev] = ptr;
+        }
+        scratch = g_static_ptr[dev];
+    }
+    Dev D{};
+    MeshDev M{};
+    EnvDev E{};
+    M.n_sv = n_surf_verts;
+    M.n_st = n_surf_tris;
+    M.n_se = n_surf_edges;
+    E.n_v = n_ind_verts;
+    E.n_t = n_ind_tris;
+    E.n_e = n_ind_edges;
+    D.sv = surf_verts_dev;
+    D.st = surf_tris_dev;
+    D.se = surf_edges_dev;
+    D.it = ind_tris_dev;
+    D.ie = ind_edges_dev;
+    D.meshes = nullptr;
+    D.envs = nullptr;
+    broadphase_static_kernel2<<<1, kThreads, shared_bytes(), static_cast<cudaStream_t>(stream)>>>(
+        D, M, E, x_dev, y_dev, r, static_cast<int4*>(scratch), (int)n_list_int4, pairs_out_dev, capacity, count_dev);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return static_fail(TAC_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
+    return TAC_OK;
+}

@@ -19,7 +19,8 @@ TAC_OK = 0
 PAD_STATUS = {0: "converged", 1: "maxiter", 2: "nonfinite", 3: "linesearch", 4: "pair_overflow"}
 
 SYMBOLS = ("tac_create_batch", "tac_destroy_batch", "tac_reset", "tac_set_indenter", "tac_step", "tac_markers",
-           "tac_get_state", "tac_set_state", "tac_set_params", "tac_broadphase", "tac_debug_eval", "tac_stats",
+           "tac_get_state", "tac_set_state", "tac_set_params", "tac_broadphase", "tac_broadphase_static",
+           "tac_debug_eval", "tac_stats",
            "tac_pad_norms", "tac_sizes", "tac_last_error")
 
 
@@ -63,6 +64,7 @@ def load_library(path=_LIB_PATH):
         "tac_set_state": [vp, vp, vp, vp],
         "tac_set_params": [vp, ctypes.POINTER(Params), i],
         "tac_broadphase": [vp, i, vp, vp, d, vp, i, vp, vp],
+        "tac_broadphase_static": [vp, vp, i, vp, i, vp, i, vp, i, vp, i, vp, i, d, vp, i, vp, vp],
         "tac_debug_eval": [vp, vp, vp, f, vp, vp, vp, vp],
         "tac_stats": [vp, vp, vp],
         "tac_pad_norms": [vp, vp, vp],
@@ -248,6 +250,26 @@ class TacBatch:
         out = torch.empty(self.n_pads, 16, dtype=torch.int64, device=self.device)
         _check(lib().tac_stats(self._h, _ptr(out), _stream(stream)))
         return out
+
+
+def broadphase_static(x, surf_verts, surf_tris, surf_edges, y, ind_tris, ind_edges, r, capacity=1 << 16,
+                      stream=None):
+    """Allocation-free candidate search (tac_broadphase_static): every array
+    is a caller-owned CUDA tensor; the call allocates nothing itself. The
+    output tensors are created here by torch, outside the library."""
+    dev = x.device
+    i32 = lambda a: torch.as_tensor(a, dtype=torch.int32, device=dev).contiguous()
+    f32 = lambda a: torch.as_tensor(a, dtype=torch.float32, device=dev).contiguous()
+    x, y = f32(x).reshape(-1, 3), f32(y).reshape(-1, 3)
+    sv, st, se = i32(surf_verts).reshape(-1), i32(surf_tris).reshape(-1, 3), i32(surf_edges).reshape(-1, 2)
+    it, ie = i32(ind_tris).reshape(-1, 3), i32(ind_edges).reshape(-1, 2)
+    out = torch.zeros(capacity, 3, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    _check(lib().tac_broadphase_static(_ptr(x), _ptr(sv), sv.numel(), _ptr(st), st.shape[0], _ptr(se), se.shape[0],
+                                       _ptr(y), y.shape[0], _ptr(it), it.shape[0], _ptr(ie), ie.shape[0], float(r),
+                                       _ptr(out), capacity, _ptr(cnt), _stream(stream)))
+    n = int(cnt.item())
+    return out[:min(n, capacity)], n
 
 
 def batch_from_workload(w, tol=1e-6, tol_advance=1e-2, max_iter=10000, precond=0, pair_capacity=0,
