@@ -142,6 +142,27 @@ int tac_set_indenter(tac_handle h, const float* pose6_dev, const float* twist6_d
  * v = (x - x^t) / h and the current pose becomes the target pose. */
 int tac_step(tac_handle h, int* pad_status_dev, int* iters_dev, void* stream);
 
+/* Adjoint of the last frame (north star "Differentiation"; the paper itself
+ * calibrates with gradient-free CMA-ES, Sec. 4). At the frame's equilibrium
+ * x* the gradient g vanishes on the free DOFs, so for a loss L of the
+ * markers dL/dtheta = -lambda^T dg/dtheta with H lambda = dL/dx, H the exact
+ * Hessian (mass + elastic + barrier + lagged friction). lambda is found by
+ * block-Jacobi preconditioned CG with a matrix-free Hessian-vector product,
+ * stopped at |r| <= tol |dL/dx| or max_iter iterations.
+ * dL_dmarkers_dev: device [total_markers*2] float, dL/d(u_x, u_y) per marker
+ *   in the layout of tac_markers.
+ * dL_dtheta_dev: device [n_pads*9] double, per pad d L / d(Lame lambda,
+ *   Lame mu, friction mu_f, rotation vector (3), translation (3)) of the
+ *   indenter pose the frame ended at. kappa, eps_v, the frame's start state
+ *   (x^t, v^t), its start pose and its friction lag are held fixed.
+ * status_dev / iters_dev: device [n_pads] int (0 converged, 1 iteration cap,
+ *   2 non-positive curvature d^T H d, 3 non-finite), PCG iterations; either
+ *   may be NULL.
+ * Must follow the tac_step whose frame is differentiated, with no other
+ * state-changing call in between. */
+int tac_adjoint(tac_handle h, const float* dL_dmarkers_dev, double* dL_dtheta_dev, int* status_dev,
+                int* iters_dev, int max_iter, float tol, void* stream);
+
 /* Marker displacement field (u_x, u_y) per marker of every pad, in pad order:
  * out_dev: device [sum_p n_markers(p) * 2] float (Sec. 3.2). */
 int tac_markers(tac_handle h, float* out_dev, void* stream);
@@ -154,6 +175,10 @@ int tac_set_state(tac_handle h, const float* x_dev, const float* v_dev, void* st
 
 /* Replace the material / solver parameters of all pads (host [n_pads]). */
 int tac_set_params(tac_handle h, const tac_params* per_pad, int n);
+
+/* The parameters in effect per pad (host [n]): as last set, with kappa and
+ * eps_v resolved to the values the solve uses (their defaults filled in). */
+int tac_get_params(tac_handle h, tac_params* per_pad, int n);
 
 /* Candidate contact set (the set C of Eq. ipc_energy) of one pad for given
  * positions: every (type, i, j) whose gel-primitive AABB inflated by r

@@ -19,6 +19,8 @@ __global__ void debug_eval_kernel(const __grid_constant__ Dev D, float alpha, do
 __global__ void broadphase_kernel(const __grid_constant__ Dev D, int pad, const float* x, const float* y, double r, int* out, int cap,
                                   int* count);
 __global__ void markers_kernel(const __grid_constant__ Dev D, float* out);
+__global__ void adjoint_kernel(const __grid_constant__ Dev D, const float* dLdm, double* out, int* status, int* iters,
+                               int max_iter, float tol);
 size_t shared_bytes();
 cudaError_t configure_kernels();
 void set_last_error(const std::string& msg);
@@ -368,6 +370,9 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     int* ilist = dalloc<int>(K, il, rc);
     long long* stats = dalloc<long long>(K, 16 * (size_t)n_pads, rc);
     double* norms = dalloc<double>(K, 4 * (size_t)n_pads, rc);
+    int* pad_nlag = dalloc<int>(K, n_pads, rc);
+    float* adj_x = dalloc<float>(K, 3 * (size_t)Vt, rc);
+    float* adj_r = dalloc<float>(K, 3 * (size_t)Vt, rc);
     int* queue = dalloc<int>(K, 1, rc);
     int* order_d = dalloc<int>(K, n_pads, rc);
     b->d_meshes = dalloc<MeshDev>(K, b->hmesh.size(), rc);
@@ -457,6 +462,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)Vt * 4, st));
     CUDA_TRY(cudaMemsetAsync(stats, 0, 16 * (size_t)n_pads * 8, st));
     CUDA_TRY(cudaMemsetAsync(norms, 0, 4 * (size_t)n_pads * 8, st));
+    CUDA_TRY(cudaMemsetAsync(pad_nlag, 0, (size_t)n_pads * 4, st));
     CUDA_TRY(cudaMemsetAsync(b->d_pose_t, 0, 6 * (size_t)n_pads * 4, st));
     CUDA_TRY(cudaMemsetAsync(b->d_pose_n, 0, 6 * (size_t)n_pads * 4, st));
     D.meshes = b->d_meshes;
@@ -472,6 +478,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     D.g[0] = g0; D.g[1] = g1; D.blk[0] = k0; D.blk[1] = k1;
     D.pairs = pairs; D.lag = lag; D.slotbuf = slotbuf; D.ent = ent; D.cvl = cvl; D.cvo = cvo; D.cnt = cnt;
     D.ilist = ilist; D.stats = stats; D.norms = norms; D.queue = queue;
+    D.pad_nlag = pad_nlag; D.adj_x = adj_x; D.adj_r = adj_r;
     D.status = nullptr; D.iters = nullptr;
     D.budget_ns = 20ull * 1000000000ull;
     int nsm = 0, occ = 0;
@@ -573,6 +580,16 @@ int tac_set_params(tac_handle h, const tac_params* per_pad, int n) {
     return TAC_OK;
 }
 
+int tac_get_params(tac_handle h, tac_params* per_pad, int n) {
+    if (!h || !per_pad || n != h->n_pads) return fail(TAC_ERR_INVALID_ARG, "need n_pads parameter slots");
+    for (int p = 0; p < n; ++p) {
+        per_pad[p] = h->params[p];
+        per_pad[p].kappa = h->hpad[p].kappa;
+        per_pad[p].eps_v = h->hpad[p].eps_v;
+    }
+    return TAC_OK;
+}
+
 int tac_broadphase(tac_handle h, int pad, const float* x_dev, const float* y_dev, double r, int* pairs_out_dev,
                    int capacity, int* count_dev, void* stream) {
     if (!h || pad < 0 || pad >= h->n_pads || !x_dev || !y_dev || !pairs_out_dev || !count_dev || capacity < 0 ||
@@ -602,6 +619,16 @@ int tac_stats(tac_handle h, long long* stats_dev, void* stream) {
     if (!h || !stats_dev) return fail(TAC_ERR_INVALID_ARG, "null argument");
     CUDA_TRY(cudaMemcpyAsync(stats_dev, h->dev.stats, 16 * (size_t)h->n_pads * 8, cudaMemcpyDeviceToDevice,
                              static_cast<cudaStream_t>(stream)));
+    return TAC_OK;
+}
+
+int tac_adjoint(tac_handle h, const float* dL_dmarkers_dev, double* dL_dtheta_dev, int* status_dev, int* iters_dev,
+                int max_iter, float tol, void* stream) {
+    if (!h || !dL_dmarkers_dev || !dL_dtheta_dev || max_iter < 0 || !(tol > 0))
+        return fail(TAC_ERR_INVALID_ARG, "invalid argument");
+    adjoint_kernel<<<h->n_pads, kThreads, shared_bytes(), static_cast<cudaStream_t>(stream)>>>(
+        h->dev, dL_dmarkers_dev, dL_dtheta_dev, status_dev, iters_dev, max_iter, tol);
+    CUDA_TRY(cudaGetLastError());
     return TAC_OK;
 }
 

@@ -295,6 +295,51 @@ __device__ __forceinline__ void feat_dir_derivs(const Feature<double>& f, const 
     d2 = (D2 - 2.0 * d1 * d1) / (2.0 * f.d);
 }
 
+// Action of the distance Hessian on slot directions dl (same sensitivity):
+// the optimal free parameters move by thd = -(J^T J)^-1 b, the closest-point
+// vector by rt = rdot + sum_k thd_k J_k, and per slot
+//   (grad^2 d . dl)_s = (sum_k thd_k e_ks) rhat + w_s (I - rhat rhat^T) rt / d.
+// Also returns d1 = rhat . rdot and rhat.
+__device__ __forceinline__ void feat_hess_vec(const Feature<double>& f, const V3<double> X[4], const V3<double> dl[4],
+                                              double& d1, V3<double> hv[4], V3<double>& rh) {
+    V3<double> r = feat_r(f, X);
+    rh = (1.0 / f.d) * r;
+    V3<double> rd = {0, 0, 0};
+#pragma unroll
+    for (int s = 0; s < 4; ++s) rd = rd + f.w[s] * dl[s];
+    double thd[2] = {0.0, 0.0};
+    V3<double> J[2] = {{0, 0, 0}, {0, 0, 0}};
+    if (f.nf > 0) {
+        V3<double> Gk[2];
+        double bk[2];
+        for (int k = 0; k < f.nf; ++k) {
+            Gk[k] = {0, 0, 0};
+            for (int s = 0; s < 4; ++s) {
+                J[k] = J[k] + f.e[k][s] * X[s];
+                Gk[k] = Gk[k] + f.e[k][s] * dl[s];
+            }
+            bk[k] = dot(Gk[k], r) + dot(J[k], rd);
+        }
+        if (f.nf == 1) {
+            double m = dot(J[0], J[0]);
+            if (m > 0) thd[0] = -bk[0] / m;
+        } else {
+            double m00 = dot(J[0], J[0]), m01 = dot(J[0], J[1]), m11 = dot(J[1], J[1]);
+            double det = m00 * m11 - m01 * m01;
+            if (det > 0) {
+                thd[0] = -(m11 * bk[0] - m01 * bk[1]) / det;
+                thd[1] = -(m00 * bk[1] - m01 * bk[0]) / det;
+            }
+        }
+    }
+    V3<double> rt = rd + thd[0] * J[0] + thd[1] * J[1];
+    V3<double> tang = rt - dot(rh, rt) * rh;
+    double inv = 1.0 / f.d;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) hv[s] = (thd[0] * f.e[0][s] + thd[1] * f.e[1][s]) * rh + (f.w[s] * inv) * tang;
+    d1 = dot(rh, rd);
+}
+
 // ---------------------------------------------------------------------------
 // Friction mollifier f(s) of Eq. (friction_mollifier) and helpers.
 

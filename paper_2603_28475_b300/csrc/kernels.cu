@@ -320,9 +320,10 @@ __device__ __forceinline__ double pair_distance(const Dev& D, const PadDev& P, c
 // tet passes
 
 struct TetOut {
-    double acc;       // p^T H_e p (pass 0) or remainder R' (pass 1)
+    double acc;       // p^T H_e p (pass 0), remainder R' (pass 1), lambda-sensitivity (pass 3)
     int bad;          // trial state inverted a tet
     float fmax;       // largest per-corner force component (pass 1)
+    double acc2;      // mu-sensitivity (pass 3)
 };
 
 struct PatchHdr {
@@ -368,7 +369,7 @@ __device__ __forceinline__ void issue_patch(const Dev& D, const PadDev& P, const
 // is computed and its vertices are reduced.
 template <int PASS>
 __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, int gb) {
-    TetOut out{0.0, 0, 0.f};
+    TetOut out{0.0, 0, 0.f, 0.0};
     const int tid = threadIdx.x;
     const float mu = P.mu, lam = P.lam, h2 = P.h * P.h;
     const int np = M.n_patch;
@@ -382,7 +383,7 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
         cp_async_wait_all();
         __syncthreads();     // stage b complete; every thread is done with patch pi-1
         int s0 = 0, s1 = 0;
-        if (PASS == 1 && tid < hc.nv) {
+        if ((PASS == 1 || PASS == 2) && tid < hc.nv) {
             s0 = __ldg(D.pcsr + M.pcsr_off + hc.cb + tid);
             s1 = __ldg(D.pcsr + M.pcsr_off + hc.cb + tid + 1);
         }
@@ -429,6 +430,49 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
             AInv ai = a_invariants(f, dF);
             if (PASS == 0) {
                 out.acc += (double)(hV * (mu * dF2 + (mu - lam * f.lnJ) * ai.trA2 + lam * ai.c1 * ai.c1));
+            } else if (PASS == 3) {
+                // direction dF = D_lambda Dm^-1: dP/dlam : dF = ln J tr(F^-1 dF),
+                // dP/dmu : dF = (F - F^-T) : dF = tr dF + G : dF - tr(F^-1 dF)
+                float GdF = 0.f;
+#pragma unroll
+                for (int e = 0; e < 9; ++e) GdF += G[e] * dF[e];
+                out.acc += (double)(hV * f.lnJ * ai.c1);
+                out.acc2 += (double)(hV * ((dF[0] + dF[4] + dF[8]) + GdF - ai.c1));
+            } else if (PASS == 2) {
+                // dP = mu dF + (mu - lam ln J) F^-T dF^T F^-T + lam tr(F^-1 dF) F^-T
+                float C[9];
+#pragma unroll
+                for (int e = 0; e < 9; ++e) C[e] = f.cof[e] * f.invJ;
+                float M1[9];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int l = 0; l < 3; ++l)
+                        M1[3 * i + l] = C[3 * i] * dF[3 * l] + C[3 * i + 1] * dF[3 * l + 1] + C[3 * i + 2] * dF[3 * l + 2];
+                float a2 = mu - lam * f.lnJ, a3 = lam * ai.c1;
+                float dP[9];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+                        dP[3 * i + j] = mu * dF[3 * i + j] +
+                                        a2 * (M1[3 * i] * C[j] + M1[3 * i + 1] * C[3 + j] + M1[3 * i + 2] * C[6 + j]) +
+                                        a3 * C[3 * i + j];
+                float Hc[3][3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+                        Hc[k][r] = hV * (dP[3 * r] * Bm[3 * k] + dP[3 * r + 1] * Bm[3 * k + 1] + dP[3 * r + 2] * Bm[3 * k + 2]);
+                uint2 slw = st.sl[tid];
+                uint64_t sl = (uint64_t)slw.x | ((uint64_t)slw.y << 32);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    int slot = (int)((sl >> (16 * k)) & 0xffff);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        S.stg[c][slot] = (k == 0) ? -(Hc[0][c] + Hc[1][c] + Hc[2][c]) : Hc[k - 1][c];
+                }
             } else {
                 if (!(f.J > 0.0f)) out.bad = 1;
                 // remainder of the line expanded at the trial point (step -alpha)
@@ -486,6 +530,26 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
                 }
             }
         }
+        if (PASS == 2) {
+            __syncthreads();     // every corner of patch pi staged
+            if (tid < hc.nv) {
+                int gv = gvf_c & ((1 << 29) - 1);
+                bool first = (gvf_c & (1 << 30)) != 0;
+                float acc[3] = {0.f, 0.f, 0.f};
+                for (int q = s0; q < s1; ++q)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) acc[c] += S.stg[c][q];
+                float* g = D.g[gb];
+                int si = P.v_off + gv;
+                if (first) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) g[c * D.Vt + si] = acc[c];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) g[c * D.Vt + si] += acc[c];
+                }
+            }
+        }
         if (PASS == 1) {
             __syncthreads();     // every corner of patch pi staged
             if (tid < hc.nv) {
@@ -519,10 +583,11 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
     }
     __syncthreads();
     // every thread must see the same totals: the caller branches on them
-    double v[2] = {out.acc, (double)out.bad};
-    block_sum<2>(v);
+    double v[3] = {out.acc, (double)out.bad, out.acc2};
+    block_sum<3>(v);
     out.acc = v[0];
     out.bad = v[1] > 0.0 ? 1 : 0;
+    out.acc2 = v[2];
     float fm[1] = {out.fmax};
     block_max_f<1>(fm);
     out.fmax = fm[0];
@@ -1057,16 +1122,27 @@ __device__ __noinline__ int lag_build(const Dev& D, const PadDev& P, const MeshD
                 L.n[2] = (float)(r.z * inv);
                 L.lam = -kap * barrier_b1(f.d, dh);
                 double dY[3] = {0, 0, 0};
+                int ni = 0;
+                for (int q = 0; q < 3; ++q) {
+                    L.iv[q] = -1;
+                    L.iw[q] = 0.f;
+                }
                 for (int sl = 0; sl < 4; ++sl) {
                     if (sl < 3) {
                         L.g[sl] = gsl[sl];          // mesh-local vertex id or -1
                         L.w[sl] = gsl[sl] >= 0 ? (float)f.w[sl] : 0.f;
                     }
-                    if (isl[sl] >= 0)
+                    if (isl[sl] >= 0) {
 #pragma unroll
                         for (int c = 0; c < 3; ++c)
                             dY[c] += -f.w[sl] * ((double)D.Yn[3 * (P.yw_off + isl[sl]) + c] -
                                                  (double)D.Yt[3 * (P.yw_off + isl[sl]) + c]);
+                        if (ni < 3) {
+                            L.iv[ni] = isl[sl];
+                            L.iw[ni] = (float)(-f.w[sl]);
+                            ++ni;
+                        }
+                    }
                 }
                 L.dY[0] = (float)dY[0];
                 L.dY[1] = (float)dY[1];
@@ -1541,6 +1617,7 @@ __device__ void solve_pad(const Dev& D, int pad) {
         st[15] = (long long)(global_ns() - t0);
         double* nr = D.norms + 4 * pad;
         nr[0] = ginf; nr[1] = target; nr[2] = g_ref; nr[3] = fmax;
+        D.pad_nlag[pad] = cc.nlag;
     }
     __syncthreads();
 }
@@ -1678,6 +1755,400 @@ __global__ void markers_kernel(const __grid_constant__ Dev D, float* out) {
 }
 
 // ---------------------------------------------------------------------------
+// adjoint of a frame's equilibrium: H lambda = dL/dx by block-Jacobi PCG with
+// a matrix-free Hessian-vector product, then dL/dtheta = -lambda^T dg/dtheta
+
+// exact Hessian action of the barrier and lagged friction on the direction
+// in p, written as slot values (3 force components, zero blocks)
+__device__ __noinline__ void pair_hvp(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np, int nl,
+                                      double s) {
+    const int4* pr = D.pairs + P.pair_off;
+    float* sb = D.slotbuf + (size_t)9 * 6 * P.pair_off;
+    const double dh = P.dhat, kap = P.kappa;
+    for (int k = threadIdx.x; k < np; k += kThreads) {
+        int gsl[4], isl[4];
+        int4 q = pr[k];
+        pair_slots(D, M, E, q, gsl, isl);
+        float out[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        V3<float> Xf[4];
+        load_slots<float>(D, P, M, gsl, isl, 0.0f, s, Xf);
+        if ((double)pair_feature<float>(q.x, Xf).d <= 2.0 * dh) {
+            V3<double> X[4], dl[4];
+            load_slots<double>(D, P, M, gsl, isl, 0.0f, s, X);
+            Feature<double> f = pair_feature<double>(q.x, X);
+            if (f.d < dh && f.d > 0.0) {
+#pragma unroll
+                for (int sl = 0; sl < 4; ++sl) {
+                    if (gsl[sl] >= 0) {
+                        int si = P.v_off + gsl[sl];
+                        dl[sl] = {D.p[si], D.p[D.Vt + si], D.p[2 * D.Vt + si]};
+                    } else {
+                        dl[sl] = {0.0, 0.0, 0.0};
+                    }
+                }
+                double d1;
+                V3<double> hv[4], rh;
+                feat_hess_vec(f, X, dl, d1, hv, rh);
+                double b1 = kap * barrier_b1(f.d, dh), b2 = kap * barrier_b2(f.d, dh);
+#pragma unroll
+                for (int sl = 0; sl < 3; ++sl)
+                    if (gsl[sl] >= 0) {
+                        double a = b2 * d1 * f.w[sl];
+                        out[sl][0] = (float)(a * rh.x + b1 * hv[sl].x);
+                        out[sl][1] = (float)(a * rh.y + b1 * hv[sl].y);
+                        out[sl][2] = (float)(a * rh.z + b1 * hv[sl].z);
+                    }
+            }
+        }
+#pragma unroll
+        for (int sl = 0; sl < 3; ++sl)
+            if (gsl[sl] >= 0) {
+                float* e = sb + 9 * (3 * k + sl);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) e[c] = out[sl][c];
+#pragma unroll
+                for (int c = 3; c < 9; ++c) e[c] = 0.f;
+            }
+    }
+    const LagRec* lg = D.lag + P.pair_off;
+    for (int l = threadIdx.x; l < nl; l += kThreads) {
+        const LagRec& L = lg[l];
+        double Dl[3] = {-s * L.dY[0], -s * L.dY[1], -s * L.dY[2]}, pd[3] = {0, 0, 0};
+        for (int gs = 0; gs < 3; ++gs)
+            if (L.g[gs] >= 0) {
+                int si = P.v_off + L.g[gs];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    int sc = c * D.Vt + si;
+                    Dl[c] += (double)L.w[gs] * (double)((D.uh[sc] - D.u0h[sc]) + (D.ul[sc] - D.u0l[sc]));
+                    pd[c] += (double)L.w[gs] * (double)D.p[sc];
+                }
+            }
+        double nD = L.n[0] * Dl[0] + L.n[1] * Dl[1] + L.n[2] * Dl[2];
+        double tD[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) tD[c] = Dl[c] - L.n[c] * nD;
+        double sv = sqrt(tD[0] * tD[0] + tD[1] * tD[1] + tD[2] * tD[2]);
+        double eps = P.eps_v, cf = (double)P.mu_f * L.lam;
+        double f1s = moll_f1_over_s(sv, eps), cs = moll_c(sv, eps);
+        double uu[3] = {0, 0, 0};
+        if (sv > 0)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) uu[c] = tD[c] / sv;
+        double npd = L.n[0] * pd[0] + L.n[1] * pd[1] + L.n[2] * pd[2];
+        double upd = uu[0] * pd[0] + uu[1] * pd[1] + uu[2] * pd[2];
+        double Hp[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Hp[c] = f1s * (pd[c] - L.n[c] * npd) - cs * uu[c] * upd;
+        for (int gs = 0; gs < 3; ++gs)
+            if (L.g[gs] >= 0) {
+                float* e = sb + 9 * (3 * (P.pair_cap + l) + gs);
+                double a = cf * L.w[gs];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) e[c] = (float)(a * Hp[c]);
+#pragma unroll
+                for (int c = 3; c < 9; ++c) e[c] = 0.f;
+            }
+    }
+    __syncthreads();
+}
+
+// dR(r)/dr_m of the rotation vector r (derivative of the Rodrigues formula)
+__device__ void rotation_jacobian(const float* pose, double dR[3][9]) {
+    double r[3] = {pose[0], pose[1], pose[2]};
+    double th2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    double R[9];
+    rotation(pose, R);
+    for (int m = 0; m < 3; ++m) {
+        double K[9];
+        if (th2 < 1e-16) {
+            double e[3] = {0, 0, 0};
+            e[m] = 1.0;
+            double Km[9] = {0, -e[2], e[1], e[2], 0, -e[0], -e[1], e[0], 0};
+            for (int q = 0; q < 9; ++q) dR[m][q] = Km[q];
+            continue;
+        }
+        // v = r x ((I - R) e_m); K = (r_m [r]x + [v]x) / |r|^2; dR_m = K R
+        double c[3] = {-R[m], -R[3 + m], -R[6 + m]};
+        c[m] += 1.0;
+        double v[3] = {r[1] * c[2] - r[2] * c[1], r[2] * c[0] - r[0] * c[2], r[0] * c[1] - r[1] * c[0]};
+        double a[3] = {r[m] * r[0] + v[0], r[m] * r[1] + v[1], r[m] * r[2] + v[2]};
+        double Kx[9] = {0, -a[2], a[1], a[2], 0, -a[0], -a[1], a[0], 0};
+        for (int q = 0; q < 9; ++q) K[q] = Kx[q] / th2;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                dR[m][3 * i + j] = K[3 * i] * R[j] + K[3 * i + 1] * R[3 + j] + K[3 * i + 2] * R[6 + j];
+    }
+}
+
+// lambda (in p) against dg/dtheta of the contact terms: out[0] the friction
+// coefficient, out[1..6] the end pose (rotation vector, translation) through
+// the mixed gel / indenter second derivatives
+__device__ __noinline__ void pair_theta(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np,
+                                        int nl, const double dR[3][9], double out7[7]) {
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    const int4* pr = D.pairs + P.pair_off;
+    const double dh = P.dhat, kap = P.kappa;
+    auto dy_of = [&](int j, int m) -> V3<double> {
+        if (m >= 3) {
+            V3<double> e = {0, 0, 0};
+            if (m == 3) e.x = 1.0;
+            else if (m == 4) e.y = 1.0;
+            else e.z = 1.0;
+            return e;
+        }
+        const float* y = D.Y + 3 * (E.y_off + j);
+        const double* A = dR[m];
+        return V3<double>{A[0] * y[0] + A[1] * y[1] + A[2] * y[2], A[3] * y[0] + A[4] * y[1] + A[5] * y[2],
+                          A[6] * y[0] + A[7] * y[1] + A[8] * y[2]};
+    };
+    for (int k = threadIdx.x; k < np; k += kThreads) {
+        int gsl[4], isl[4];
+        int4 q = pr[k];
+        pair_slots(D, M, E, q, gsl, isl);
+        V3<float> Xf[4];
+        load_slots<float>(D, P, M, gsl, isl, 0.0f, 1.0, Xf);
+        if ((double)pair_feature<float>(q.x, Xf).d > 2.0 * dh) continue;
+        V3<double> X[4];
+        load_slots<double>(D, P, M, gsl, isl, 0.0f, 1.0, X);
+        Feature<double> f = pair_feature<double>(q.x, X);
+        if (!(f.d < dh && f.d > 0.0)) continue;
+        double b1 = kap * barrier_b1(f.d, dh), b2 = kap * barrier_b2(f.d, dh);
+        V3<double> dl[4], dlam[4];
+#pragma unroll
+        for (int sl = 0; sl < 4; ++sl) {
+            if (gsl[sl] >= 0) {
+                int si = P.v_off + gsl[sl];
+                dlam[sl] = {D.p[si], D.p[D.Vt + si], D.p[2 * D.Vt + si]};
+            } else {
+                dlam[sl] = {0.0, 0.0, 0.0};
+            }
+        }
+        double d1, d2;
+        feat_dir_derivs(f, X, dlam, d1, d2);
+        double Ql = b2 * d1 * d1 + b1 * d2;
+        for (int m = 0; m < 6; ++m) {
+#pragma unroll
+            for (int sl = 0; sl < 4; ++sl) dl[sl] = isl[sl] >= 0 ? dy_of(isl[sl], m) : V3<double>{0.0, 0.0, 0.0};
+            feat_dir_derivs(f, X, dl, d1, d2);
+            double Qd = b2 * d1 * d1 + b1 * d2;
+#pragma unroll
+            for (int sl = 0; sl < 4; ++sl) dl[sl] = dl[sl] + dlam[sl];
+            feat_dir_derivs(f, X, dl, d1, d2);
+            double Qs = b2 * d1 * d1 + b1 * d2;
+            acc[1 + m] += 0.5 * (Qs - Ql - Qd);
+        }
+    }
+    const LagRec* lg = D.lag + P.pair_off;
+    if (P.mu_f > 0.f)
+        for (int l = threadIdx.x; l < nl; l += kThreads) {
+            const LagRec& L = lg[l];
+            double Dl[3] = {-L.dY[0], -L.dY[1], -L.dY[2]}, pd[3] = {0, 0, 0};
+            for (int gs = 0; gs < 3; ++gs)
+                if (L.g[gs] >= 0) {
+                    int si = P.v_off + L.g[gs];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        int sc = c * D.Vt + si;
+                        Dl[c] += (double)L.w[gs] * (double)((D.uh[sc] - D.u0h[sc]) + (D.ul[sc] - D.u0l[sc]));
+                        pd[c] += (double)L.w[gs] * (double)D.p[sc];
+                    }
+                }
+            double nD = L.n[0] * Dl[0] + L.n[1] * Dl[1] + L.n[2] * Dl[2];
+            double tD[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) tD[c] = Dl[c] - L.n[c] * nD;
+            double sv = sqrt(tD[0] * tD[0] + tD[1] * tD[1] + tD[2] * tD[2]);
+            double eps = P.eps_v, cf = (double)P.mu_f * L.lam;
+            double f1s = moll_f1_over_s(sv, eps), cs = moll_c(sv, eps);
+            acc[0] += L.lam * f1s * (tD[0] * pd[0] + tD[1] * pd[1] + tD[2] * pd[2]);
+            double uu[3] = {0, 0, 0};
+            if (sv > 0)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) uu[c] = tD[c] / sv;
+            for (int m = 0; m < 6; ++m) {
+                V3<double> dy = {0, 0, 0};
+                for (int q = 0; q < 3; ++q)
+                    if (L.iv[q] >= 0) dy = dy + (double)L.iw[q] * dy_of(L.iv[q], m);
+                double a[3] = {dy.x, dy.y, dy.z};
+                double na = L.n[0] * a[0] + L.n[1] * a[1] + L.n[2] * a[2];
+                double ua = uu[0] * a[0] + uu[1] * a[1] + uu[2] * a[2];
+                double Ha = 0.0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Ha += pd[c] * (f1s * (a[c] - L.n[c] * na) - cs * uu[c] * ua);
+                acc[1 + m] -= cf * Ha;
+            }
+        }
+    block_sum<7>(acc);
+#pragma unroll
+    for (int q = 0; q < 7; ++q) out7[q] = acc[q];
+}
+
+// z = P r with P the block-Jacobi inverse of (blk[gp] + m I); returns r.z, r.r
+__device__ __noinline__ void pcg_precond(const Dev& D, const PadDev& P, const MeshDev& M, int gp, double& rz,
+                                         double& rr) {
+    double v[2] = {0.0, 0.0};
+    for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
+        int si = P.v_off + i;
+        if (D.fixed[M.xv_off + i]) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) D.z[c * D.Vt + si] = 0.f;
+            continue;
+        }
+        float m = P.rho * D.vlump[M.xv_off + i];
+        float K[6], Ki[6], r[3], z[3];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) K[c] = D.blk[gp][c * D.Vt + si];
+        K[0] += m; K[1] += m; K[2] += m;
+        if (P.precond == 0) {
+            if (!sym_inverse(K, Ki)) { Ki[0] = Ki[1] = Ki[2] = 1.f / m; Ki[3] = Ki[4] = Ki[5] = 0.f; }
+        } else {
+            Ki[0] = 1.f / K[0]; Ki[1] = 1.f / K[1]; Ki[2] = 1.f / K[2];
+            Ki[3] = Ki[4] = Ki[5] = 0.f;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r[c] = D.adj_r[c * D.Vt + si];
+        sym_apply(Ki, r, z);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            D.z[c * D.Vt + si] = z[c];
+            v[0] += (double)r[c] * (double)z[c];
+            v[1] += (double)r[c] * (double)r[c];
+        }
+    }
+    block_sum<2>(v);
+    rz = v[0];
+    rr = v[1];
+}
+
+// q = H d: completes g[gq] (elastic + contact) with the mass term, zero on
+// Dirichlet vertices; returns d . q
+__device__ __noinline__ double hvp_finish(const Dev& D, const PadDev& P, const MeshDev& M, int gq) {
+    double v[1] = {0.0};
+    for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
+        int si = P.v_off + i;
+        bool fx = D.fixed[M.xv_off + i] != 0;
+        float m = P.rho * D.vlump[M.xv_off + i];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            int sc = c * D.Vt + si;
+            float q = fx ? 0.f : D.g[gq][sc] + m * D.p[sc];
+            D.g[gq][sc] = q;
+            v[0] += (double)q * (double)D.p[sc];
+        }
+    }
+    block_sum<1>(v);
+    return v[0];
+}
+
+// x += alpha d, r -= alpha q (mode 0); d = z + beta d (mode 1); d = z (mode 2)
+__device__ __noinline__ void pcg_vectors(const Dev& D, const PadDev& P, const MeshDev& M, int mode, double ab,
+                                         int gq) {
+    const float a = (float)ab;
+    for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
+        int si = P.v_off + i;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            int sc = c * D.Vt + si;
+            if (mode == 0) {
+                D.adj_x[sc] += a * D.p[sc];
+                D.adj_r[sc] -= a * D.g[gq][sc];
+            } else if (mode == 1) {
+                D.p[sc] = D.z[sc] + a * D.p[sc];
+            } else {
+                D.p[sc] = D.z[sc];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+enum { ADJ_CONVERGED = 0, ADJ_MAXITER = 1, ADJ_BREAKDOWN = 2, ADJ_NONFINITE = 3 };
+
+__global__ void __launch_bounds__(kThreads, 2) adjoint_kernel(const __grid_constant__ Dev D, const float* dLdm,
+                                                              double* out, int* status, int* iters, int max_iter,
+                                                              float tol) {
+    const int pad = blockIdx.x;
+    const PadDev P = D.pads[pad];
+    const MeshDev M = D.meshes[P.mesh];
+    const EnvDev E = D.envs[P.env];
+    if (threadIdx.x == 0) S.flag = 0;
+    __syncthreads();
+    // candidates at the equilibrium with the indenter at the frame's end
+    SrcState src{&D, &P, &M, 1.0f};
+    int n = bp_build(src, D, M, E, D.ilist + P.il_off, (P.dhat + P.dhat) * (1.0 + 1e-6), D.pairs + P.pair_off,
+                     P.pair_cap);
+    ContactCtl cc{min(n, P.pair_cap), D.pad_nlag[pad], 0};
+    csr_build(D, P, M, E, cc);
+    // preconditioner blocks at x* (buffer 0)
+    TetOut t0 = tet_pass<1>(D, P, M, 0.0f, 0);
+    double rem;
+    int bad;
+    pair_trial(D, P, M, E, cc.npairs, cc.nlag, 1.0, 0.0f, rem, bad);
+    contact_gather(D, P, cc, 0);
+    // right-hand side dL/dx (transpose of the marker readout), lambda = 0
+    for (int i = threadIdx.x; i < M.n_v; i += kThreads)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            D.adj_r[c * D.Vt + P.v_off + i] = 0.f;
+            D.adj_x[c * D.Vt + P.v_off + i] = 0.f;
+        }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int m = 0; m < M.n_mk; ++m)
+            for (int k = 0; k < 3; ++k) {
+                int v = D.mk_ids[3 * (M.mk_off + m) + k];
+                float w = D.mk_w[3 * (M.mk_off + m) + k];
+                if (D.fixed[M.xv_off + v]) continue;
+                for (int c = 0; c < 2; ++c)
+                    D.adj_r[c * D.Vt + P.v_off + v] += w * dLdm[2 * (P.mk_out + m) + c];
+            }
+    __syncthreads();
+    double rz, rr;
+    pcg_precond(D, P, M, 0, rz, rr);
+    const double bnorm = sqrt(rr);
+    int st = (t0.bad || bad) ? ADJ_NONFINITE : ADJ_CONVERGED;
+    int it = 0;
+    if (st == ADJ_CONVERGED && bnorm > 0.0) {
+        pcg_vectors(D, P, M, 2, 0.0, 1);
+        st = ADJ_MAXITER;
+        for (it = 0; it < max_iter; ++it) {
+            tet_pass<2>(D, P, M, 0.0f, 1);
+            pair_hvp(D, P, M, E, cc.npairs, cc.nlag, 1.0);
+            contact_gather(D, P, cc, 1);
+            double dq = hvp_finish(D, P, M, 1);
+            if (!(dq > 0.0)) { st = ADJ_BREAKDOWN; break; }
+            double alpha = rz / dq;
+            pcg_vectors(D, P, M, 0, alpha, 1);
+            double rz1;
+            pcg_precond(D, P, M, 0, rz1, rr);
+            if (!isfinite(rr)) { st = ADJ_NONFINITE; break; }
+            if (sqrt(rr) <= (double)tol * bnorm) { st = ADJ_CONVERGED; ++it; break; }
+            pcg_vectors(D, P, M, 1, rz1 / rz, 1);
+            rz = rz1;
+        }
+    }
+    // dL/dtheta = -lambda^T dg/dtheta
+    for (int i = threadIdx.x; i < M.n_v; i += kThreads)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) D.p[c * D.Vt + P.v_off + i] = D.adj_x[c * D.Vt + P.v_off + i];
+    __syncthreads();
+    TetOut t3 = tet_pass<3>(D, P, M, 0.0f, 0);
+    double dR[3][9];
+    rotation_jacobian(D.pose_t + 6 * pad, dR);
+    double c7[7];
+    pair_theta(D, P, M, E, cc.npairs, cc.nlag, dR, c7);
+    if (threadIdx.x == 0) {
+        double* o = out + 9 * pad;
+        o[0] = -t3.acc;
+        o[1] = -t3.acc2;
+        for (int q = 0; q < 7; ++q) o[2 + q] = -c7[q];
+        if (status) status[pad] = st;
+        if (iters) iters[pad] = it;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // allocation-free broad phase: the same candidate search as broadphase_kernel
 // on caller arrays, with its scratch (culled indenter primitives and the
 // staged candidate list) in one fixed array of this file instead of the
@@ -1715,6 +2186,8 @@ cudaError_t configure_kernels() {
     cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(debug_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(broadphase_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }

@@ -47,6 +47,8 @@ struct LagRec {
     float w[3];               // gel slot weights
     float n[3];               // lagged contact normal
     float dY[3];              // indenter closest-point displacement over the frame
+    int iv[3];                // indenter vertex (env-local id) of each indenter slot, -1 if none
+    float iw[3];              // indenter slot weights (>= 0)
     double lam;               // lagged normal force magnitude -kappa b'(d)
 };
 
@@ -100,6 +102,9 @@ struct Dev {
     int* iters;
     long long* stats;         // [n_pads][16] counters and per-phase nanoseconds
     double* norms;            // [n_pads][4] final |g|_inf, stopping target, g_ref, force scale
+    int* pad_nlag;            // [n_pads] lag records of the last frame
+    float* adj_x;             // [3][Vt] adjoint solution lambda
+    float* adj_r;             // [3][Vt] adjoint residual
     int* queue;
     unsigned long long budget_ns;   // wall-clock cap of one pad's frame solve
 };

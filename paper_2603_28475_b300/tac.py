@@ -19,7 +19,9 @@ TAC_OK = 0
 PAD_STATUS = {0: "converged", 1: "maxiter", 2: "nonfinite", 3: "linesearch", 4: "pair_overflow"}
 
 SYMBOLS = ("tac_create_batch", "tac_destroy_batch", "tac_reset", "tac_set_indenter", "tac_step", "tac_markers",
-           "tac_get_state", "tac_set_state", "tac_set_params", "tac_broadphase", "tac_broadphase_static",
+           "tac_adjoint",
+           "tac_get_state", "tac_set_state", "tac_set_params", "tac_get_params", "tac_broadphase",
+           "tac_broadphase_static",
            "tac_debug_eval", "tac_stats",
            "tac_pad_norms", "tac_sizes", "tac_last_error")
 
@@ -60,9 +62,11 @@ def load_library(path=_LIB_PATH):
         "tac_set_indenter": [vp, vp, vp, vp],
         "tac_step": [vp, vp, vp, vp],
         "tac_markers": [vp, vp, vp],
+        "tac_adjoint": [vp, vp, vp, vp, vp, i, f, vp],
         "tac_get_state": [vp, vp, vp, vp],
         "tac_set_state": [vp, vp, vp, vp],
         "tac_set_params": [vp, ctypes.POINTER(Params), i],
+        "tac_get_params": [vp, ctypes.POINTER(Params), i],
         "tac_broadphase": [vp, i, vp, vp, d, vp, i, vp, vp],
         "tac_broadphase_static": [vp, vp, i, vp, i, vp, i, vp, i, vp, i, vp, i, d, vp, i, vp, vp],
         "tac_debug_eval": [vp, vp, vp, f, vp, vp, vp, vp],
@@ -208,6 +212,19 @@ class TacBatch:
         _check(lib().tac_markers(self._h, _ptr(out), _stream(stream)))
         return out
 
+    def adjoint(self, dL_dmarkers, max_iter=4000, tol=1e-6, stream=None):
+        """dL/dtheta [n_pads, 9] (Lame lambda, Lame mu, mu_f, rotation vector,
+        translation) of the last frame for dL/d(markers); also the PCG status
+        and iterations per pad."""
+        g = self._f32(dL_dmarkers).reshape(self.total_markers, 2)
+        out = torch.empty(self.n_pads, 9, dtype=torch.float64, device=self.device)
+        st = torch.empty(self.n_pads, dtype=torch.int32, device=self.device)
+        it = torch.empty(self.n_pads, dtype=torch.int32, device=self.device)
+        _check(lib().tac_adjoint(self._h, _ptr(g), _ptr(out), _ptr(st), _ptr(it), int(max_iter), float(tol),
+                                 _stream(stream)))
+        self._hold = g
+        return out, st, it
+
     def get_state(self, stream=None):
         x = torch.empty(self.total_verts, 3, dtype=torch.float32, device=self.device)
         v = torch.empty_like(x)
@@ -222,6 +239,11 @@ class TacBatch:
     def set_params(self, params):
         prm = (Params * self.n_pads)(*params)
         _check(lib().tac_set_params(self._h, prm, self.n_pads))
+
+    def get_params(self):
+        prm = (Params * self.n_pads)()
+        _check(lib().tac_get_params(self._h, prm, self.n_pads))
+        return list(prm)
 
     def broadphase(self, pad, x, y, r, capacity=1 << 16, stream=None):
         x, y = self._f32(x).reshape(-1, 3), self._f32(y).reshape(-1, 3)

@@ -1,0 +1,119 @@
+"""GPU adjoint (tac_adjoint) against the FP64 oracle adjoint, which is itself
+pinned to full-solve central differences (tests/test_oracle_adjoint.py),
+and the torch.autograd.Function built on it."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import adjoint as AD
+from oracle import geometry as G
+from oracle import newton as NW
+from oracle import solver as SV
+from paper_2603_28475_b300 import scenes as S
+
+from _cases import MM, oracle_pad
+
+pytestmark = pytest.mark.gpu
+
+DH = 0.05 * MM
+
+
+@pytest.fixture(scope="module")
+def tac():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_28475_b300 import build
+    build.build()
+    from paper_2603_28475_b300 import tac as T
+    return T
+
+
+def _scene():
+    pd = S.hex_pad((6 * MM, 6 * MM, 2 * MM), (4, 4, 2), marker_shape=(3, 3))
+    mat = S.Material(mu_f=0.5)
+    ind_s = S.icosphere(2 * MM, 1)
+    z0 = 2 * MM + DH - S.lowest_z(ind_s.verts, np.zeros(3))
+    p0 = np.array([0.0, 0.0, 0.0, 3 * MM, 3 * MM, z0])
+    p1 = p0 + np.array([0, 0, 0, 0, 0, -0.08 * MM])
+    p2 = p0 + np.array([0.02, -0.01, 0.0, 0.02 * MM, 0.0, -0.12 * MM])
+    poses = np.stack([p0, p1, p2]).astype(np.float32)
+    return pd, mat, ind_s, poses
+
+
+def _oracle_solve(pad, ind, st_prev, pose):
+    prm = SV.Params(tol=1e-6)
+    st, info = SV.solve_frame(pad, ind, st_prev, pose, prm)
+    assert info.status == SV.CONVERGED
+    fr = AD.frame_of(pad, ind, st_prev, pose)
+    x, _, _ = NW.newton_polish(fr, st.x, 1.0, prm, tol_rel=1e-13)
+    return SV.State(x=x, v=(x - st_prev.x) / pad.h, pose=np.asarray(pose, np.float64))
+
+
+@pytest.fixture(scope="module")
+def oracle_ref():
+    pd, mat, ind_s, poses = _scene()
+    pad = oracle_pad(pd, mat)
+    ind = G.build_indenter(ind_s.verts, ind_s.tris)
+    P = poses.astype(np.float64)
+    s0 = SV.rest_state(pad, P[0])
+    s1 = _oracle_solve(pad, ind, s0, P[1])
+    s2 = _oracle_solve(pad, ind, s1, P[2])
+    c = np.random.default_rng(0).normal(size=(pd.markers.shape[0], 2))
+    return pad, ind, s1, s2, c, AD.adjoint(pad, ind, s1, s2, c)
+
+
+# The adjoint is taken at the frame's equilibrium, which the oracle reaches to
+# 1e-13 (Newton); the GPU frames are solved down to their float32 floor.
+TIGHT = 1e-9
+
+
+def _gpu_batch(tac):
+    pd, mat, ind_s, poses = _scene()
+    w = S.Workload("adjoint", [pd], [mat], [ind_s], 1, poses[:, None, :])
+    b = tac.batch_from_workload(w, tol=TIGHT)
+    b.reset(torch.tensor(poses[0]).reshape(1, 6))
+    for f in (1, 2):
+        b.set_indenter(torch.tensor(poses[f]).reshape(1, 6))
+        st, _ = b.step()
+        assert int(st.item()) == 0
+    return b, w
+
+
+def test_adjoint_matches_oracle(tac, oracle_ref):
+    pad, ind, s1, s2, c, ref = oracle_ref
+    b, w = _gpu_batch(tac)
+    g, st, it = b.adjoint(torch.tensor(c, dtype=torch.float32))
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0, int(st.item())
+    got = g.cpu().numpy()[0]
+    scale = np.abs(ref).max()
+    for k in range(9):
+        assert got[k] == pytest.approx(ref[k], rel=1e-3, abs=1e-4 * scale), (k, got, ref)
+    b.close()
+
+
+def test_autograd_function_gives_the_adjoint(tac, oracle_ref):
+    from paper_2603_28475_b300 import autograd as A
+    pad, ind, s1, s2, c, ref = oracle_ref
+    pd, mat, ind_s, poses = _scene()
+    w = S.Workload("adjoint", [pd], [mat], [ind_s], 1, poses[:, None, :])
+    b = tac.batch_from_workload(w, tol=TIGHT)
+    b.reset(torch.tensor(poses[0]).reshape(1, 6))
+    b.set_indenter(torch.tensor(poses[1]).reshape(1, 6))
+    b.step()
+    ck = A.FrameCheckpoint(b, poses[1])
+    base = b.get_params()
+    lame = torch.tensor([[pad.lam, pad.mu]], dtype=torch.float64, requires_grad=True)
+    mu_f = torch.tensor([pad.mu_f], dtype=torch.float64, requires_grad=True)
+    pose = torch.tensor(poses[2].astype(np.float64).reshape(1, 6), requires_grad=True)
+    m = A.frame_markers(b, ck, lame, mu_f, pose, base)
+    loss = (torch.tensor(c, dtype=torch.float32, device=m.device) * m).sum()
+    loss.backward()
+    got = np.concatenate([lame.grad.numpy()[0], mu_f.grad.numpy(), pose.grad.numpy()[0]])
+    scale = np.abs(ref).max()
+    for k in range(9):
+        assert got[k] == pytest.approx(ref[k], rel=2e-3, abs=2e-4 * scale), (k, got, ref)
+    # the marker field of the forward pass is the frame's solution
+    assert np.abs(m.detach().cpu().numpy() - SV.markers(pad, s2.x)).max() <= 1e-4 * 2 * MM
+    b.close()
