@@ -272,6 +272,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     }
     // layouts
     int XVt = 0, Tt = 0, np_tot = 0, pv_tot = 0, pc_tot = 0, sv_tot = 0, st_tot = 0, se_tot = 0, mk_tot = 0;
+    int col_tot = 0;
     for (auto& M : b->meshes) {
         MeshDev md{};
         md.xv_off = XVt; md.n_v = M.n_v;
@@ -282,6 +283,8 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
         md.st_off = st_tot; md.n_st = (int)(M.st.size() / 3);
         md.se_off = se_tot; md.n_se = (int)(M.se.size() / 2);
         md.mk_off = mk_tot; md.n_mk = M.n_mk;
+        md.col_off = col_tot; md.n_col = M.n_colour();
+        col_tot += (int)M.colour_off.size();
         XVt += M.n_v; Tt += M.n_t; np_tot += M.n_patch(); pv_tot += (int)M.pvert.size();
         pc_tot += (int)M.pcsr.size(); sv_tot += md.n_sv; st_tot += md.n_st; se_tot += md.n_se; mk_tot += M.n_mk;
         b->hmesh.push_back(md);
@@ -337,7 +340,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     uint8_t* fixed = dalloc<uint8_t>(K, XVt, rc);
     float* B = dalloc<float>(K, 9 * (size_t)Tt, rc);
     uint32_t* lconn = dalloc<uint32_t>(K, Tt, rc);
-    uint64_t* slot = dalloc<uint64_t>(K, Tt, rc);
+    uint32_t* slot = dalloc<uint32_t>(K, Tt, rc);
     int4* patch = dalloc<int4>(K, np_tot, rc);
     int* pvert = dalloc<int>(K, pv_tot, rc);
     uint16_t* pcsr = dalloc<uint16_t>(K, pc_tot, rc);
@@ -368,6 +371,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     int* cvo = dalloc<int>(K, 6 * pc + 1, rc);
     int* cnt = dalloc<int>(K, Vt, rc);
     int* ilist = dalloc<int>(K, il, rc);
+    int* colour = dalloc<int>(K, col_tot, rc);
     long long* stats = dalloc<long long>(K, 16 * (size_t)n_pads, rc);
     double* norms = dalloc<double>(K, 4 * (size_t)n_pads, rc);
     int* pad_nlag = dalloc<int>(K, n_pads, rc);
@@ -388,7 +392,8 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     std::vector<float> hX(3 * (size_t)XVt), hvl(XVt), hB(9 * (size_t)Tt), hmkw, hY;
     std::vector<uint8_t> hfx(XVt);
     std::vector<uint32_t> hlc(Tt);
-    std::vector<uint64_t> hsl(Tt);
+    std::vector<uint32_t> hsl(Tt);
+    std::vector<int> hcol;
     std::vector<int4> hpatch;
     std::vector<int> hpv, hsv, hst, hse, hmki, hit, hie;
     std::vector<uint16_t> hpc;
@@ -414,6 +419,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
         hse.insert(hse.end(), M.se.begin(), M.se.end());
         hmki.insert(hmki.end(), M.mk_ids.begin(), M.mk_ids.end());
         hmkw.insert(hmkw.end(), M.mk_w.begin(), M.mk_w.end());
+        hcol.insert(hcol.end(), M.colour_off.begin(), M.colour_off.end());
     }
     for (auto& I : b->inds) {
         hY.insert(hY.end(), I.Y.begin(), I.Y.end());
@@ -431,7 +437,8 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     r2 |= up(fixed, hfx.data(), hfx.size());
     r2 |= up(B, hB.data(), hB.size() * 4);
     r2 |= up(lconn, hlc.data(), hlc.size() * 4);
-    r2 |= up(slot, hsl.data(), hsl.size() * 8);
+    r2 |= up(slot, hsl.data(), hsl.size() * 4);
+    r2 |= up(colour, hcol.data(), hcol.size() * 4);
     r2 |= up(patch, hpatch.data(), hpatch.size() * sizeof(int4));
     r2 |= up(pvert, hpv.data(), hpv.size() * 4);
     r2 |= up(pcsr, hpc.data(), hpc.size() * 2);
@@ -469,7 +476,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     D.envs = b->d_envs;
     D.pads = b->d_pads;
     D.order = order_d;
-    D.X = X; D.vlump = vlump; D.fixed = fixed; D.B = B; D.lconn = lconn; D.slot = slot;
+    D.X = X; D.vlump = vlump; D.fixed = fixed; D.B = B; D.lconn = lconn; D.slot = slot; D.colour = colour;
     D.patch = patch; D.pvert = pvert; D.pcsr = pcsr; D.sv = sv; D.st = stt; D.se = se;
     D.mk_ids = mk_ids; D.mk_w = mk_w; D.Y = Y; D.it = it; D.ie = ie; D.Yt = Yt; D.Yn = Yn;
     D.pose_t = b->d_pose_t; D.pose_n = b->d_pose_n;

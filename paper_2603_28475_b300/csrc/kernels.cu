@@ -33,19 +33,25 @@ constexpr float kFloat32Floor = 256.0f / 16777216.0f;
 // ---------------------------------------------------------------------------
 // shared memory of one CTA
 
-// raw data of one tet patch, copied asynchronously from global memory
+// raw data of one warp-sized tet patch, copied asynchronously from global
+// memory (one tet and one vertex per lane)
 struct PatchStage {
-    float B[9][kThreads];       // Dm^-1 entries of the patch's tets
-    uint32_t lc[kThreads];      // 4 x 8-bit local vertex ids
-    uint2 sl[kThreads];         // 4 x 16-bit corner slots
-    float uh[3][kThreads];      // displacement (hi) of the patch's vertices
-    float ul[3][kThreads];      // displacement (lo)
-    float p[3][kThreads];       // direction
+    float B[9][32];             // Dm^-1 entries of the patch's tets
+    uint32_t lc[32];            // 4 x 8-bit local vertex ids
+    uint32_t sl[32];            // 4 x 8-bit corner slots
+    float uh[3][32];            // displacement (hi) of the patch's vertices
+    float ul[3][32];            // displacement (lo)
+    float p[3][32];             // direction
+};
+
+// per-warp scratch of the tet passes
+struct WarpScratch {
+    PatchStage st[2];           // double buffer: the warp's next patch loads while this one computes
+    float stg[9][kStage];       // corner contributions of the current patch
 };
 
 struct Shared {
-    PatchStage st[2];           // double buffer: patch k+1 loads while k computes
-    float stg[9][kStage];
+    WarpScratch w[kWarps];
     double rd[kWarps][8];
     float rf[kWarps][4];
     int ri[kWarps];
@@ -335,253 +341,264 @@ __device__ __forceinline__ PatchHdr patch_hdr(const Dev& D, const MeshDev& M, in
     return PatchHdr{ph.x, ph.y, ph.z & 0xffff, ph.z >> 16, ph.w};
 }
 
-// this thread's entry of the patch's vertex list (mesh vertex id | flags)
-__device__ __forceinline__ int patch_vertex(const Dev& D, const MeshDev& M, const PatchHdr& h) {
-    return threadIdx.x < h.nv ? __ldg(D.pvert + M.pvert_off + h.vb + threadIdx.x) : 0;
-}
-
-// asynchronous copy of one patch (tet data and raw vertex data) into a stage
+// asynchronous copy of one warp patch (tet data and raw vertex data) into a
+// stage; lane k copies tet k and vertex k
 __device__ __forceinline__ void issue_patch(const Dev& D, const PadDev& P, const MeshDev& M, const PatchHdr& h,
-                                            int gvf, PatchStage& st) {
-    const int tid = threadIdx.x;
-    if (tid < h.nt) {
-        size_t t = (size_t)M.tet_off + h.tb + tid;
+                                            PatchStage& st, int lane) {
+    if (lane < h.nt) {
+        size_t t = (size_t)M.tet_off + h.tb + lane;
 #pragma unroll
-        for (int e = 0; e < 9; ++e) cp_async4(&st.B[e][tid], D.B + (size_t)e * D.Tt + t);
-        cp_async4(&st.lc[tid], D.lconn + t);
-        cp_async8(&st.sl[tid], D.slot + t);
+        for (int e = 0; e < 9; ++e) cp_async4(&st.B[e][lane], D.B + (size_t)e * D.Tt + t);
+        cp_async4(&st.lc[lane], D.lconn + t);
+        cp_async4(&st.sl[lane], D.slot + t);
     }
-    if (tid < h.nv) {
+    if (lane < h.nv) {
+        int gvf = __ldg(D.pvert + M.pvert_off + h.vb + lane);
         int si = P.v_off + (gvf & ((1 << 29) - 1));
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            cp_async4(&st.uh[c][tid], D.uh + (size_t)c * D.Vt + si);
-            cp_async4(&st.ul[c][tid], D.ul + (size_t)c * D.Vt + si);
-            cp_async4(&st.p[c][tid], D.p + (size_t)c * D.Vt + si);
+            cp_async4(&st.uh[c][lane], D.uh + (size_t)c * D.Vt + si);
+            cp_async4(&st.ul[c][lane], D.ul + (size_t)c * D.Vt + si);
+            cp_async4(&st.p[c][lane], D.p + (size_t)c * D.Vt + si);
         }
     }
     cp_async_commit();
 }
 
 // pass 0: p^T H_e p at u; pass 1: gradient, diagonal blocks and remainder at
-// u + alpha p, scattered into g[gb], blk[gb]. Patches stream through a
-// double-buffered stage: the copies of patch k+1 are in flight while patch k
-// is computed and its vertices are reduced.
+// u + alpha p into g[gb], blk[gb]; pass 2: H_e p into g[gb]; pass 3: lambda
+// (in p) against the Lame derivatives of the stress.
+// Each warp streams its own patches (one tet per lane) through a private
+// double-buffered stage and sums its patch's corner contributions per vertex
+// (one vertex per lane) before writing them: no CTA barrier inside a colour
+// class. Passes that scatter walk the colour classes in order with one CTA
+// barrier between classes (patches of one class share no vertex); the
+// reduction passes walk all patches without any.
 template <int PASS>
 __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, int gb) {
     TetOut out{0.0, 0, 0.f, 0.0};
     const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    WarpScratch& W = S.w[warp];
     const float mu = P.mu, lam = P.lam, h2 = P.h * P.h;
-    const int np = M.n_patch;
-    PatchHdr hc = patch_hdr(D, M, 0);
-    int gvf_c = patch_vertex(D, M, hc);
-    issue_patch(D, P, M, hc, gvf_c, S.st[0]);
-    int gvf_n = 0;
-    if (np > 1) gvf_n = patch_vertex(D, M, patch_hdr(D, M, 1));
-    for (int pi = 0; pi < np; ++pi) {
-        const int b = pi & 1;
-        cp_async_wait_all();
-        __syncthreads();     // stage b complete; every thread is done with patch pi-1
-        int s0 = 0, s1 = 0;
-        if ((PASS == 1 || PASS == 2) && tid < hc.nv) {
-            s0 = __ldg(D.pcsr + M.pcsr_off + hc.cb + tid);
-            s1 = __ldg(D.pcsr + M.pcsr_off + hc.cb + tid + 1);
+    constexpr bool kScatter = (PASS == 1 || PASS == 2);
+    const int ncls = kScatter ? M.n_col : 1;
+    for (int cls = 0; cls < ncls; ++cls) {
+        const int p_begin = kScatter ? __ldg(D.colour + M.col_off + cls) : 0;
+        const int p_end = kScatter ? __ldg(D.colour + M.col_off + cls + 1) : M.n_patch;
+        int pi = p_begin + warp;
+        int b = 0;
+        PatchHdr hc{0, 0, 0, 0, 0};
+        if (pi < p_end) {
+            hc = patch_hdr(D, M, pi);
+            issue_patch(D, P, M, hc, W.st[0], lane);
         }
-        int gvf_a = 0;
-        if (pi + 1 < np) {
-            issue_patch(D, P, M, patch_hdr(D, M, pi + 1), gvf_n, S.st[b ^ 1]);
-            if (pi + 2 < np) gvf_a = patch_vertex(D, M, patch_hdr(D, M, pi + 2));
-        }
-        const PatchStage& st = S.st[b];
-        if (tid < hc.nt) {
-            uint32_t lc = st.lc[tid];
-            int l0 = lc & 255, l1 = (lc >> 8) & 255, l2 = (lc >> 16) & 255, l3 = lc >> 24;
-            float Bm[9];
-#pragma unroll
-            for (int e = 0; e < 9; ++e) Bm[e] = st.B[e][tid];
-            float Du[9], Dp[9];
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                float h0 = st.uh[r][l0], o0 = st.ul[r][l0], p0 = st.p[r][l0];
-                float p1 = st.p[r][l1] - p0, p2 = st.p[r][l2] - p0, p3 = st.p[r][l3] - p0;
-                Dp[3 * r + 0] = p1;
-                Dp[3 * r + 1] = p2;
-                Dp[3 * r + 2] = p3;
-                Du[3 * r + 0] = ((st.uh[r][l1] - h0) + (st.ul[r][l1] - o0)) + alpha * p1;
-                Du[3 * r + 1] = ((st.uh[r][l2] - h0) + (st.ul[r][l2] - o0)) + alpha * p2;
-                Du[3 * r + 2] = ((st.uh[r][l3] - h0) + (st.ul[r][l3] - o0)) + alpha * p3;
+        while (pi < p_end) {
+            const int pn = pi + kWarps;
+            cp_async_wait_all();
+            __syncwarp();                       // stage b complete for every lane
+            int gvf_c = 0, s0 = 0, s1 = 0;
+            if (kScatter && lane < hc.nv) {
+                gvf_c = __ldg(D.pvert + M.pvert_off + hc.vb + lane);
+                s0 = __ldg(D.pcsr + M.pcsr_off + hc.cb + lane);
+                s1 = __ldg(D.pcsr + M.pcsr_off + hc.cb + lane + 1);
             }
-            float G[9], dF[9];
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    G[3 * r + c] = Du[3 * r] * Bm[c] + Du[3 * r + 1] * Bm[3 + c] + Du[3 * r + 2] * Bm[6 + c];
-                    dF[3 * r + c] = Dp[3 * r] * Bm[c] + Dp[3 * r + 1] * Bm[3 + c] + Dp[3 * r + 2] * Bm[6 + c];
+            PatchHdr hn{0, 0, 0, 0, 0};
+            if (pn < p_end) {
+                hn = patch_hdr(D, M, pn);
+                issue_patch(D, P, M, hn, W.st[b ^ 1], lane);
+            }
+            const PatchStage& st = W.st[b];
+                if (lane < hc.nt) {
+                uint32_t lc = st.lc[lane];
+                int l0 = lc & 255, l1 = (lc >> 8) & 255, l2 = (lc >> 16) & 255, l3 = lc >> 24;
+                float Bm[9];
+    #pragma unroll
+                for (int e = 0; e < 9; ++e) Bm[e] = st.B[e][lane];
+                float Du[9], Dp[9];
+    #pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    float h0 = st.uh[r][l0], o0 = st.ul[r][l0], p0 = st.p[r][l0];
+                    float p1 = st.p[r][l1] - p0, p2 = st.p[r][l2] - p0, p3 = st.p[r][l3] - p0;
+                    Dp[3 * r + 0] = p1;
+                    Dp[3 * r + 1] = p2;
+                    Dp[3 * r + 2] = p3;
+                    Du[3 * r + 0] = ((st.uh[r][l1] - h0) + (st.ul[r][l1] - o0)) + alpha * p1;
+                    Du[3 * r + 1] = ((st.uh[r][l2] - h0) + (st.ul[r][l2] - o0)) + alpha * p2;
+                    Du[3 * r + 2] = ((st.uh[r][l3] - h0) + (st.ul[r][l3] - o0)) + alpha * p3;
                 }
-            float detB = Bm[0] * (Bm[4] * Bm[8] - Bm[5] * Bm[7]) - Bm[1] * (Bm[3] * Bm[8] - Bm[5] * Bm[6]) +
-                         Bm[2] * (Bm[3] * Bm[7] - Bm[4] * Bm[6]);
-            float hV = h2 / (6.0f * detB);
-            FAnalysis f;
-            f_analysis(G, f);
-            float dF2 = 0.f;
-#pragma unroll
-            for (int e = 0; e < 9; ++e) dF2 += dF[e] * dF[e];
-            AInv ai = a_invariants(f, dF);
-            if (PASS == 0) {
-                out.acc += (double)(hV * (mu * dF2 + (mu - lam * f.lnJ) * ai.trA2 + lam * ai.c1 * ai.c1));
-            } else if (PASS == 3) {
-                // direction dF = D_lambda Dm^-1: dP/dlam : dF = ln J tr(F^-1 dF),
-                // dP/dmu : dF = (F - F^-T) : dF = tr dF + G : dF - tr(F^-1 dF)
-                float GdF = 0.f;
-#pragma unroll
-                for (int e = 0; e < 9; ++e) GdF += G[e] * dF[e];
-                out.acc += (double)(hV * f.lnJ * ai.c1);
-                out.acc2 += (double)(hV * ((dF[0] + dF[4] + dF[8]) + GdF - ai.c1));
-            } else if (PASS == 2) {
-                // dP = mu dF + (mu - lam ln J) F^-T dF^T F^-T + lam tr(F^-1 dF) F^-T
-                float C[9];
-#pragma unroll
-                for (int e = 0; e < 9; ++e) C[e] = f.cof[e] * f.invJ;
-                float M1[9];
-#pragma unroll
-                for (int i = 0; i < 3; ++i)
-#pragma unroll
-                    for (int l = 0; l < 3; ++l)
-                        M1[3 * i + l] = C[3 * i] * dF[3 * l] + C[3 * i + 1] * dF[3 * l + 1] + C[3 * i + 2] * dF[3 * l + 2];
-                float a2 = mu - lam * f.lnJ, a3 = lam * ai.c1;
-                float dP[9];
-#pragma unroll
-                for (int i = 0; i < 3; ++i)
-#pragma unroll
-                    for (int j = 0; j < 3; ++j)
-                        dP[3 * i + j] = mu * dF[3 * i + j] +
-                                        a2 * (M1[3 * i] * C[j] + M1[3 * i + 1] * C[3 + j] + M1[3 * i + 2] * C[6 + j]) +
-                                        a3 * C[3 * i + j];
-                float Hc[3][3];
-#pragma unroll
-                for (int k = 0; k < 3; ++k)
-#pragma unroll
-                    for (int r = 0; r < 3; ++r)
-                        Hc[k][r] = hV * (dP[3 * r] * Bm[3 * k] + dP[3 * r + 1] * Bm[3 * k + 1] + dP[3 * r + 2] * Bm[3 * k + 2]);
-                uint2 slw = st.sl[tid];
-                uint64_t sl = (uint64_t)slw.x | ((uint64_t)slw.y << 32);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    int slot = (int)((sl >> (16 * k)) & 0xffff);
-#pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        S.stg[c][slot] = (k == 0) ? -(Hc[0][c] + Hc[1][c] + Hc[2][c]) : Hc[k - 1][c];
-                }
-            } else {
-                if (!(f.J > 0.0f)) out.bad = 1;
-                // remainder of the line expanded at the trial point (step -alpha)
-                float q = alpha * (-ai.c1 + alpha * (ai.c2 - alpha * ai.c3));
-                float a2c = alpha * alpha * (ai.c2 - alpha * ai.c3);
-                float dl = log1p_minus(q) + a2c;          // ln det(I - aA) + a tr A
-                float dlnJ = log1pf(q);
-                out.acc += (double)(hV * (0.5f * mu * alpha * alpha * dF2 + (lam * f.lnJ - mu) * dl +
-                                          0.5f * lam * dlnJ * dlnJ));
-                // first Piola-Kirchhoff stress P = (mu Q + lam ln J cof) / J
-                float Pm[9];
-#pragma unroll
-                for (int e = 0; e < 9; ++e) Pm[e] = (mu * f.Q[e] + lam * f.lnJ * f.cof[e]) * f.invJ;
-                // H = hV P B^T: column k is the force on corner k+1
-                float Hc[3][3];
-#pragma unroll
-                for (int k = 0; k < 3; ++k)
-#pragma unroll
-                    for (int r = 0; r < 3; ++r)
-                        Hc[k][r] = hV * (Pm[3 * r] * Bm[3 * k] + Pm[3 * r + 1] * Bm[3 * k + 1] + Pm[3 * r + 2] * Bm[3 * k + 2]);
-                float coef = fmaxf(mu + lam * (1.0f - f.lnJ), 0.0f) * f.invJ * f.invJ;
-                uint2 slw = st.sl[tid];
-                uint64_t sl = (uint64_t)slw.x | ((uint64_t)slw.y << 32);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    float bv[3], fo[3];
-                    if (k == 0) {
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            bv[c] = -(Bm[c] + Bm[3 + c] + Bm[6 + c]);
-                            fo[c] = -(Hc[0][c] + Hc[1][c] + Hc[2][c]);
+                float G[9], dF[9];
+    #pragma unroll
+                for (int r = 0; r < 3; ++r)
+    #pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        G[3 * r + c] = Du[3 * r] * Bm[c] + Du[3 * r + 1] * Bm[3 + c] + Du[3 * r + 2] * Bm[6 + c];
+                        dF[3 * r + c] = Dp[3 * r] * Bm[c] + Dp[3 * r + 1] * Bm[3 + c] + Dp[3 * r + 2] * Bm[6 + c];
+                    }
+                float detB = Bm[0] * (Bm[4] * Bm[8] - Bm[5] * Bm[7]) - Bm[1] * (Bm[3] * Bm[8] - Bm[5] * Bm[6]) +
+                             Bm[2] * (Bm[3] * Bm[7] - Bm[4] * Bm[6]);
+                float hV = h2 / (6.0f * detB);
+                FAnalysis f;
+                f_analysis(G, f);
+                float dF2 = 0.f;
+    #pragma unroll
+                for (int e = 0; e < 9; ++e) dF2 += dF[e] * dF[e];
+                AInv ai = a_invariants(f, dF);
+                if (PASS == 0) {
+                    out.acc += (double)(hV * (mu * dF2 + (mu - lam * f.lnJ) * ai.trA2 + lam * ai.c1 * ai.c1));
+                } else if (PASS == 3) {
+                    // direction dF = D_lambda Dm^-1: dP/dlam : dF = ln J tr(F^-1 dF),
+                    // dP/dmu : dF = (F - F^-T) : dF = tr dF + G : dF - tr(F^-1 dF)
+                    float GdF = 0.f;
+    #pragma unroll
+                    for (int e = 0; e < 9; ++e) GdF += G[e] * dF[e];
+                    out.acc += (double)(hV * f.lnJ * ai.c1);
+                    out.acc2 += (double)(hV * ((dF[0] + dF[4] + dF[8]) + GdF - ai.c1));
+                } else if (PASS == 2) {
+                    // dP = mu dF + (mu - lam ln J) F^-T dF^T F^-T + lam tr(F^-1 dF) F^-T
+                    float C[9];
+    #pragma unroll
+                    for (int e = 0; e < 9; ++e) C[e] = f.cof[e] * f.invJ;
+                    float M1[9];
+    #pragma unroll
+                    for (int i = 0; i < 3; ++i)
+    #pragma unroll
+                        for (int l = 0; l < 3; ++l)
+                            M1[3 * i + l] = C[3 * i] * dF[3 * l] + C[3 * i + 1] * dF[3 * l + 1] + C[3 * i + 2] * dF[3 * l + 2];
+                    float a2 = mu - lam * f.lnJ, a3 = lam * ai.c1;
+                    float dP[9];
+    #pragma unroll
+                    for (int i = 0; i < 3; ++i)
+    #pragma unroll
+                        for (int j = 0; j < 3; ++j)
+                            dP[3 * i + j] = mu * dF[3 * i + j] +
+                                            a2 * (M1[3 * i] * C[j] + M1[3 * i + 1] * C[3 + j] + M1[3 * i + 2] * C[6 + j]) +
+                                            a3 * C[3 * i + j];
+                    float Hc[3][3];
+    #pragma unroll
+                    for (int k = 0; k < 3; ++k)
+    #pragma unroll
+                        for (int r = 0; r < 3; ++r)
+                            Hc[k][r] = hV * (dP[3 * r] * Bm[3 * k] + dP[3 * r + 1] * Bm[3 * k + 1] + dP[3 * r + 2] * Bm[3 * k + 2]);
+                    uint32_t sl = st.sl[lane];
+    #pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        int slot = (int)((sl >> (8 * k)) & 0xff);
+    #pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            W.stg[c][slot] = (k == 0) ? -(Hc[0][c] + Hc[1][c] + Hc[2][c]) : Hc[k - 1][c];
+                    }
+                } else {
+                    if (!(f.J > 0.0f)) out.bad = 1;
+                    // remainder of the line expanded at the trial point (step -alpha)
+                    float q = alpha * (-ai.c1 + alpha * (ai.c2 - alpha * ai.c3));
+                    float a2c = alpha * alpha * (ai.c2 - alpha * ai.c3);
+                    float dl = log1p_minus(q) + a2c;          // ln det(I - aA) + a tr A
+                    float dlnJ = log1pf(q);
+                    out.acc += (double)(hV * (0.5f * mu * alpha * alpha * dF2 + (lam * f.lnJ - mu) * dl +
+                                              0.5f * lam * dlnJ * dlnJ));
+                    // first Piola-Kirchhoff stress P = (mu Q + lam ln J cof) / J
+                    float Pm[9];
+    #pragma unroll
+                    for (int e = 0; e < 9; ++e) Pm[e] = (mu * f.Q[e] + lam * f.lnJ * f.cof[e]) * f.invJ;
+                    // H = hV P B^T: column k is the force on corner k+1
+                    float Hc[3][3];
+    #pragma unroll
+                    for (int k = 0; k < 3; ++k)
+    #pragma unroll
+                        for (int r = 0; r < 3; ++r)
+                            Hc[k][r] = hV * (Pm[3 * r] * Bm[3 * k] + Pm[3 * r + 1] * Bm[3 * k + 1] + Pm[3 * r + 2] * Bm[3 * k + 2]);
+                    float coef = fmaxf(mu + lam * (1.0f - f.lnJ), 0.0f) * f.invJ * f.invJ;
+                    uint32_t sl = st.sl[lane];
+    #pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        float bv[3], fo[3];
+                        if (k == 0) {
+    #pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                bv[c] = -(Bm[c] + Bm[3 + c] + Bm[6 + c]);
+                                fo[c] = -(Hc[0][c] + Hc[1][c] + Hc[2][c]);
+                            }
+                        } else {
+    #pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                bv[c] = Bm[3 * (k - 1) + c];
+                                fo[c] = Hc[k - 1][c];
+                            }
                         }
+                        float cc[3];
+    #pragma unroll
+                        for (int r = 0; r < 3; ++r) cc[r] = f.cof[3 * r] * bv[0] + f.cof[3 * r + 1] * bv[1] + f.cof[3 * r + 2] * bv[2];
+                        float bb = mu * (bv[0] * bv[0] + bv[1] * bv[1] + bv[2] * bv[2]);
+                        int slot = (int)((sl >> (8 * k)) & 0xff);
+                        out.fmax = fmaxf(out.fmax, fmaxf(fabsf(fo[0]), fmaxf(fabsf(fo[1]), fabsf(fo[2]))));
+                        W.stg[0][slot] = fo[0];
+                        W.stg[1][slot] = fo[1];
+                        W.stg[2][slot] = fo[2];
+                        W.stg[3][slot] = hV * (bb + coef * cc[0] * cc[0]);
+                        W.stg[4][slot] = hV * (bb + coef * cc[1] * cc[1]);
+                        W.stg[5][slot] = hV * (bb + coef * cc[2] * cc[2]);
+                        W.stg[6][slot] = hV * (coef * cc[0] * cc[1]);
+                        W.stg[7][slot] = hV * (coef * cc[0] * cc[2]);
+                        W.stg[8][slot] = hV * (coef * cc[1] * cc[2]);
+                    }
+                }
+            }
+
+            if (PASS == 2) {
+                __syncwarp();                   // every corner of the patch staged
+                if (lane < hc.nv) {
+                    int gv = gvf_c & ((1 << 29) - 1);
+                    bool first = (gvf_c & (1 << 30)) != 0;
+                    float acc[3] = {0.f, 0.f, 0.f};
+                    for (int q = s0; q < s1; ++q)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) acc[c] += W.stg[c][q];
+                    float* g = D.g[gb];
+                    int si = P.v_off + gv;
+                    if (first) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) g[c * D.Vt + si] = acc[c];
                     } else {
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            bv[c] = Bm[3 * (k - 1) + c];
-                            fo[c] = Hc[k - 1][c];
-                        }
+                        for (int c = 0; c < 3; ++c) g[c * D.Vt + si] += acc[c];
                     }
-                    float cc[3];
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) cc[r] = f.cof[3 * r] * bv[0] + f.cof[3 * r + 1] * bv[1] + f.cof[3 * r + 2] * bv[2];
-                    float bb = mu * (bv[0] * bv[0] + bv[1] * bv[1] + bv[2] * bv[2]);
-                    int slot = (int)((sl >> (16 * k)) & 0xffff);
-                    out.fmax = fmaxf(out.fmax, fmaxf(fabsf(fo[0]), fmaxf(fabsf(fo[1]), fabsf(fo[2]))));
-                    S.stg[0][slot] = fo[0];
-                    S.stg[1][slot] = fo[1];
-                    S.stg[2][slot] = fo[2];
-                    S.stg[3][slot] = hV * (bb + coef * cc[0] * cc[0]);
-                    S.stg[4][slot] = hV * (bb + coef * cc[1] * cc[1]);
-                    S.stg[5][slot] = hV * (bb + coef * cc[2] * cc[2]);
-                    S.stg[6][slot] = hV * (coef * cc[0] * cc[1]);
-                    S.stg[7][slot] = hV * (coef * cc[0] * cc[2]);
-                    S.stg[8][slot] = hV * (coef * cc[1] * cc[2]);
                 }
             }
-        }
-        if (PASS == 2) {
-            __syncthreads();     // every corner of patch pi staged
-            if (tid < hc.nv) {
-                int gv = gvf_c & ((1 << 29) - 1);
-                bool first = (gvf_c & (1 << 30)) != 0;
-                float acc[3] = {0.f, 0.f, 0.f};
-                for (int q = s0; q < s1; ++q)
+            if (PASS == 1) {
+                __syncwarp();                   // every corner of the patch staged
+                if (lane < hc.nv) {
+                    int gv = gvf_c & ((1 << 29) - 1);
+                    bool first = (gvf_c & (1 << 30)) != 0;
+                    float acc[9];
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) acc[c] += S.stg[c][q];
-                float* g = D.g[gb];
-                int si = P.v_off + gv;
-                if (first) {
+                    for (int c = 0; c < 9; ++c) acc[c] = 0.f;
+                    for (int q = s0; q < s1; ++q)
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) g[c * D.Vt + si] = acc[c];
-                } else {
+                        for (int c = 0; c < 9; ++c) acc[c] += W.stg[c][q];
+                    int si = P.v_off + gv;
+                    float* g = D.g[gb];
+                    float* k = D.blk[gb];
+                    if (first) {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) g[c * D.Vt + si] += acc[c];
+                        for (int c = 0; c < 3; ++c) g[c * D.Vt + si] = acc[c];
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) k[c * D.Vt + si] = acc[3 + c];
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) g[c * D.Vt + si] += acc[c];
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) k[c * D.Vt + si] += acc[3 + c];
+                    }
                 }
             }
+            __syncwarp();                       // lanes done with stage b and the corner slots
+            hc = hn;
+            pi = pn;
+            b ^= 1;
         }
-        if (PASS == 1) {
-            __syncthreads();     // every corner of patch pi staged
-            if (tid < hc.nv) {
-                int gv = gvf_c & ((1 << 29) - 1);
-                bool first = (gvf_c & (1 << 30)) != 0;
-                float acc[9];
-#pragma unroll
-                for (int c = 0; c < 9; ++c) acc[c] = 0.f;
-                for (int q = s0; q < s1; ++q)
-#pragma unroll
-                    for (int c = 0; c < 9; ++c) acc[c] += S.stg[c][q];
-                int si = P.v_off + gv;
-                float* g = D.g[gb];
-                float* k = D.blk[gb];
-                if (first) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) g[c * D.Vt + si] = acc[c];
-#pragma unroll
-                    for (int c = 0; c < 6; ++c) k[c * D.Vt + si] = acc[3 + c];
-                } else {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) g[c * D.Vt + si] += acc[c];
-#pragma unroll
-                    for (int c = 0; c < 6; ++c) k[c * D.Vt + si] += acc[3 + c];
-                }
-            }
-        }
-        if (pi + 1 < np) hc = patch_hdr(D, M, pi + 1);
-        gvf_c = gvf_n;
-        gvf_n = gvf_a;
+        if (kScatter) __syncthreads();          // colour class complete: its writes are visible
     }
-    __syncthreads();
     // every thread must see the same totals: the caller branches on them
     double v[3] = {out.acc, (double)out.bad, out.acc2};
     block_sum<3>(v);

@@ -187,7 +187,8 @@ bool build_pad_mesh(int nv, int nt, int nf, int nm, const float* rest, const int
     }
 
     // patches: tets in Morton order of their centroids, cut greedily so that a
-    // patch has at most kPatchTets tets and kPatchVerts distinct vertices
+    // patch has at most kPatchTets tets and kPatchVerts distinct vertices, then
+    // coloured so that patches of one colour share no vertex
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     for (int i = 0; i < nv; ++i)
         for (int r = 0; r < 3; ++r) {
@@ -210,6 +211,69 @@ bool build_pad_mesh(int nv, int nt, int nf, int nm, const float* rest, const int
     std::iota(M.tet_order.begin(), M.tet_order.end(), 0);
     std::stable_sort(M.tet_order.begin(), M.tet_order.end(), [&](int a, int b) { return code[a] < code[b]; });
 
+    // 1. greedy patches in Morton order (at most kPatchTets tets, kPatchVerts vertices)
+    std::vector<std::vector<int>> ptets, pverts;
+    {
+        std::vector<int> mark(nv, -1);
+        std::vector<int> cur_t, cur_v;
+        int pid = 0;
+        for (int k = 0; k < nt; ++k) {
+            const int* c = tets + 4 * static_cast<size_t>(M.tet_order[k]);
+            int add = 0;
+            for (int j = 0; j < 4; ++j) {
+                bool seen = mark[c[j]] == pid;
+                for (int jj = 0; jj < j; ++jj) seen = seen || (c[jj] == c[j]);
+                add += seen ? 0 : 1;
+            }
+            if (static_cast<int>(cur_t.size()) >= kPatchTets || static_cast<int>(cur_v.size()) + add > kPatchVerts) {
+                ptets.push_back(cur_t);
+                pverts.push_back(cur_v);
+                cur_t.clear();
+                cur_v.clear();
+                ++pid;
+            }
+            cur_t.push_back(M.tet_order[k]);
+            for (int j = 0; j < 4; ++j)
+                if (mark[c[j]] != pid) {
+                    mark[c[j]] = pid;
+                    cur_v.push_back(c[j]);
+                }
+        }
+        if (!cur_t.empty()) {
+            ptets.push_back(cur_t);
+            pverts.push_back(cur_v);
+        }
+    }
+    const int np0 = static_cast<int>(ptets.size());
+    // 2. colour the patches: two patches sharing a vertex get different colours
+    std::vector<std::vector<int>> vpatch(nv);
+    for (int q = 0; q < np0; ++q)
+        for (int v : pverts[q]) vpatch[v].push_back(q);
+    std::vector<int> colour(np0, -1);
+    int ncol = 0;
+    {
+        std::vector<int> used(64, -1);
+        for (int q = 0; q < np0; ++q) {
+            for (int v : pverts[q])
+                for (int o : vpatch[v])
+                    if (colour[o] >= 0) {
+                        if (colour[o] >= static_cast<int>(used.size())) used.resize(colour[o] + 1, -1);
+                        used[colour[o]] = q;
+                    }
+            int c = 0;
+            while (c < static_cast<int>(used.size()) && used[c] == q) ++c;
+            colour[q] = c;
+            ncol = std::max(ncol, c + 1);
+        }
+    }
+    // 3. patches in colour-major order; tets laid out in that order
+    std::vector<int> porder(np0);
+    std::iota(porder.begin(), porder.end(), 0);
+    std::stable_sort(porder.begin(), porder.end(), [&](int a, int b) { return colour[a] < colour[b]; });
+    M.colour_off.assign(ncol + 1, 0);
+    for (int q = 0; q < np0; ++q) M.colour_off[colour[q] + 1]++;
+    for (int c = 0; c < ncol; ++c) M.colour_off[c + 1] += M.colour_off[c];
+
     M.B.assign(9 * static_cast<size_t>(nt), 0.0f);
     M.lconn.assign(nt, 0);
     M.slot.assign(nt, 0);
@@ -218,75 +282,53 @@ bool build_pad_mesh(int nv, int nt, int nf, int nm, const float* rest, const int
     M.pcsr.clear();
     std::vector<int> local(nv, -1);
     std::vector<int> first_patch(nv, -1), last_patch(nv, -1);
-    std::vector<int> cur_verts;
-    int begin = 0;
-    auto flush = [&](int end) {
-        // local vertex list sorted by mesh id, local ids remapped accordingly
-        std::vector<int> verts = cur_verts;
-        std::sort(verts.begin(), verts.end());
-        int pidx = static_cast<int>(M.patch.size() / 4);
+    int tpos = 0;
+    for (int pi = 0; pi < np0; ++pi) {
+        const std::vector<int>& tl = ptets[porder[pi]];
+        std::vector<int> verts = pverts[porder[pi]];
+        std::sort(verts.begin(), verts.end());        // local ids follow mesh ids
         for (size_t l = 0; l < verts.size(); ++l) local[verts[l]] = static_cast<int>(l);
         int nloc = static_cast<int>(verts.size());
-        int ntl = end - begin;
+        int ntl = static_cast<int>(tl.size());
         // corner slots: for each local vertex, its (tet, corner) pairs in (tet, corner) order
         std::vector<int> count(nloc + 1, 0);
-        for (int k = begin; k < end; ++k) {
-            const int* c = tets + 4 * static_cast<size_t>(M.tet_order[k]);
+        for (int t : tl) {
+            const int* c = tets + 4 * static_cast<size_t>(t);
             for (int j = 0; j < 4; ++j) count[local[c[j]] + 1]++;
         }
         for (int l = 0; l < nloc; ++l) count[l + 1] += count[l];
         std::vector<int> cursor(count.begin(), count.end() - 1);
         int csr_begin = static_cast<int>(M.pcsr.size());
         for (int l = 0; l <= nloc; ++l) M.pcsr.push_back(static_cast<uint16_t>(count[l]));
-        for (int k = begin; k < end; ++k) {
-            int t = M.tet_order[k];
+        int tb = tpos;
+        for (int t : tl) {
             const int* c = tets + 4 * static_cast<size_t>(t);
-            uint32_t lc = 0;
-            uint64_t sl = 0;
+            uint32_t lc = 0, sl = 0;
             for (int j = 0; j < 4; ++j) {
                 int l = local[c[j]];
                 lc |= static_cast<uint32_t>(l) << (8 * j);
-                sl |= static_cast<uint64_t>(cursor[l]++) << (16 * j);
+                sl |= static_cast<uint32_t>(cursor[l]++) << (8 * j);
             }
-            M.lconn[k] = lc;
-            M.slot[k] = sl;
-            for (int e = 0; e < 9; ++e) M.B[static_cast<size_t>(e) * nt + k] = static_cast<float>(Binv[9 * static_cast<size_t>(t) + e]);
+            M.lconn[tpos] = lc;
+            M.slot[tpos] = sl;
+            M.tet_order[tpos] = t;
+            for (int e = 0; e < 9; ++e)
+                M.B[static_cast<size_t>(e) * nt + tpos] = static_cast<float>(Binv[9 * static_cast<size_t>(t) + e]);
+            ++tpos;
         }
         int vert_begin = static_cast<int>(M.pvert.size());
         for (int v : verts) {
             M.pvert.push_back(v);
-            if (first_patch[v] < 0) first_patch[v] = pidx;
-            last_patch[v] = pidx;
+            if (first_patch[v] < 0) first_patch[v] = pi;
+            last_patch[v] = pi;
             local[v] = -1;
         }
-        M.patch.push_back(begin);
+        M.patch.push_back(tb);
         M.patch.push_back(vert_begin);
         M.patch.push_back(ntl | (nloc << 16));
         M.patch.push_back(csr_begin);
-        cur_verts.clear();
-        begin = end;
-    };
-    for (int k = 0; k < nt; ++k) {
-        const int* c = tets + 4 * static_cast<size_t>(M.tet_order[k]);
-        int add = 0;
-        for (int j = 0; j < 4; ++j) {
-            bool seen = local[c[j]] >= 0;
-            for (int jj = 0; jj < j; ++jj) seen = seen || (c[jj] == c[j]);
-            add += seen ? 0 : 1;
-        }
-        if (k - begin >= kPatchTets || static_cast<int>(cur_verts.size()) + add > kPatchVerts) {
-            for (int v : cur_verts) local[v] = -1;
-            flush(k);
-        }
-        for (int j = 0; j < 4; ++j)
-            if (local[c[j]] < 0) {
-                local[c[j]] = 1;
-                cur_verts.push_back(c[j]);
-            }
     }
-    for (int v : cur_verts) local[v] = -1;
-    flush(nt);
-    // first / last flags
+    // first / last flags (processing order: colour-major)
     int np = M.n_patch();
     for (int p = 0; p < np; ++p) {
         int vb = M.patch[4 * p + 1], nl = M.patch[4 * p + 2] >> 16;

@@ -12,10 +12,10 @@
 
 namespace tac {
 
-// Limits of one tet patch: its tets are processed one per thread of a CTA and
-// its vertices are addressed with 8-bit local indices.
-constexpr int kPatchTets = 256;
-constexpr int kPatchVerts = 256;
+// Limits of one tet patch: a warp processes it with one tet per lane and one
+// vertex per lane when the patch's corner contributions are reduced.
+constexpr int kPatchTets = 32;
+constexpr int kPatchVerts = 32;
 
 // Flags carried in the high bits of a patch's vertex list entry.
 constexpr int kFirstFlag = 1 << 30;   // first patch (in processing order) touching the vertex
@@ -30,11 +30,12 @@ struct PadMesh {
     // tets in patch order
     std::vector<float> B;             // [9][n_t] Dm^-1 (row-major entries), SoA
     std::vector<uint32_t> lconn;      // [n_t] 4 x 8-bit local vertex ids
-    std::vector<uint64_t> slot;       // [n_t] 4 x 16-bit corner slots in the patch CSR
+    std::vector<uint32_t> slot;       // [n_t] 4 x 8-bit corner slots in the patch CSR
     std::vector<int> patch;           // [n_patch*4] tet_begin, vert_begin, n_t | n_v << 16, csr_begin
     std::vector<int> pvert;           // per patch local vertex -> mesh vertex id | flags
     std::vector<uint16_t> pcsr;       // per patch CSR offsets (n_v + 1 entries)
     std::vector<int> tet_order;       // patch-order position -> input tet id
+    std::vector<int> colour_off;      // patches of colour c: [colour_off[c], colour_off[c+1])
     // canonical surface
     std::vector<int> sv;              // surface vertex ids, sorted
     std::vector<int> st;              // [n_st*3] surface triangles (sorted ids), sorted
@@ -44,6 +45,7 @@ struct PadMesh {
     std::vector<int> mk_ids;          // [n_mk*3]
     std::vector<float> mk_w;          // [n_mk*3]
     int n_patch() const { return static_cast<int>(patch.size() / 4); }
+    int n_colour() const { return static_cast<int>(colour_off.size()) - 1; }
 };
 
 struct IndenterMesh {

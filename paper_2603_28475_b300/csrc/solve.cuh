@@ -16,12 +16,13 @@
 namespace tac {
 
 constexpr int kThreads = 256;
-constexpr int kStage = 4 * 256;      // corner slots of one patch
+constexpr int kStage = 4 * 32;       // corner slots of one warp-sized tet patch
 
 struct MeshDev {
     int xv_off, n_v;          // static per-vertex arrays (X, vlump, fixed)
     int tet_off, n_t;         // tet arrays (B, lconn, slot)
     int patch_off, n_patch;
+    int col_off, n_col;       // colour classes: patches [colour[col_off+c], colour[col_off+c+1])
     int pvert_off, pcsr_off;
     int sv_off, n_sv, st_off, n_st, se_off, n_se;
     int mk_off, n_mk;
@@ -67,7 +68,8 @@ struct Dev {
     const float* B;           // [9][Tt]
     int Tt;
     const uint32_t* lconn;    // [Tt]
-    const uint64_t* slot;     // [Tt]
+    const uint32_t* slot;     // [Tt] 4 x 8-bit corner slots
+    const int* colour;        // per mesh colour offsets into its patch list
     const int4* patch;
     const int* pvert;
     const uint16_t* pcsr;
