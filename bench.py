@@ -269,6 +269,7 @@ def run_ours(args, rank, world):
     total_ms = start.elapsed_time(stop)
     solve_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
     phase = np.zeros(8)
+    pad_ms_max = 0.0
     for stt, it, st in stats_all:
         s_np = stt.cpu().numpy().reshape(-1, w.pads_per_env)
         conv += int(np.all(s_np == 0, axis=1).sum())
@@ -276,8 +277,13 @@ def run_ours(args, rank, world):
         st_np = st.cpu().numpy()
         bytes_alg += algorithmic_bytes(st_np, w)
         phase += st_np[:, 8:16].sum(axis=0)
+        pad_ms_max = max(pad_ms_max, float(st_np[:, 15].max()) / 1e6)
     names = ["tet_pHp", "tet_grad", "pair_pHp", "pair_grad", "vertex", "advance_rebuild", "setup"]
     phase_share = {n: float(phase[i] / phase[7]) for i, n in enumerate(names)} if phase[7] > 0 else None
+    # CTA-time spent inside pads over the launch's CTA-time: below 1 the grid idles
+    # behind the queue's last pads
+    queue = {"ctas": b.grid_ctas, "busy": float(phase[7] / 1e6 / (b.grid_ctas * sum(solve_ms))),
+             "longest_pad_ms": pad_ms_max}
     if world > 1:
         t = torch.tensor([total_ms, float(conv)], dtype=torch.float64, device=dev)
         mx = t.clone()
@@ -352,7 +358,7 @@ def run_ours(args, rank, world):
                "iters_per_pad_frame": {"p50": float(np.percentile(its, 50)), "p99": float(np.percentile(its, 99)),
                                        "max": int(its.max())},
                "frame_ms": {"p50": float(np.percentile(solve_ms, 50)), "p99": float(np.percentile(solve_ms, 99))},
-               "setup_s": t_create, "phase_share": phase_share}
+               "setup_s": t_create, "phase_share": phase_share, "queue": queue}
         print(json.dumps(out), flush=True)
     b.close()
 

@@ -109,8 +109,8 @@ typedef struct {
 } tac_options;
 
 /* Create a batch of n_pads pads, pads_per_env consecutive pads per
- * environment (n_pads = n_envs * pads_per_env), one indenter per
- * environment. params has n_pads entries. opts may be NULL (defaults).
+ * environment (n_pads = n_envs * pads_per_env, at most 2^24), one indenter
+ * per environment. params has n_pads entries. opts may be NULL (defaults).
  * Validates every mesh on the host (TAC_ERR_INVALID_MESH with the pad index
  * in tac_last_error), builds the rest shape (Dm^-1, volumes, lumped masses),
  * surface primitives, marker weights and the tet patches, allocates all
@@ -139,7 +139,10 @@ int tac_set_indenter(tac_handle h, const float* pose6_dev, const float* twist6_d
  * its target pose and minimise E (Supp. A). Writes the per-pad status
  * (TAC_PAD_*) and iteration count to caller-owned device arrays
  * pad_status_dev [n_pads] and iters_dev [n_pads] (either may be NULL), then
- * v = (x - x^t) / h and the current pose becomes the target pose. */
+ * v = (x - x^t) / h and the current pose becomes the target pose.
+ * Each pad is solved whole by one CTA of a persistent launch that takes pads
+ * from a queue, longest first: the order is by the pad's solve time in its
+ * previous frame, then by its tet count. Results do not depend on the order. */
 int tac_step(tac_handle h, int* pad_status_dev, int* iters_dev, void* stream);
 
 /* Adjoint of the last frame (north star "Differentiation"; the paper itself
@@ -255,8 +258,10 @@ int tac_stats(tac_handle h, long long* stats_dev, void* stream);
  * below a few hundred ulps of the forces summed into it. */
 int tac_pad_norms(tac_handle h, double* norms_dev, void* stream);
 
-/* Sizes: total vertices, total markers, candidate capacity per pad. */
-int tac_sizes(tac_handle h, int* total_verts, int* total_markers, int* pair_capacity);
+/* Sizes: total vertices, total markers, candidate capacity per pad, and the
+ * number of CTAs of one tac_step launch (resident CTAs of the device, at most
+ * one per pad). Any output pointer may be NULL. */
+int tac_sizes(tac_handle h, int* total_verts, int* total_markers, int* pair_capacity, int* grid_ctas);
 
 /* Message of the last error on this thread (static storage, never NULL). */
 const char* tac_last_error(void);

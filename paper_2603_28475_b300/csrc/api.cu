@@ -19,6 +19,7 @@ __global__ void debug_eval_kernel(const __grid_constant__ Dev D, float alpha, do
 __global__ void broadphase_kernel(const __grid_constant__ Dev D, int pad, const float* x, const float* y, double r, int* out, int cap,
                                   int* count);
 __global__ void markers_kernel(const __grid_constant__ Dev D, float* out);
+__global__ void schedule_kernel(const __grid_constant__ Dev D, unsigned long long* key, int* idx, int n2, int* order);
 __global__ void adjoint_kernel(const __grid_constant__ Dev D, const float* dLdm, double* out, int* status, int* iters,
                                int max_iter, float tol);
 size_t shared_bytes();
@@ -171,6 +172,10 @@ struct tac_batch {
     float* d_hstep = nullptr;
     float* d_pose_t = nullptr;
     float* d_pose_n = nullptr;
+    int* d_order = nullptr;                 // processing order, rewritten before each solve
+    unsigned long long* d_sched_key = nullptr;
+    int* d_sched_idx = nullptr;
+    int sched_n2 = 1;                       // next power of two >= n_pads
 };
 
 namespace {
@@ -211,8 +216,8 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     if (!out) return fail(TAC_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!pads || !params || !indenters || n_pads <= 0 || n_envs <= 0 || pads_per_env <= 0 ||
-        n_pads != n_envs * pads_per_env)
-        return fail(TAC_ERR_INVALID_ARG, "need n_pads = n_envs * pads_per_env > 0 and non-null arrays");
+        n_pads > (1 << 24) || (long long)n_envs * pads_per_env != n_pads)
+        return fail(TAC_ERR_INVALID_ARG, "need 0 < n_pads = n_envs * pads_per_env <= 2^24 and non-null arrays");
     for (int p = 0; p < n_pads; ++p)
         if (!params_ok(params[p])) return fail(TAC_ERR_INVALID_ARG, "invalid parameters for pad " + std::to_string(p));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -379,6 +384,10 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     float* adj_r = dalloc<float>(K, 3 * (size_t)Vt, rc);
     int* queue = dalloc<int>(K, 1, rc);
     int* order_d = dalloc<int>(K, n_pads, rc);
+    b->d_order = order_d;
+    while (b->sched_n2 < n_pads) b->sched_n2 <<= 1;
+    b->d_sched_key = dalloc<unsigned long long>(K, b->sched_n2, rc);
+    b->d_sched_idx = dalloc<int>(K, b->sched_n2, rc);
     b->d_meshes = dalloc<MeshDev>(K, b->hmesh.size(), rc);
     b->d_pads = dalloc<PadDev>(K, n_pads, rc);
     b->d_envs = dalloc<EnvDev>(K, b->henv.size(), rc);
@@ -538,6 +547,9 @@ int tac_step(tac_handle h, int* pad_status_dev, int* iters_dev, void* stream) {
     D.status = pad_status_dev;
     D.iters = iters_dev;
     CUDA_TRY(cudaMemsetAsync(D.queue, 0, sizeof(int), st));
+    // longest predicted pad first (its previous solve time, then its size)
+    schedule_kernel<<<1, 1024, 0, st>>>(D, h->d_sched_key, h->d_sched_idx, h->sched_n2, h->d_order);
+    CUDA_TRY(cudaGetLastError());
     solve_kernel<<<h->grid, kThreads, shared_bytes(), st>>>(D);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaMemcpyAsync(h->d_pose_t, h->d_pose_n, 6 * (size_t)h->n_pads * 4, cudaMemcpyDeviceToDevice, st));
@@ -646,11 +658,12 @@ int tac_pad_norms(tac_handle h, double* norms_dev, void* stream) {
     return TAC_OK;
 }
 
-int tac_sizes(tac_handle h, int* total_verts, int* total_markers, int* pair_capacity) {
+int tac_sizes(tac_handle h, int* total_verts, int* total_markers, int* pair_capacity, int* grid_ctas) {
     if (!h) return fail(TAC_ERR_INVALID_ARG, "null handle");
     if (total_verts) *total_verts = h->Vt;
     if (total_markers) *total_markers = h->total_markers;
     if (pair_capacity) *pair_capacity = h->pair_cap;
+    if (grid_ctas) *grid_ctas = h->grid;
     return TAC_OK;
 }
 

@@ -1652,6 +1652,55 @@ __global__ void __launch_bounds__(kThreads, 2) solve_kernel(const __grid_constan
 }
 
 // ---------------------------------------------------------------------------
+// processing order of the next solve launch: longest predicted pad first.
+// The prediction is the pad's solve time in its previous frame (0 before its
+// first frame), the tet count breaking ties, so the first frame runs the
+// largest meshes first. One CTA sorts (key descending, pad ascending) with a
+// bitonic network over n2 = next power of two >= n_pads entries of global
+// scratch; the padding entries (key 0, index INT_MAX) sort last.
+
+__device__ __forceinline__ bool sched_before(unsigned long long ka, int ia, unsigned long long kb, int ib) {
+    return ka > kb || (ka == kb && ia < ib);
+}
+
+__global__ void __launch_bounds__(1024) schedule_kernel(const __grid_constant__ Dev D, unsigned long long* key,
+                                                        int* idx, int n2, int* order) {
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        if (i < D.n_pads) {
+            long long ns = D.stats[16 * (size_t)i + 15];
+            unsigned long long t = ns > 0 ? (unsigned long long)ns : 0ull;
+            t = t < (1ull << 40) ? t : (1ull << 40) - 1;
+            int nt = D.meshes[D.pads[i].mesh].n_t;
+            key[i] = (t << 22) | (unsigned long long)min(nt, (1 << 22) - 1);
+            idx[i] = i;
+        } else {
+            key[i] = 0ull;
+            idx[i] = 0x7fffffff;
+        }
+    }
+    __syncthreads();
+    for (int k = 2; k <= n2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+                int l = i ^ j;
+                if (l > i) {
+                    unsigned long long ki = key[i], kl = key[l];
+                    int ii = idx[i], il = idx[l];
+                    bool up = (i & k) == 0;
+                    bool swap = up ? sched_before(kl, il, ki, ii) : sched_before(ki, ii, kl, il);
+                    if (swap) {
+                        key[i] = kl; key[l] = ki;
+                        idx[i] = il; idx[l] = ii;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < D.n_pads; i += blockDim.x) order[i] = idx[i];
+}
+
+// ---------------------------------------------------------------------------
 // verification kernel: one CTA per pad (see tac_debug_eval)
 
 __global__ void __launch_bounds__(kThreads) debug_eval_kernel(const __grid_constant__ Dev D, float alpha, double r, float* grad_out,

@@ -72,7 +72,7 @@ def load_library(path=_LIB_PATH):
         "tac_debug_eval": [vp, vp, vp, f, vp, vp, vp, vp],
         "tac_stats": [vp, vp, vp],
         "tac_pad_norms": [vp, vp, vp],
-        "tac_sizes": [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)],
+        "tac_sizes": [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -168,9 +168,10 @@ class TacBatch:
                                       ctypes.byref(h)))
         self._h = h
         self.n_pads = n
-        tv, tm, cap = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        _check(lib().tac_sizes(h, ctypes.byref(tv), ctypes.byref(tm), ctypes.byref(cap)))
+        tv, tm, cap, gr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().tac_sizes(h, ctypes.byref(tv), ctypes.byref(tm), ctypes.byref(cap), ctypes.byref(gr)))
         self.total_verts, self.total_markers, self.pair_capacity = tv.value, tm.value, cap.value
+        self.grid_ctas = gr.value
         self.vert_offsets = np.cumsum([0] + [int(np.asarray(p.rest).shape[0]) for p in pads])
         self.marker_offsets = np.cumsum([0] + [int(np.asarray(p.markers).shape[0]) for p in pads])
         self.device = torch.device("cuda", torch.cuda.current_device())
