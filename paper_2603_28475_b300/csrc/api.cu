@@ -276,13 +276,13 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
         iseen[key] = id;
     }
     // layouts
-    int XVt = 0, Tt = 0, np_tot = 0, pv_tot = 0, pc_tot = 0, sv_tot = 0, st_tot = 0, se_tot = 0, mk_tot = 0;
+    int XVt = 0, Tt = 0, pv_tot = 0, pc_tot = 0, sv_tot = 0, st_tot = 0, se_tot = 0, mk_tot = 0;
     int col_tot = 0;
     for (auto& M : b->meshes) {
         MeshDev md{};
         md.xv_off = XVt; md.n_v = M.n_v;
         md.tet_off = Tt; md.n_t = M.n_t;
-        md.patch_off = np_tot; md.n_patch = M.n_patch();
+        md.n_patch = M.n_patch();
         md.pvert_off = pv_tot; md.pcsr_off = pc_tot;
         md.sv_off = sv_tot; md.n_sv = (int)M.sv.size();
         md.st_off = st_tot; md.n_st = (int)(M.st.size() / 3);
@@ -290,7 +290,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
         md.mk_off = mk_tot; md.n_mk = M.n_mk;
         md.col_off = col_tot; md.n_col = M.n_colour();
         col_tot += (int)M.colour_off.size();
-        XVt += M.n_v; Tt += M.n_t; np_tot += M.n_patch(); pv_tot += (int)M.pvert.size();
+        XVt += M.n_v; Tt += M.n_slots(); pv_tot += (int)M.pvert.size();
         pc_tot += (int)M.pcsr.size(); sv_tot += md.n_sv; st_tot += md.n_st; se_tot += md.n_se; mk_tot += M.n_mk;
         b->hmesh.push_back(md);
     }
@@ -346,7 +346,6 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     float* B = dalloc<float>(K, 9 * (size_t)Tt, rc);
     uint32_t* lconn = dalloc<uint32_t>(K, Tt, rc);
     uint32_t* slot = dalloc<uint32_t>(K, Tt, rc);
-    int4* patch = dalloc<int4>(K, np_tot, rc);
     int* pvert = dalloc<int>(K, pv_tot, rc);
     uint16_t* pcsr = dalloc<uint16_t>(K, pc_tot, rc);
     int* sv = dalloc<int>(K, sv_tot, rc);
@@ -403,7 +402,6 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     std::vector<uint32_t> hlc(Tt);
     std::vector<uint32_t> hsl(Tt);
     std::vector<int> hcol;
-    std::vector<int4> hpatch;
     std::vector<int> hpv, hsv, hst, hse, hmki, hit, hie;
     std::vector<uint16_t> hpc;
     for (size_t m = 0; m < b->meshes.size(); ++m) {
@@ -414,13 +412,12 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
             hvl[md.xv_off + i] = M.vlump[i];
             hfx[md.xv_off + i] = M.fixed[i];
         }
-        for (int t = 0; t < M.n_t; ++t) {
-            for (int e = 0; e < 9; ++e) hB[(size_t)e * Tt + md.tet_off + t] = M.B[(size_t)e * M.n_t + t];
+        const int ns = M.n_slots();
+        for (int t = 0; t < ns; ++t) {
+            for (int e = 0; e < 9; ++e) hB[(size_t)e * Tt + md.tet_off + t] = M.B[(size_t)e * ns + t];
             hlc[md.tet_off + t] = M.lconn[t];
             hsl[md.tet_off + t] = M.slot[t];
         }
-        for (int q = 0; q < M.n_patch(); ++q)
-            hpatch.push_back(make_int4(M.patch[4 * q], M.patch[4 * q + 1], M.patch[4 * q + 2], M.patch[4 * q + 3]));
         hpv.insert(hpv.end(), M.pvert.begin(), M.pvert.end());
         hpc.insert(hpc.end(), M.pcsr.begin(), M.pcsr.end());
         hsv.insert(hsv.end(), M.sv.begin(), M.sv.end());
@@ -448,7 +445,6 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     r2 |= up(lconn, hlc.data(), hlc.size() * 4);
     r2 |= up(slot, hsl.data(), hsl.size() * 4);
     r2 |= up(colour, hcol.data(), hcol.size() * 4);
-    r2 |= up(patch, hpatch.data(), hpatch.size() * sizeof(int4));
     r2 |= up(pvert, hpv.data(), hpv.size() * 4);
     r2 |= up(pcsr, hpc.data(), hpc.size() * 2);
     r2 |= up(sv, hsv.data(), hsv.size() * 4);
@@ -486,7 +482,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     D.pads = b->d_pads;
     D.order = order_d;
     D.X = X; D.vlump = vlump; D.fixed = fixed; D.B = B; D.lconn = lconn; D.slot = slot; D.colour = colour;
-    D.patch = patch; D.pvert = pvert; D.pcsr = pcsr; D.sv = sv; D.st = stt; D.se = se;
+    D.pvert = pvert; D.pcsr = pcsr; D.sv = sv; D.st = stt; D.se = se;
     D.mk_ids = mk_ids; D.mk_w = mk_w; D.Y = Y; D.it = it; D.ie = ie; D.Yt = Yt; D.Yn = Yn;
     D.pose_t = b->d_pose_t; D.pose_n = b->d_pose_n;
     D.uh = st3[0]; D.ul = st3[1]; D.u0h = st3[2]; D.u0l = st3[3]; D.vel = st3[4]; D.uhat = st3[5];

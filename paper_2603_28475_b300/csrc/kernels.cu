@@ -37,11 +37,12 @@ constexpr float kFloat32Floor = 256.0f / 16777216.0f;
 // memory (one tet and one vertex per lane)
 struct PatchStage {
     float B[9][32];             // Dm^-1 entries of the patch's tets
-    uint32_t lc[32];            // 4 x 8-bit local vertex ids
+    uint32_t lc[32];            // 4 x 8-bit local vertex ids (kNoTet: unused slot)
     uint32_t sl[32];            // 4 x 8-bit corner slots
     float uh[3][32];            // displacement (hi) of the patch's vertices
     float ul[3][32];            // displacement (lo)
     float p[3][32];             // direction
+    float og[9][32];            // scatter passes: the vertices' sums so far (gradient, blocks)
 };
 
 // per-warp scratch of the tet passes
@@ -332,37 +333,43 @@ struct TetOut {
     double acc2;      // mu-sensitivity (pass 3)
 };
 
-struct PatchHdr {
-    int tb, vb, nt, nv, cb;
-};
-
-__device__ __forceinline__ PatchHdr patch_hdr(const Dev& D, const MeshDev& M, int pi) {
-    int4 ph = __ldg(D.patch + M.patch_off + pi);
-    return PatchHdr{ph.x, ph.y, ph.z & 0xffff, ph.z >> 16, ph.w};
-}
-
-// asynchronous copy of one warp patch (tet data and raw vertex data) into a
-// stage; lane k copies tet k and vertex k
-__device__ __forceinline__ void issue_patch(const Dev& D, const PadDev& P, const MeshDev& M, const PatchHdr& h,
-                                            PatchStage& st, int lane) {
-    if (lane < h.nt) {
-        size_t t = (size_t)M.tet_off + h.tb + lane;
+// asynchronous copy of one warp patch into a stage; lane k copies tet slot k
+// and, when the patch has a vertex entry k (gvf >= 0), that vertex's data.
+// The scatter passes also copy the vertex's sums so far when this is not its
+// first patch: patches of one colour class share no vertex and earlier
+// classes are complete, so those sums are final when the copy is issued.
+template <int PASS>
+__device__ __forceinline__ void issue_patch(const Dev& D, const PadDev& P, const MeshDev& M, int pi, int gvf,
+                                            PatchStage& st, int lane, int gb) {
+    {
+        size_t t = (size_t)M.tet_off + (size_t)kPatchTets * pi + lane;
 #pragma unroll
         for (int e = 0; e < 9; ++e) cp_async4(&st.B[e][lane], D.B + (size_t)e * D.Tt + t);
         cp_async4(&st.lc[lane], D.lconn + t);
         cp_async4(&st.sl[lane], D.slot + t);
     }
-    if (lane < h.nv) {
-        int gvf = __ldg(D.pvert + M.pvert_off + h.vb + lane);
-        int si = P.v_off + (gvf & ((1 << 29) - 1));
+    if (gvf >= 0) {
+        int si = P.v_off + (gvf & kVertMask);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             cp_async4(&st.uh[c][lane], D.uh + (size_t)c * D.Vt + si);
             cp_async4(&st.ul[c][lane], D.ul + (size_t)c * D.Vt + si);
             cp_async4(&st.p[c][lane], D.p + (size_t)c * D.Vt + si);
         }
+        if ((PASS == 1 || PASS == 2) && !(gvf & kFirstFlag)) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) cp_async4(&st.og[c][lane], D.g[gb] + (size_t)c * D.Vt + si);
+            if (PASS == 1) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) cp_async4(&st.og[3 + c][lane], D.blk[gb] + (size_t)c * D.Vt + si);
+            }
+        }
     }
     cp_async_commit();
+}
+
+__device__ __forceinline__ int patch_vert(const Dev& D, const MeshDev& M, int pi, int lane) {
+    return __ldg(D.pvert + M.pvert_off + kPatchVerts * pi + lane);
 }
 
 // pass 0: p^T H_e p at u; pass 1: gradient, diagonal blocks and remainder at
@@ -388,29 +395,31 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
         const int p_end = kScatter ? __ldg(D.colour + M.col_off + cls + 1) : M.n_patch;
         int pi = p_begin + warp;
         int b = 0;
-        PatchHdr hc{0, 0, 0, 0, 0};
+        // vertex entries of this lane: current patch (gvf_c), the next one
+        // (gvf_n, loaded one patch ahead so that issuing its copy does not wait)
+        int gvf_c = -1, gvf_n = -1;
         if (pi < p_end) {
-            hc = patch_hdr(D, M, pi);
-            issue_patch(D, P, M, hc, W.st[0], lane);
+            gvf_c = patch_vert(D, M, pi, lane);
+            issue_patch<PASS>(D, P, M, pi, gvf_c, W.st[0], lane, gb);
+            if (pi + kWarps < p_end) gvf_n = patch_vert(D, M, pi + kWarps, lane);
         }
         while (pi < p_end) {
             const int pn = pi + kWarps;
             cp_async_wait_all();
             __syncwarp();                       // stage b complete for every lane
-            int gvf_c = 0, s0 = 0, s1 = 0;
-            if (kScatter && lane < hc.nv) {
-                gvf_c = __ldg(D.pvert + M.pvert_off + hc.vb + lane);
-                s0 = __ldg(D.pcsr + M.pcsr_off + hc.cb + lane);
-                s1 = __ldg(D.pcsr + M.pcsr_off + hc.cb + lane + 1);
+            int s0 = 0, s1 = 0;
+            if (kScatter) {
+                s0 = __ldg(D.pcsr + M.pcsr_off + kPatchCsr * pi + lane);
+                s1 = __ldg(D.pcsr + M.pcsr_off + kPatchCsr * pi + lane + 1);
             }
-            PatchHdr hn{0, 0, 0, 0, 0};
+            int gvf_nn = -1;
             if (pn < p_end) {
-                hn = patch_hdr(D, M, pn);
-                issue_patch(D, P, M, hn, W.st[b ^ 1], lane);
+                issue_patch<PASS>(D, P, M, pn, gvf_n, W.st[b ^ 1], lane, gb);
+                if (pn + kWarps < p_end) gvf_nn = patch_vert(D, M, pn + kWarps, lane);
             }
             const PatchStage& st = W.st[b];
-                if (lane < hc.nt) {
-                uint32_t lc = st.lc[lane];
+            const uint32_t lc = st.lc[lane];
+            if (lc != kNoTet) {
                 int l0 = lc & 255, l1 = (lc >> 8) & 255, l2 = (lc >> 16) & 255, l3 = lc >> 24;
                 float Bm[9];
     #pragma unroll
@@ -547,29 +556,24 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
 
             if (PASS == 2) {
                 __syncwarp();                   // every corner of the patch staged
-                if (lane < hc.nv) {
-                    int gv = gvf_c & ((1 << 29) - 1);
-                    bool first = (gvf_c & (1 << 30)) != 0;
+                if (gvf_c >= 0) {
+                    int gv = gvf_c & kVertMask;
+                    bool first = (gvf_c & kFirstFlag) != 0;
                     float acc[3] = {0.f, 0.f, 0.f};
                     for (int q = s0; q < s1; ++q)
 #pragma unroll
                         for (int c = 0; c < 3; ++c) acc[c] += W.stg[c][q];
                     float* g = D.g[gb];
                     int si = P.v_off + gv;
-                    if (first) {
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) g[c * D.Vt + si] = acc[c];
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) g[c * D.Vt + si] += acc[c];
-                    }
+                    for (int c = 0; c < 3; ++c) g[c * D.Vt + si] = first ? acc[c] : st.og[c][lane] + acc[c];
                 }
             }
             if (PASS == 1) {
                 __syncwarp();                   // every corner of the patch staged
-                if (lane < hc.nv) {
-                    int gv = gvf_c & ((1 << 29) - 1);
-                    bool first = (gvf_c & (1 << 30)) != 0;
+                if (gvf_c >= 0) {
+                    int gv = gvf_c & kVertMask;
+                    bool first = (gvf_c & kFirstFlag) != 0;
                     float acc[9];
 #pragma unroll
                     for (int c = 0; c < 9; ++c) acc[c] = 0.f;
@@ -579,21 +583,15 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
                     int si = P.v_off + gv;
                     float* g = D.g[gb];
                     float* k = D.blk[gb];
-                    if (first) {
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) g[c * D.Vt + si] = acc[c];
+                    for (int c = 0; c < 3; ++c) g[c * D.Vt + si] = first ? acc[c] : st.og[c][lane] + acc[c];
 #pragma unroll
-                        for (int c = 0; c < 6; ++c) k[c * D.Vt + si] = acc[3 + c];
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) g[c * D.Vt + si] += acc[c];
-#pragma unroll
-                        for (int c = 0; c < 6; ++c) k[c * D.Vt + si] += acc[3 + c];
-                    }
+                    for (int c = 0; c < 6; ++c) k[c * D.Vt + si] = first ? acc[3 + c] : st.og[3 + c][lane] + acc[3 + c];
                 }
             }
             __syncwarp();                       // lanes done with stage b and the corner slots
-            hc = hn;
+            gvf_c = gvf_n;
+            gvf_n = gvf_nn;
             pi = pn;
             b ^= 1;
         }

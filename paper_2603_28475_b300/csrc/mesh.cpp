@@ -274,15 +274,16 @@ bool build_pad_mesh(int nv, int nt, int nf, int nm, const float* rest, const int
     for (int q = 0; q < np0; ++q) M.colour_off[colour[q] + 1]++;
     for (int c = 0; c < ncol; ++c) M.colour_off[c + 1] += M.colour_off[c];
 
-    M.B.assign(9 * static_cast<size_t>(nt), 0.0f);
-    M.lconn.assign(nt, 0);
-    M.slot.assign(nt, 0);
+    const size_t nsl = static_cast<size_t>(np0) * kPatchTets;
+    M.B.assign(9 * nsl, 0.0f);
+    M.lconn.assign(nsl, kNoTet);
+    M.slot.assign(nsl, 0);
+    M.tet_order.assign(nsl, -1);
     M.patch.clear();
-    M.pvert.clear();
-    M.pcsr.clear();
+    M.pvert.assign(static_cast<size_t>(np0) * kPatchVerts, -1);
+    M.pcsr.assign(static_cast<size_t>(np0) * kPatchCsr, 0);
     std::vector<int> local(nv, -1);
     std::vector<int> first_patch(nv, -1), last_patch(nv, -1);
-    int tpos = 0;
     for (int pi = 0; pi < np0; ++pi) {
         const std::vector<int>& tl = ptets[porder[pi]];
         std::vector<int> verts = pverts[porder[pi]];
@@ -291,17 +292,18 @@ bool build_pad_mesh(int nv, int nt, int nf, int nm, const float* rest, const int
         int nloc = static_cast<int>(verts.size());
         int ntl = static_cast<int>(tl.size());
         // corner slots: for each local vertex, its (tet, corner) pairs in (tet, corner) order
-        std::vector<int> count(nloc + 1, 0);
+        std::vector<int> count(kPatchCsr, 0);
         for (int t : tl) {
             const int* c = tets + 4 * static_cast<size_t>(t);
             for (int j = 0; j < 4; ++j) count[local[c[j]] + 1]++;
         }
-        for (int l = 0; l < nloc; ++l) count[l + 1] += count[l];
+        for (int l = 0; l < kPatchVerts; ++l) count[l + 1] += count[l];   // unused entries: empty runs
         std::vector<int> cursor(count.begin(), count.end() - 1);
-        int csr_begin = static_cast<int>(M.pcsr.size());
-        for (int l = 0; l <= nloc; ++l) M.pcsr.push_back(static_cast<uint16_t>(count[l]));
-        int tb = tpos;
-        for (int t : tl) {
+        const int csr_begin = pi * kPatchCsr;
+        for (int l = 0; l < kPatchCsr; ++l) M.pcsr[csr_begin + l] = static_cast<uint16_t>(count[l]);
+        const int tb = pi * kPatchTets;
+        for (int k = 0; k < ntl; ++k) {
+            const int t = tl[k];
             const int* c = tets + 4 * static_cast<size_t>(t);
             uint32_t lc = 0, sl = 0;
             for (int j = 0; j < 4; ++j) {
@@ -309,16 +311,16 @@ bool build_pad_mesh(int nv, int nt, int nf, int nm, const float* rest, const int
                 lc |= static_cast<uint32_t>(l) << (8 * j);
                 sl |= static_cast<uint32_t>(cursor[l]++) << (8 * j);
             }
-            M.lconn[tpos] = lc;
-            M.slot[tpos] = sl;
-            M.tet_order[tpos] = t;
+            M.lconn[tb + k] = lc;
+            M.slot[tb + k] = sl;
+            M.tet_order[tb + k] = t;
             for (int e = 0; e < 9; ++e)
-                M.B[static_cast<size_t>(e) * nt + tpos] = static_cast<float>(Binv[9 * static_cast<size_t>(t) + e]);
-            ++tpos;
+                M.B[static_cast<size_t>(e) * nsl + tb + k] = static_cast<float>(Binv[9 * static_cast<size_t>(t) + e]);
         }
-        int vert_begin = static_cast<int>(M.pvert.size());
-        for (int v : verts) {
-            M.pvert.push_back(v);
+        const int vert_begin = pi * kPatchVerts;
+        for (int l = 0; l < nloc; ++l) {
+            int v = verts[l];
+            M.pvert[vert_begin + l] = v;
             if (first_patch[v] < 0) first_patch[v] = pi;
             last_patch[v] = pi;
             local[v] = -1;

@@ -10,31 +10,23 @@
 #include <string>
 #include <vector>
 
+#include "layout.h"
+
 namespace tac {
-
-// Limits of one tet patch: a warp processes it with one tet per lane and one
-// vertex per lane when the patch's corner contributions are reduced.
-constexpr int kPatchTets = 32;
-constexpr int kPatchVerts = 32;
-
-// Flags carried in the high bits of a patch's vertex list entry.
-constexpr int kFirstFlag = 1 << 30;   // first patch (in processing order) touching the vertex
-constexpr int kLastFlag = 1 << 29;    // last patch touching the vertex
-constexpr int kVertMask = (1 << 29) - 1;
 
 struct PadMesh {
     int n_v = 0, n_t = 0, n_mk = 0;
     std::vector<float> X;             // [n_v*3] rest positions
     std::vector<float> vlump;         // [n_v] lumped rest volume (sum of V/4); mass = rho * vlump
     std::vector<uint8_t> fixed;       // [n_v] 1 = Dirichlet
-    // tets in patch order
-    std::vector<float> B;             // [9][n_t] Dm^-1 (row-major entries), SoA
-    std::vector<uint32_t> lconn;      // [n_t] 4 x 8-bit local vertex ids
-    std::vector<uint32_t> slot;       // [n_t] 4 x 8-bit corner slots in the patch CSR
-    std::vector<int> patch;           // [n_patch*4] tet_begin, vert_begin, n_t | n_v << 16, csr_begin
-    std::vector<int> pvert;           // per patch local vertex -> mesh vertex id | flags
-    std::vector<uint16_t> pcsr;       // per patch CSR offsets (n_v + 1 entries)
-    std::vector<int> tet_order;       // patch-order position -> input tet id
+    // tets in patch order, kPatchTets slots per patch
+    std::vector<float> B;             // [9][n_slots] Dm^-1 (row-major entries), SoA
+    std::vector<uint32_t> lconn;      // [n_slots] 4 x 8-bit local vertex ids (kNoTet: unused slot)
+    std::vector<uint32_t> slot;       // [n_slots] 4 x 8-bit corner slots in the patch CSR
+    std::vector<int> patch;           // [n_patch*4] tet_begin, vert_begin, n_t | n_v << 16, csr_begin (host)
+    std::vector<int> pvert;           // [n_patch*kPatchVerts] mesh vertex id | flags, -1 unused
+    std::vector<uint16_t> pcsr;       // [n_patch*kPatchCsr] per patch CSR offsets
+    std::vector<int> tet_order;       // slot -> input tet id (-1 unused)
     std::vector<int> colour_off;      // patches of colour c: [colour_off[c], colour_off[c+1])
     // canonical surface
     std::vector<int> sv;              // surface vertex ids, sorted
@@ -45,6 +37,7 @@ struct PadMesh {
     std::vector<int> mk_ids;          // [n_mk*3]
     std::vector<float> mk_w;          // [n_mk*3]
     int n_patch() const { return static_cast<int>(patch.size() / 4); }
+    int n_slots() const { return n_patch() * kPatchTets; }
     int n_colour() const { return static_cast<int>(colour_off.size()) - 1; }
 };
 

@@ -4,24 +4,27 @@
 // path in CCD-bounded substeps, keeps the contact candidate set valid, and
 // runs the preconditioned nonlinear CG (Supp. A, Eq. dk_direction and
 // Eq. step_size) to convergence with only CTA-level barriers. The tet passes
-// stream spatial patches of <= 256 tets through shared memory; per-corner
-// contributions are summed per vertex through the patch's corner CSR
-// (a deterministic segmented reduction, no atomics).
+// stream warp-sized spatial patches of <= 32 tets through per-warp shared
+// memory stages; per-corner contributions are summed per vertex through the
+// patch's corner CSR (a deterministic segmented reduction, no atomics), and
+// patches of one colour class share no vertex.
 #pragma once
 
 #include <cstdint>
 
 #include "device_math.cuh"
+#include "layout.h"
 
 namespace tac {
 
 constexpr int kThreads = 256;
-constexpr int kStage = 4 * 32;       // corner slots of one warp-sized tet patch
+constexpr int kStage = 4 * kPatchTets;  // corner slots of one warp-sized tet patch
 
 struct MeshDev {
     int xv_off, n_v;          // static per-vertex arrays (X, vlump, fixed)
-    int tet_off, n_t;         // tet arrays (B, lconn, slot)
-    int patch_off, n_patch;
+    int tet_off, n_t;         // tet arrays (B, lconn, slot): kPatchTets slots per patch; n_t real tets
+    int n_patch;              // patch q: tet slots tet_off + 32 q, vertex entries pvert_off + 32 q,
+                              // CSR offsets pcsr_off + 33 q
     int col_off, n_col;       // colour classes: patches [colour[col_off+c], colour[col_off+c+1])
     int pvert_off, pcsr_off;
     int sv_off, n_sv, st_off, n_st, se_off, n_se;
@@ -65,12 +68,11 @@ struct Dev {
     int XVt;
     const float* vlump;       // [XVt]
     const uint8_t* fixed;     // [XVt]
-    const float* B;           // [9][Tt]
+    const float* B;           // [9][Tt], Tt = total tet slots
     int Tt;
     const uint32_t* lconn;    // [Tt]
     const uint32_t* slot;     // [Tt] 4 x 8-bit corner slots
     const int* colour;        // per mesh colour offsets into its patch list
-    const int4* patch;
     const int* pvert;
     const uint16_t* pcsr;
     const int* sv;
