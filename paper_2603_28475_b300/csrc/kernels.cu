@@ -53,7 +53,11 @@ struct WarpScratch {
 
 struct Shared {
     WarpScratch w[kWarps];
+    PadDev P;                   // descriptors of the CTA's current pad (see load_pad)
+    MeshDev M;
+    EnvDev E;
     double rd[kWarps][8];
+    double rsum[8];
     float rf[kWarps][4];
     int ri[kWarps];
     int cnt[4];
@@ -114,6 +118,18 @@ __device__ __forceinline__ bool over_budget(unsigned long long t0, unsigned long
     return e;
 }
 
+// The CTA's pad descriptors, identical for all its threads, go to shared
+// memory once per pad: the phase functions take them by reference, and a
+// per-thread copy would live on the stack and be re-read from local memory.
+__device__ __forceinline__ void load_pad(const Dev& D, int pad) {
+    if (threadIdx.x == 0) {
+        S.P = D.pads[pad];
+        S.M = D.meshes[S.P.mesh];
+        S.E = D.envs[S.P.env];
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // block-wide helpers (every thread receives the same result)
 
@@ -123,8 +139,11 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// K <= 8 sums; thread k adds the warps' partial sums of value k in warp
+// order, so every thread receives the same, order-fixed result
 template <int K>
 __device__ __forceinline__ void block_sum(double (&v)[K]) {
+    static_assert(K <= 8, "block_sum holds at most 8 values");
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
@@ -132,15 +151,34 @@ __device__ __forceinline__ void block_sum(double (&v)[K]) {
 #pragma unroll
         for (int k = 0; k < K; ++k) S.rd[w][k] = v[k];
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
+    if (threadIdx.x < K) {
         double t = 0.0;
 #pragma unroll
-        for (int i = 0; i < kWarps; ++i) t += S.rd[i][k];
-        v[k] = t;
+        for (int i = 0; i < kWarps; ++i) t += S.rd[i][threadIdx.x];
+        S.rsum[threadIdx.x] = t;
     }
     __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = S.rsum[k];
 }
+
+// Running sum of float terms without float64 arithmetic (FP64 is a narrow
+// pipe on this part): hi is the float sum, lo collects the exact rounding
+// error of each addition (Knuth's TwoSum), so hi + lo carries the sum to
+// about 2^-44 relative. Each term enters as the float it is computed as.
+struct FSum {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void fsum_add(FSum& a, float b) {
+    float s = __fadd_rn(a.hi, b);
+    float bp = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+    a.hi = s;
+    a.lo = __fadd_rn(a.lo, e);
+}
+
+__device__ __forceinline__ double fsum_value(const FSum& a) { return (double)a.hi + (double)a.lo; }
 
 __device__ __forceinline__ double block_min_d(double v) {
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -384,6 +422,7 @@ __device__ __forceinline__ int patch_vert(const Dev& D, const MeshDev& M, int pi
 template <int PASS>
 __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, int gb) {
     TetOut out{0.0, 0, 0.f, 0.0};
+    FSum acc{0.f, 0.f}, acc2{0.f, 0.f};
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     WarpScratch& W = S.w[warp];
@@ -454,15 +493,15 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
                 for (int e = 0; e < 9; ++e) dF2 += dF[e] * dF[e];
                 AInv ai = a_invariants(f, dF);
                 if (PASS == 0) {
-                    out.acc += (double)(hV * (mu * dF2 + (mu - lam * f.lnJ) * ai.trA2 + lam * ai.c1 * ai.c1));
+                    fsum_add(acc, hV * (mu * dF2 + (mu - lam * f.lnJ) * ai.trA2 + lam * ai.c1 * ai.c1));
                 } else if (PASS == 3) {
                     // direction dF = D_lambda Dm^-1: dP/dlam : dF = ln J tr(F^-1 dF),
                     // dP/dmu : dF = (F - F^-T) : dF = tr dF + G : dF - tr(F^-1 dF)
                     float GdF = 0.f;
     #pragma unroll
                     for (int e = 0; e < 9; ++e) GdF += G[e] * dF[e];
-                    out.acc += (double)(hV * f.lnJ * ai.c1);
-                    out.acc2 += (double)(hV * ((dF[0] + dF[4] + dF[8]) + GdF - ai.c1));
+                    fsum_add(acc, hV * f.lnJ * ai.c1);
+                    fsum_add(acc2, hV * ((dF[0] + dF[4] + dF[8]) + GdF - ai.c1));
                 } else if (PASS == 2) {
                     // dP = mu dF + (mu - lam ln J) F^-T dF^T F^-T + lam tr(F^-1 dF) F^-T
                     float C[9];
@@ -504,7 +543,7 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
                     float a2c = alpha * alpha * (ai.c2 - alpha * ai.c3);
                     float dl = log1p_minus(q) + a2c;          // ln det(I - aA) + a tr A
                     float dlnJ = log1pf(q);
-                    out.acc += (double)(hV * (0.5f * mu * alpha * alpha * dF2 + (lam * f.lnJ - mu) * dl +
+                    fsum_add(acc, hV * (0.5f * mu * alpha * alpha * dF2 + (lam * f.lnJ - mu) * dl +
                                               0.5f * lam * dlnJ * dlnJ));
                     // first Piola-Kirchhoff stress P = (mu Q + lam ln J cof) / J
                     float Pm[9];
@@ -598,7 +637,7 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
         if (kScatter) __syncthreads();          // colour class complete: its writes are visible
     }
     // every thread must see the same totals: the caller branches on them
-    double v[3] = {out.acc, (double)out.bad, out.acc2};
+    double v[3] = {fsum_value(acc), (double)out.bad, fsum_value(acc2)};
     block_sum<3>(v);
     out.acc = v[0];
     out.bad = v[1] > 0.0 ? 1 : 0;
@@ -1185,7 +1224,7 @@ struct Dots {
 // Completes g and the blocks at u + alpha p (inertia, Dirichlet), applies
 // the preconditioner and reduces the Dai-Kou dot products.
 __device__ __noinline__ Dots finalize(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, int gb, int go, bool dots) {
-    double v[4] = {0, 0, 0, 0};
+    FSum sv[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     float gi[1] = {0.f};
     int bad = 0;
     const float rho = P.rho;
@@ -1233,13 +1272,17 @@ __device__ __noinline__ Dots finalize(const Dev& D, const PadDev& P, const MeshD
 #pragma unroll
             for (int c = 0; c < 3; ++c) y[c] = g1[c] - D.g[go][c * D.Vt + si];
             sym_apply(Ki, y, Py);
-            v[0] += (double)(z[0] * y[0]) + (double)(z[1] * y[1]) + (double)(z[2] * y[2]);
-            v[1] += (double)(y[0] * Py[0]) + (double)(y[1] * Py[1]) + (double)(y[2] * Py[2]);
-            v[2] += (double)(pv[0] * g1[0]) + (double)(pv[1] * g1[1]) + (double)(pv[2] * g1[2]);
-            v[3] += (double)(y[0] * pv[0]) + (double)(y[1] * pv[1]) + (double)(y[2] * pv[2]);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                fsum_add(sv[0], __fmul_rn(z[c], y[c]));
+                fsum_add(sv[1], __fmul_rn(y[c], Py[c]));
+                fsum_add(sv[2], __fmul_rn(pv[c], g1[c]));
+                fsum_add(sv[3], __fmul_rn(y[c], pv[c]));
+            }
         }
     }
     if (bad) S.flag = 1;
+    double v[4] = {fsum_value(sv[0]), fsum_value(sv[1]), fsum_value(sv[2]), fsum_value(sv[3])};
     block_sum<4>(v);
     block_max_f<1>(gi);
     Dots d{v[0], v[1], v[2], v[3], gi[0], 0};
@@ -1259,7 +1302,7 @@ struct DirOut {
 // g^T p, p^T M p and max_i |p_i|
 __device__ __noinline__ DirOut direction(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, bool move, double beta,
                             int gb) {
-    double v[2] = {0, 0};
+    FSum sgp{0.f, 0.f}, smp{0.f, 0.f};
     float pn[1] = {0.f};
     const float rho = P.rho;
     const float bf = (float)beta;
@@ -1268,7 +1311,6 @@ __device__ __noinline__ DirOut direction(const Dev& D, const PadDev& P, const Me
         bool fx = D.fixed[M.xv_off + i] != 0;
         float m = rho * D.vlump[M.xv_off + i];
         float n2 = 0.f;
-        double gp = 0.0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             int sc = c * D.Vt + si;
@@ -1287,12 +1329,12 @@ __device__ __noinline__ DirOut direction(const Dev& D, const PadDev& P, const Me
             float np = fx ? 0.f : (-D.z[sc] + bf * pv);
             D.p[sc] = np;
             n2 += np * np;
-            gp += (double)(D.g[gb][sc] * np);
+            fsum_add(sgp, __fmul_rn(D.g[gb][sc], np));
         }
-        v[0] += gp;
-        v[1] += (double)(m * n2);
+        fsum_add(smp, __fmul_rn(m, n2));
         pn[0] = fmaxf(pn[0], sqrtf(n2));
     }
+    double v[2] = {fsum_value(sgp), fsum_value(smp)};
     block_sum<2>(v);
     block_max_f<1>(pn);
     return DirOut{v[0], v[1], pn[0]};
@@ -1382,9 +1424,10 @@ struct PadCounters {
 };
 
 __device__ void solve_pad(const Dev& D, int pad) {
-    const PadDev P = D.pads[pad];
-    const MeshDev M = D.meshes[P.mesh];
-    const EnvDev E = D.envs[P.env];
+    load_pad(D, pad);
+    const PadDev& P = S.P;
+    const MeshDev& M = S.M;
+    const EnvDev& E = S.E;
     const int tid = threadIdx.x;
     PadCounters ctr{0, 0, 0, 0, 0, 0, 0, 0};
     int status = ST_CONVERGED;
@@ -1706,9 +1749,10 @@ __global__ void __launch_bounds__(kThreads) debug_eval_kernel(const __grid_const
     if (threadIdx.x == 0) S.flag = 0;
     __syncthreads();
     const int pad = blockIdx.x;
-    const PadDev P = D.pads[pad];
-    const MeshDev M = D.meshes[P.mesh];
-    const EnvDev E = D.envs[P.env];
+    load_pad(D, pad);
+    const PadDev& P = S.P;
+    const MeshDev& M = S.M;
+    const EnvDev& E = S.E;
     world_indenter(D, P, E, D.pose_t + 6 * pad, D.Yt);
     world_indenter(D, P, E, D.pose_t + 6 * pad, D.Yn);
     __syncthreads();
@@ -1785,9 +1829,10 @@ __global__ void __launch_bounds__(kThreads) debug_eval_kernel(const __grid_const
 // candidate set of one pad for caller positions (see tac_broadphase)
 __global__ void __launch_bounds__(kThreads) broadphase_kernel(const __grid_constant__ Dev D, int pad, const float* x, const float* y,
                                                               double r, int* out, int cap, int* count) {
-    const PadDev P = D.pads[pad];
-    const MeshDev M = D.meshes[P.mesh];
-    const EnvDev E = D.envs[P.env];
+    load_pad(D, pad);
+    const PadDev& P = S.P;
+    const MeshDev& M = S.M;
+    const EnvDev& E = S.E;
     SrcArrays src{x, y};
     int n = bp_build(src, D, M, E, D.ilist + P.il_off, r, D.pairs + P.pair_off, P.pair_cap);
     for (int k = threadIdx.x; k < min(n, min(cap, P.pair_cap)); k += kThreads) {
@@ -2133,9 +2178,10 @@ __global__ void __launch_bounds__(kThreads, 2) adjoint_kernel(const __grid_const
                                                               double* out, int* status, int* iters, int max_iter,
                                                               float tol) {
     const int pad = blockIdx.x;
-    const PadDev P = D.pads[pad];
-    const MeshDev M = D.meshes[P.mesh];
-    const EnvDev E = D.envs[P.env];
+    load_pad(D, pad);
+    const PadDev& P = S.P;
+    const MeshDev& M = S.M;
+    const EnvDev& E = S.E;
     if (threadIdx.x == 0) S.flag = 0;
     __syncthreads();
     // candidates at the equilibrium with the indenter at the frame's end
