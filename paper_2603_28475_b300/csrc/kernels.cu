@@ -29,6 +29,11 @@ constexpr int kWarps = kThreads / 32;
 // a float32 gradient is resolved only down to a few hundred ulps of the
 // largest per-corner force that enters it: 256 * 2^-24
 constexpr float kFloat32Floor = 256.0f / 16777216.0f;
+// A pair whose float32 distance exceeds kNearBand * dhat is outside the
+// barrier's support in float64 as well: at the workloads' coordinate
+// magnitudes (a few cm) the float32 distance is off by ~1e-8 m at most,
+// far below the band's 0.05 dhat. Such pairs skip the float64 feature.
+constexpr double kNearBand = 1.05;
 
 // ---------------------------------------------------------------------------
 // shared memory of one CTA
@@ -942,16 +947,19 @@ __device__ __noinline__ double pair_dmin(const Dev& D, const PadDev& P, const Me
         int gsl[4], isl[4];
         int4 q = pr[k];
         pair_slots(D, M, E, q, gsl, isl);
-        dm = fmin(dm, pair_distance(D, P, M, q.x, gsl, isl, 0.0f, s, 2.0 * P.dhat));
+        dm = fmin(dm, pair_distance(D, P, M, q.x, gsl, isl, 0.0f, s, kNearBand * P.dhat));
     }
     return block_min_d(dm);
 }
 
-// p^T H p of the barrier and friction terms and the per-pair step bound
+// p^T H p of the barrier and friction terms and the per-pair step bound at
+// the current point; also stores each pair's barrier value b(d) there, which
+// the line-search trials of this point subtract from (see pair_trial)
 __device__ __noinline__ void pair_php(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np, int nl, double s,
                          double& php, double& accd) {
     double acc = 0.0, amin = 1e300;
     const int4* pr = D.pairs + P.pair_off;
+    double* bcur = D.bpair + P.pair_off;
     const double dh = P.dhat, kap = P.kappa;
     for (int k = threadIdx.x; k < np; k += kThreads) {
         int gsl[4], isl[4];
@@ -973,8 +981,8 @@ __device__ __noinline__ void pair_php(const Dev& D, const PadDev& P, const MeshD
         V3<float> Xf[4];
         load_slots<float>(D, P, M, gsl, isl, 0.0f, s, Xf);
         float df = pair_feature<float>(q.x, Xf).d;
-        double d;
-        if ((double)df > 2.0 * dh) {
+        double d, bv = 0.0;
+        if ((double)df > kNearBand * dh) {
             d = (double)df * (1.0 - 1e-5);
         } else {
             V3<double> X[4];
@@ -985,8 +993,10 @@ __device__ __noinline__ void pair_php(const Dev& D, const PadDev& P, const MeshD
                 double d1, d2;
                 feat_dir_derivs(f, X, dl, d1, d2);
                 acc += kap * (barrier_b2(d, dh) * d1 * d1 + barrier_b1(d, dh) * d2);
+                bv = barrier_b(d, dh);
             }
         }
+        bcur[k] = bv;
         if (pk > 0.f) amin = fmin(amin, (double)kEta * d / (double)pk);
     }
     // friction (lagged pairs)
@@ -1025,14 +1035,19 @@ __device__ __noinline__ void pair_php(const Dev& D, const PadDev& P, const MeshD
     accd = block_min_d(amin);
 }
 
-// trial pass over pairs at u + alpha p: slot contributions and remainders
+// trial pass over pairs at u + alpha p: slot contributions and remainders.
+// With alpha > 0 the remainder of pair k subtracts from its barrier value at
+// the current point, stored by pair_php of this point; alpha = 0 evaluates
+// the current point itself (remainder 0) and needs no stored value.
 __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np, int nl, double s,
                            float alpha, double& rem, int& bad) {
     double acc = 0.0;
     int badl = 0;
     const int4* pr = D.pairs + P.pair_off;
+    const double* bcur = D.bpair + P.pair_off;
     float* sb = D.slotbuf + (size_t)9 * 6 * P.pair_off;
     const double dh = P.dhat, kap = P.kappa;
+    const bool trial = alpha != 0.0f;
     for (int k = threadIdx.x; k < np; k += kThreads) {
         int gsl[4], isl[4];
         int4 q = pr[k];
@@ -1040,22 +1055,23 @@ __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const Mes
         V3<float> Xf[4];
         load_slots<float>(D, P, M, gsl, isl, alpha, s, Xf);
         float d1f = pair_feature<float>(q.x, Xf).d;
-        load_slots<float>(D, P, M, gsl, isl, 0.0f, s, Xf);
-        float d0f = pair_feature<float>(q.x, Xf).d;
+        const double b0 = trial ? bcur[k] : 0.0;
         float out[3][9];
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
             for (int c = 0; c < 9; ++c) out[a][c] = 0.f;
-        if ((double)d1f <= 2.0 * dh || (double)d0f <= 2.0 * dh) {
-            V3<double> X1[4], X0[4];
+        if ((double)d1f > kNearBand * dh) {
+            acc += kap * b0;                    // b = 0 at the trial point
+        } else {
+            V3<double> X1[4];
             load_slots<double>(D, P, M, gsl, isl, alpha, s, X1);
-            load_slots<double>(D, P, M, gsl, isl, 0.0f, s, X0);
             Feature<double> f1 = pair_feature<double>(q.x, X1);
-            Feature<double> f0 = pair_feature<double>(q.x, X0);
             if (!(f1.d > 0.0)) {
                 badl = 1;
-            } else if (f1.d < dh || f0.d < dh) {
+            } else if (f1.d >= dh) {
+                acc += kap * b0;
+            } else {
                 V3<double> r = feat_r(f1, X1);
                 double inv = 1.0 / f1.d;
                 V3<double> rh = inv * r;
@@ -1078,7 +1094,7 @@ __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const Mes
                         out[sl][7] = (float)(kw * rh.x * rh.z);
                         out[sl][8] = (float)(kw * rh.y * rh.z);
                     }
-                acc += kap * (barrier_b(f0.d, dh) - barrier_b(f1.d, dh)) + (double)alpha * b1 * gdp;
+                if (trial) acc += kap * (b0 - barrier_b(f1.d, dh)) + (double)alpha * b1 * gdp;
             }
         }
 #pragma unroll

@@ -96,6 +96,7 @@ struct Dev {
     int4* pairs;
     LagRec* lag;
     float* slotbuf;           // [6 * pair_cap][9] per pad region (pairs then lag, 3 slots each)
+    double* bpair;            // [pair_cap] per pad: barrier value b(d) of each pair at the current point
     int* ent;                 // [6 * pair_cap]
     int* cvl;                 // [6 * pair_cap + 1] contact vertex list / offsets
     int* cvo;                 // [6 * pair_cap + 1]
