@@ -52,36 +52,41 @@ namespace {
 
 // ---- small helper kernels ---------------------------------------------------
 
-__global__ void aos_to_state(const float* x, const float* X, int XVt, const int* xv_of_state, float* uh, float* ul,
-                             int Vt, bool subtract_rest) {
+// Caller arrays are [Vt][3] in input vertex order (pad by pad); the state is
+// SoA in the internal vertex order. u2i maps a caller index to its state index.
+__global__ void aos_to_state(const float* x, const float* X, int XVt, const int* xv_of_state, const int* u2i,
+                             float* uh, float* ul, int Vt, bool subtract_rest) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= Vt) return;
-    int xi = xv_of_state[i];
+    int j = u2i[i];
+    int xi = xv_of_state[j];
     for (int c = 0; c < 3; ++c) {
         float v = x[3 * i + c];
         if (subtract_rest) v -= X[c * XVt + xi];
-        uh[c * Vt + i] = v;
-        if (ul) ul[c * Vt + i] = 0.f;
+        uh[c * Vt + j] = v;
+        if (ul) ul[c * Vt + j] = 0.f;
     }
 }
 
 __global__ void state_to_aos(const float* uh, const float* ul, const float* X, int XVt, const int* xv_of_state,
-                             float* out, int Vt) {
+                             const int* u2i, float* out, int Vt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= Vt) return;
-    int xi = xv_of_state[i];
+    int j = u2i[i];
+    int xi = xv_of_state[j];
     for (int c = 0; c < 3; ++c) {
-        float v = uh[c * Vt + i];
-        if (ul) v += ul[c * Vt + i];
+        float v = uh[c * Vt + j];
+        if (ul) v += ul[c * Vt + j];
         if (X) v += X[c * XVt + xi];
         out[3 * i + c] = v;
     }
 }
 
-__global__ void copy_aos_to_soa(const float* a, float* s, int Vt) {
+__global__ void copy_aos_to_soa(const float* a, const int* u2i, float* s, int Vt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= Vt) return;
-    for (int c = 0; c < 3; ++c) s[c * Vt + i] = a[3 * i + c];
+    int j = u2i[i];
+    for (int c = 0; c < 3; ++c) s[c * Vt + j] = a[3 * i + c];
 }
 
 // target pose = current pose advanced by h * twist (rotation composed with
@@ -169,6 +174,7 @@ struct tac_batch {
     PadDev* d_pads = nullptr;
     EnvDev* d_envs = nullptr;
     int* d_xv_of_state = nullptr;
+    int* d_u2i = nullptr;                   // caller vertex index -> state index
     float* d_hstep = nullptr;
     float* d_pose_t = nullptr;
     float* d_pose_n = nullptr;
@@ -303,6 +309,9 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     int Vt = 0, yw = 0, il = 0, mko = 0;
     b->hpad.resize(n_pads);
     std::vector<int> xv_of_state;
+    int vt_all = 0;
+    for (int p = 0; p < n_pads; ++p) vt_all += b->hmesh[b->pad_mesh[p]].n_v;
+    std::vector<int> u2i(vt_all);
     for (int p = 0; p < n_pads; ++p) {
         PadDev& P = b->hpad[p];
         const MeshDev& md = b->hmesh[b->pad_mesh[p]];
@@ -316,6 +325,8 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
         P.il_off = il;
         P.mk_out = mko;
         for (int i = 0; i < md.n_v; ++i) xv_of_state.push_back(md.xv_off + i);
+        const PadMesh& pm = b->meshes[P.mesh];
+        for (int i = 0; i < md.n_v; ++i) u2i[Vt + pm.vuser[i]] = Vt + i;
         Vt += md.n_v;
         yw += ed.n_v;
         il += ed.n_t + ed.n_v + ed.n_e;
@@ -392,6 +403,8 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     b->d_pads = dalloc<PadDev>(K, n_pads, rc);
     b->d_envs = dalloc<EnvDev>(K, b->henv.size(), rc);
     b->d_xv_of_state = dalloc<int>(K, Vt, rc);
+    b->d_u2i = dalloc<int>(K, Vt, rc);
+    int* vuser = dalloc<int>(K, XVt, rc);
     b->d_hstep = dalloc<float>(K, n_pads, rc);
     if (rc != TAC_OK) {
         tac_destroy_batch(b);
@@ -400,6 +413,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     // host staging of static data
     std::vector<float> hX(3 * (size_t)XVt), hvl(XVt), hB(9 * (size_t)Tt), hmkw, hY;
     std::vector<uint8_t> hfx(XVt);
+    std::vector<int> hvu(XVt);
     std::vector<uint32_t> hlc(Tt);
     std::vector<uint32_t> hsl(Tt);
     std::vector<int> hcol;
@@ -412,6 +426,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
             for (int c = 0; c < 3; ++c) hX[(size_t)c * XVt + md.xv_off + i] = M.X[3 * i + c];
             hvl[md.xv_off + i] = M.vlump[i];
             hfx[md.xv_off + i] = M.fixed[i];
+            hvu[md.xv_off + i] = M.vuser[i];
         }
         const int ns = M.n_slots();
         for (int t = 0; t < ns; ++t) {
@@ -460,6 +475,8 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     r2 |= up(b->d_pads, b->hpad.data(), b->hpad.size() * sizeof(PadDev));
     r2 |= up(b->d_envs, b->henv.data(), b->henv.size() * sizeof(EnvDev));
     r2 |= up(b->d_xv_of_state, xv_of_state.data(), xv_of_state.size() * 4);
+    r2 |= up(b->d_u2i, u2i.data(), u2i.size() * 4);
+    r2 |= up(vuser, hvu.data(), hvu.size() * 4);
     r2 |= up(b->d_hstep, b->hstep.data(), b->hstep.size() * 4);
     r2 |= up(order_d, order.data(), order.size() * 4);
     if (r2 != TAC_OK) {
@@ -482,7 +499,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     D.envs = b->d_envs;
     D.pads = b->d_pads;
     D.order = order_d;
-    D.X = X; D.vlump = vlump; D.fixed = fixed; D.B = B; D.lconn = lconn; D.slot = slot; D.colour = colour;
+    D.X = X; D.vlump = vlump; D.fixed = fixed; D.vuser = vuser; D.B = B; D.lconn = lconn; D.slot = slot; D.colour = colour;
     D.pvert = pvert; D.pcsr = pcsr; D.sv = sv; D.st = stt; D.se = se;
     D.mk_ids = mk_ids; D.mk_w = mk_w; D.Y = Y; D.it = it; D.ie = ie; D.Yt = Yt; D.Yn = Yn;
     D.pose_t = b->d_pose_t; D.pose_n = b->d_pose_n;
@@ -568,8 +585,8 @@ int tac_get_state(tac_handle h, float* x_dev, float* v_dev, void* stream) {
     if (!h) return fail(TAC_ERR_INVALID_ARG, "null handle");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int nb = (h->Vt + 255) / 256;
-    if (x_dev) state_to_aos<<<nb, 256, 0, st>>>(h->dev.uh, h->dev.ul, h->dev.X, h->XVt, h->d_xv_of_state, x_dev, h->Vt);
-    if (v_dev) state_to_aos<<<nb, 256, 0, st>>>(h->dev.vel, nullptr, nullptr, h->XVt, h->d_xv_of_state, v_dev, h->Vt);
+    if (x_dev) state_to_aos<<<nb, 256, 0, st>>>(h->dev.uh, h->dev.ul, h->dev.X, h->XVt, h->d_xv_of_state, h->d_u2i, x_dev, h->Vt);
+    if (v_dev) state_to_aos<<<nb, 256, 0, st>>>(h->dev.vel, nullptr, nullptr, h->XVt, h->d_xv_of_state, h->d_u2i, v_dev, h->Vt);
     CUDA_TRY(cudaGetLastError());
     return TAC_OK;
 }
@@ -578,8 +595,8 @@ int tac_set_state(tac_handle h, const float* x_dev, const float* v_dev, void* st
     if (!h || !x_dev || !v_dev) return fail(TAC_ERR_INVALID_ARG, "null argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int nb = (h->Vt + 255) / 256;
-    aos_to_state<<<nb, 256, 0, st>>>(x_dev, h->dev.X, h->XVt, h->d_xv_of_state, h->dev.uh, h->dev.ul, h->Vt, true);
-    aos_to_state<<<nb, 256, 0, st>>>(v_dev, h->dev.X, h->XVt, h->d_xv_of_state, h->dev.vel, nullptr, h->Vt, false);
+    aos_to_state<<<nb, 256, 0, st>>>(x_dev, h->dev.X, h->XVt, h->d_xv_of_state, h->d_u2i, h->dev.uh, h->dev.ul, h->Vt, true);
+    aos_to_state<<<nb, 256, 0, st>>>(v_dev, h->dev.X, h->XVt, h->d_xv_of_state, h->d_u2i, h->dev.vel, nullptr, h->Vt, false);
     CUDA_TRY(cudaGetLastError());
     return TAC_OK;
 }
@@ -622,8 +639,8 @@ int tac_debug_eval(tac_handle h, const float* u_dev, const float* p_dev, float a
     if (!h || !u_dev || !p_dev) return fail(TAC_ERR_INVALID_ARG, "null argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int nb = (h->Vt + 255) / 256;
-    aos_to_state<<<nb, 256, 0, st>>>(u_dev, h->dev.X, h->XVt, h->d_xv_of_state, h->dev.uh, h->dev.ul, h->Vt, false);
-    copy_aos_to_soa<<<nb, 256, 0, st>>>(p_dev, h->dev.p, h->Vt);
+    aos_to_state<<<nb, 256, 0, st>>>(u_dev, h->dev.X, h->XVt, h->d_xv_of_state, h->d_u2i, h->dev.uh, h->dev.ul, h->Vt, false);
+    copy_aos_to_soa<<<nb, 256, 0, st>>>(p_dev, h->d_u2i, h->dev.p, h->Vt);
     CUDA_TRY(cudaMemsetAsync(h->dev.vel, 0, 3 * (size_t)h->Vt * 4, st));
     double r = 2.0 * (double)h->hpad[0].dhat;
     debug_eval_kernel<<<h->n_pads, kThreads, shared_bytes(), st>>>(h->dev, alpha, r, grad_dev, blk_dev, scal_dev);

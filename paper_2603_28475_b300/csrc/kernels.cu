@@ -691,10 +691,14 @@ struct SrcState {
     __device__ float gel(int gv, int c) const { return gel_pos32(*D, *P, *M, gv, c, 0.0f); }
     __device__ float ind(int j, int c) const { return ind_pos32(*D, *P, j, c, s); }
 };
+// caller positions: gel [n_v][3] in input vertex order (vu: internal ->
+// input id, or nullptr when the gel ids are the caller's own), indenter
+// [n_ind][3]
 struct SrcArrays {
     const float* x;
     const float* y;
-    __device__ float gel(int gv, int c) const { return x[3 * gv + c]; }
+    const int* vu;
+    __device__ float gel(int gv, int c) const { return x[3 * (vu ? vu[gv] : gv) + c]; }
     __device__ float ind(int j, int c) const { return y[3 * j + c]; }
 };
 
@@ -1813,17 +1817,18 @@ __global__ void __launch_bounds__(kThreads) debug_eval_kernel(const __grid_const
     float gi[1] = {0.f};
     for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
         int si = P.v_off + i;
+        int ui = P.v_off + D.vuser[M.xv_off + i];     // output row: input vertex order
         bool fx = D.fixed[M.xv_off + i] != 0;
         float m = P.rho * D.vlump[M.xv_off + i];
         for (int c = 0; c < 3; ++c) {
             int sc = c * D.Vt + si;
             float gv = fx ? 0.f : D.g[0][sc] + m * alpha * D.p[sc];
-            if (grad_out) grad_out[3 * si + c] = gv;
+            if (grad_out) grad_out[3 * ui + c] = gv;
             gp[0] += (double)(gv * D.p[sc]);
             gi[0] = fmaxf(gi[0], fabsf(gv));
         }
         if (blk_out)
-            for (int c = 0; c < 6; ++c) blk_out[6 * si + c] = D.blk[0][c * D.Vt + si] + (c < 3 ? m : 0.f);
+            for (int c = 0; c < 6; ++c) blk_out[6 * ui + c] = D.blk[0][c * D.Vt + si] + (c < 3 ? m : 0.f);
     }
     block_sum<1>(gp);
     block_max_f<1>(gi);
@@ -1849,12 +1854,12 @@ __global__ void __launch_bounds__(kThreads) broadphase_kernel(const __grid_const
     const PadDev& P = S.P;
     const MeshDev& M = S.M;
     const EnvDev& E = S.E;
-    SrcArrays src{x, y};
+    SrcArrays src{x, y, D.vuser + M.xv_off};
     int n = bp_build(src, D, M, E, D.ilist + P.il_off, r, D.pairs + P.pair_off, P.pair_cap);
     for (int k = threadIdx.x; k < min(n, min(cap, P.pair_cap)); k += kThreads) {
         int4 q = D.pairs[P.pair_off + k];
         out[3 * k] = q.x;
-        out[3 * k + 1] = q.y;
+        out[3 * k + 1] = q.x == 0 ? D.vuser[M.xv_off + q.y] : q.y;   // gel vertex: input id
         out[3 * k + 2] = q.z;
     }
     if (threadIdx.x == 0) *count = n;
@@ -2289,7 +2294,7 @@ __global__ void __launch_bounds__(kThreads) broadphase_static_kernel2(const __gr
                                                                       const float* x, const float* y, double r,
                                                                       int4* scratch, int n_list_int4, int* out,
                                                                       int cap, int* count) {
-    SrcArrays src{x, y};
+    SrcArrays src{x, y, nullptr};
     int* ilist = reinterpret_cast<int*>(scratch);
     int4* staged = scratch + n_list_int4;
     int n = bp_build(src, D, M, E, ilist, r, staged, cap);

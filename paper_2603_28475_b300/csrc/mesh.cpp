@@ -186,9 +186,7 @@ bool build_pad_mesh(int nv, int nt, int nf, int nm, const float* rest, const int
         }
     }
 
-    // patches: tets in Morton order of their centroids, cut greedily so that a
-    // patch has at most kPatchTets tets and kPatchVerts distinct vertices, then
-    // coloured so that patches of one colour share no vertex
+    // Morton codes on the rest bounding box (10 bits per axis)
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     for (int i = 0; i < nv; ++i)
         for (int r = 0; r < 3; ++r) {
@@ -196,16 +194,25 @@ bool build_pad_mesh(int nv, int nt, int nf, int nm, const float* rest, const int
             hi[r] = std::max(hi[r], static_cast<double>(rest[3 * i + r]));
         }
     double span = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+    auto morton = [&](const double q[3]) {
+        uint32_t b[3];
+        for (int r = 0; r < 3; ++r) {
+            double u = span > 0 ? (q[r] - lo[r]) / span : 0.0;
+            b[r] = static_cast<uint32_t>(std::min(1023.0, std::max(0.0, u * 1023.0)));
+        }
+        return (spread10(b[0]) << 2) | (spread10(b[1]) << 1) | spread10(b[2]);
+    };
+
+    // patches: tets in Morton order of their centroids, cut greedily so that a
+    // patch has at most kPatchTets tets and kPatchVerts distinct vertices, then
+    // coloured so that patches of one colour share no vertex
     std::vector<uint32_t> code(nt);
     for (int t = 0; t < nt; ++t) {
         const int* c = tets + 4 * static_cast<size_t>(t);
-        uint32_t q[3];
-        for (int r = 0; r < 3; ++r) {
-            double s = 0.25 * (rest[3 * c[0] + r] + rest[3 * c[1] + r] + rest[3 * c[2] + r] + rest[3 * c[3] + r]);
-            double u = span > 0 ? (s - lo[r]) / span : 0.0;
-            q[r] = static_cast<uint32_t>(std::min(1023.0, std::max(0.0, u * 1023.0)));
-        }
-        code[t] = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+        double q[3];
+        for (int r = 0; r < 3; ++r)
+            q[r] = 0.25 * (rest[3 * c[0] + r] + rest[3 * c[1] + r] + rest[3 * c[2] + r] + rest[3 * c[3] + r]);
+        code[t] = morton(q);
     }
     M.tet_order.resize(nt);
     std::iota(M.tet_order.begin(), M.tet_order.end(), 0);
@@ -245,6 +252,48 @@ bool build_pad_mesh(int nv, int nt, int nf, int nm, const float* rest, const int
         }
     }
     const int np0 = static_cast<int>(ptets.size());
+
+    // internal vertex order: first appearance along the patches in creation
+    // (spatial) order, so that the vertices of a patch lie close together in
+    // every per-vertex array. Everything stored from here on uses internal
+    // ids; the surface lists and the marker triangles keep the order they
+    // have in input ids.
+    std::vector<int> vint(nv, -1);
+    {
+        int next = 0;
+        for (int q = 0; q < np0; ++q)
+            for (int v : pverts[q])
+                if (vint[v] < 0) vint[v] = next++;
+        for (int v = 0; v < nv; ++v)
+            if (vint[v] < 0) {
+                std::snprintf(msgbuf, sizeof msgbuf, "vertex %d belongs to no tet", v);
+                err = msgbuf;
+                return false;
+            }
+    }
+    M.vuser.assign(nv, 0);
+    for (int v = 0; v < nv; ++v) M.vuser[vint[v]] = v;
+    {
+        std::vector<float> X2(3 * static_cast<size_t>(nv)), vl2(nv);
+        std::vector<uint8_t> fx2(nv);
+        for (int j = 0; j < nv; ++j) {
+            int u = M.vuser[j];
+            for (int r = 0; r < 3; ++r) X2[3 * j + r] = M.X[3 * u + r];
+            vl2[j] = M.vlump[u];
+            fx2[j] = M.fixed[u];
+        }
+        M.X.swap(X2);
+        M.vlump.swap(vl2);
+        M.fixed.swap(fx2);
+    }
+    for (int& v : M.sv) v = vint[v];
+    for (int& v : M.st) v = vint[v];
+    for (int& v : M.se) v = vint[v];
+    for (int& v : M.mk_ids) v = vint[v];
+    for (auto& pv : pverts)
+        for (int& v : pv) v = vint[v];
+    std::vector<int> itets(4 * static_cast<size_t>(nt));
+    for (size_t k = 0; k < itets.size(); ++k) itets[k] = vint[tets[k]];
     // 2. colour the patches: two patches sharing a vertex get different colours
     std::vector<std::vector<int>> vpatch(nv);
     for (int q = 0; q < np0; ++q)
@@ -294,7 +343,7 @@ bool build_pad_mesh(int nv, int nt, int nf, int nm, const float* rest, const int
         // corner slots: for each local vertex, its (tet, corner) pairs in (tet, corner) order
         std::vector<int> count(kPatchCsr, 0);
         for (int t : tl) {
-            const int* c = tets + 4 * static_cast<size_t>(t);
+            const int* c = itets.data() + 4 * static_cast<size_t>(t);
             for (int j = 0; j < 4; ++j) count[local[c[j]] + 1]++;
         }
         for (int l = 0; l < kPatchVerts; ++l) count[l + 1] += count[l];   // unused entries: empty runs
@@ -304,7 +353,7 @@ bool build_pad_mesh(int nv, int nt, int nf, int nm, const float* rest, const int
         const int tb = pi * kPatchTets;
         for (int k = 0; k < ntl; ++k) {
             const int t = tl[k];
-            const int* c = tets + 4 * static_cast<size_t>(t);
+            const int* c = itets.data() + 4 * static_cast<size_t>(t);
             uint32_t lc = 0, sl = 0;
             for (int j = 0; j < 4; ++j) {
                 int l = local[c[j]];
@@ -342,7 +391,7 @@ bool build_pad_mesh(int nv, int nt, int nf, int nm, const float* rest, const int
     }
     for (int v = 0; v < nv; ++v)
         if (first_patch[v] < 0) {
-            std::snprintf(msgbuf, sizeof msgbuf, "vertex %d belongs to no tet", v);
+            std::snprintf(msgbuf, sizeof msgbuf, "vertex %d belongs to no tet", M.vuser[v]);
             err = msgbuf;
             return false;
         }

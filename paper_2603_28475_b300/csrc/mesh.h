@@ -16,6 +16,9 @@ namespace tac {
 
 struct PadMesh {
     int n_v = 0, n_t = 0, n_mk = 0;
+    // Vertices are stored in an internal order (Morton order of the rest
+    // positions); every vertex id below is internal unless noted.
+    std::vector<int> vuser;           // [n_v] internal id -> input vertex id
     std::vector<float> X;             // [n_v*3] rest positions
     std::vector<float> vlump;         // [n_v] lumped rest volume (sum of V/4); mass = rho * vlump
     std::vector<uint8_t> fixed;       // [n_v] 1 = Dirichlet
@@ -29,9 +32,9 @@ struct PadMesh {
     std::vector<int> tet_order;       // slot -> input tet id (-1 unused)
     std::vector<int> colour_off;      // patches of colour c: [colour_off[c], colour_off[c+1])
     // canonical surface
-    std::vector<int> sv;              // surface vertex ids, sorted
-    std::vector<int> st;              // [n_st*3] surface triangles (sorted ids), sorted
-    std::vector<int> se;              // [n_se*2] surface edges (lo, hi), sorted
+    std::vector<int> sv;              // surface vertex ids, in increasing input id
+    std::vector<int> st;              // [n_st*3] surface triangles, canonical order of the input ids
+    std::vector<int> se;              // [n_se*2] surface edges, canonical order of the input ids
     double lbar = 0.0;                // mean rest surface edge length
     // markers
     std::vector<int> mk_ids;          // [n_mk*3]

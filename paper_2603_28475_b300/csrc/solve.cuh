@@ -68,6 +68,7 @@ struct Dev {
     int XVt;
     const float* vlump;       // [XVt]
     const uint8_t* fixed;     // [XVt]
+    const int* vuser;         // [XVt] internal vertex -> input vertex id (mesh-local)
     const float* B;           // [9][Tt], Tt = total tet slots
     int Tt;
     const uint32_t* lconn;    // [Tt]
