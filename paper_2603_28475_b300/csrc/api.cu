@@ -353,6 +353,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     D.Tt = Tt;
     float* X = dalloc<float>(K, 3 * (size_t)XVt, rc);
     float* vlump = dalloc<float>(K, XVt, rc);
+    float* wdiag = dalloc<float>(K, XVt, rc);
     uint8_t* fixed = dalloc<uint8_t>(K, XVt, rc);
     float* B = dalloc<float>(K, 9 * (size_t)Tt, rc);
     uint32_t* lconn = dalloc<uint32_t>(K, Tt, rc);
@@ -411,6 +412,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
         return fail(TAC_ERR_OOM, "device allocation failed");
     }
     // host staging of static data
+    std::vector<float> hwd(XVt);
     std::vector<float> hX(3 * (size_t)XVt), hvl(XVt), hB(9 * (size_t)Tt), hmkw, hY;
     std::vector<uint8_t> hfx(XVt);
     std::vector<int> hvu(XVt);
@@ -425,6 +427,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
         for (int i = 0; i < M.n_v; ++i) {
             for (int c = 0; c < 3; ++c) hX[(size_t)c * XVt + md.xv_off + i] = M.X[3 * i + c];
             hvl[md.xv_off + i] = M.vlump[i];
+            hwd[md.xv_off + i] = M.wdiag[i];
             hfx[md.xv_off + i] = M.fixed[i];
             hvu[md.xv_off + i] = M.vuser[i];
         }
@@ -476,6 +479,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     r2 |= up(b->d_envs, b->henv.data(), b->henv.size() * sizeof(EnvDev));
     r2 |= up(b->d_xv_of_state, xv_of_state.data(), xv_of_state.size() * 4);
     r2 |= up(b->d_u2i, u2i.data(), u2i.size() * 4);
+    r2 |= up(wdiag, hwd.data(), hwd.size() * 4);
     r2 |= up(vuser, hvu.data(), hvu.size() * 4);
     r2 |= up(b->d_hstep, b->hstep.data(), b->hstep.size() * 4);
     r2 |= up(order_d, order.data(), order.size() * 4);
@@ -499,7 +503,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     D.envs = b->d_envs;
     D.pads = b->d_pads;
     D.order = order_d;
-    D.X = X; D.vlump = vlump; D.fixed = fixed; D.vuser = vuser; D.B = B; D.lconn = lconn; D.slot = slot; D.colour = colour;
+    D.X = X; D.vlump = vlump; D.wdiag = wdiag; D.fixed = fixed; D.vuser = vuser; D.B = B; D.lconn = lconn; D.slot = slot; D.colour = colour;
     D.pvert = pvert; D.pcsr = pcsr; D.sv = sv; D.st = stt; D.se = se;
     D.mk_ids = mk_ids; D.mk_w = mk_w; D.Y = Y; D.it = it; D.ie = ie; D.Yt = Yt; D.Yn = Yn;
     D.pose_t = b->d_pose_t; D.pose_n = b->d_pose_n;

@@ -53,7 +53,9 @@ struct PatchStage {
 // per-warp scratch of the tet passes
 struct WarpScratch {
     PatchStage st[2];           // double buffer: the warp's next patch loads while this one computes
-    float stg[9][kStage];       // corner contributions of the current patch
+    float stg[6][kStage];       // corner values of the current patch: force (3) and, in the gradient
+                                // pass, s = sqrt(hV coef) c whose outer product is the block's
+                                // non-static part
 };
 
 struct Shared {
@@ -406,6 +408,9 @@ __device__ __forceinline__ void issue_patch(const Dev& D, const PadDev& P, const
 #pragma unroll
                 for (int c = 0; c < 6; ++c) cp_async4(&st.og[3 + c][lane], D.blk[gb] + (size_t)c * D.Vt + si);
             }
+        } else if (PASS == 1) {
+            // first patch of the vertex: the blocks' static diagonal enters here
+            cp_async4(&st.og[3][lane], D.wdiag + M.xv_off + (gvf & kVertMask));
         }
     }
     cp_async_commit();
@@ -562,6 +567,9 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
                         for (int r = 0; r < 3; ++r)
                             Hc[k][r] = hV * (Pm[3 * r] * Bm[3 * k] + Pm[3 * r + 1] * Bm[3 * k + 1] + Pm[3 * r + 2] * Bm[3 * k + 2]);
                     float coef = fmaxf(mu + lam * (1.0f - f.lnJ), 0.0f) * f.invJ * f.invJ;
+                    // corner block hV (mu |b|^2 I + coef c c^T): the first term is static
+                    // (h^2 mu wdiag per vertex), the second s s^T with s = sqrt(hV coef) c
+                    const float sq = sqrtf(hV * coef);
                     uint32_t sl = st.sl[lane];
     #pragma unroll
                     for (int k = 0; k < 4; ++k) {
@@ -582,18 +590,14 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
                         float cc[3];
     #pragma unroll
                         for (int r = 0; r < 3; ++r) cc[r] = f.cof[3 * r] * bv[0] + f.cof[3 * r + 1] * bv[1] + f.cof[3 * r + 2] * bv[2];
-                        float bb = mu * (bv[0] * bv[0] + bv[1] * bv[1] + bv[2] * bv[2]);
                         int slot = (int)((sl >> (8 * k)) & 0xff);
                         out.fmax = fmaxf(out.fmax, fmaxf(fabsf(fo[0]), fmaxf(fabsf(fo[1]), fabsf(fo[2]))));
                         W.stg[0][slot] = fo[0];
                         W.stg[1][slot] = fo[1];
                         W.stg[2][slot] = fo[2];
-                        W.stg[3][slot] = hV * (bb + coef * cc[0] * cc[0]);
-                        W.stg[4][slot] = hV * (bb + coef * cc[1] * cc[1]);
-                        W.stg[5][slot] = hV * (bb + coef * cc[2] * cc[2]);
-                        W.stg[6][slot] = hV * (coef * cc[0] * cc[1]);
-                        W.stg[7][slot] = hV * (coef * cc[0] * cc[2]);
-                        W.stg[8][slot] = hV * (coef * cc[1] * cc[2]);
+                        W.stg[3][slot] = sq * cc[0];
+                        W.stg[4][slot] = sq * cc[1];
+                        W.stg[5][slot] = sq * cc[2];
                     }
                 }
             }
@@ -621,16 +625,28 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
                     float acc[9];
 #pragma unroll
                     for (int c = 0; c < 9; ++c) acc[c] = 0.f;
-                    for (int q = s0; q < s1; ++q)
-#pragma unroll
-                        for (int c = 0; c < 9; ++c) acc[c] += W.stg[c][q];
+                    for (int q = s0; q < s1; ++q) {
+                        const float f0 = W.stg[0][q], f1 = W.stg[1][q], f2 = W.stg[2][q];
+                        const float q0 = W.stg[3][q], q1 = W.stg[4][q], q2 = W.stg[5][q];
+                        acc[0] += f0; acc[1] += f1; acc[2] += f2;
+                        acc[3] += q0 * q0; acc[4] += q1 * q1; acc[5] += q2 * q2;
+                        acc[6] += q0 * q1; acc[7] += q0 * q2; acc[8] += q1 * q2;
+                    }
                     int si = P.v_off + gv;
                     float* g = D.g[gb];
                     float* k = D.blk[gb];
+                    if (first) {
+                        const float dg = h2 * mu * st.og[3][lane];
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) g[c * D.Vt + si] = first ? acc[c] : st.og[c][lane] + acc[c];
+                        for (int c = 0; c < 3; ++c) g[c * D.Vt + si] = acc[c];
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) k[c * D.Vt + si] = first ? acc[3 + c] : st.og[3 + c][lane] + acc[3 + c];
+                        for (int c = 0; c < 6; ++c) k[c * D.Vt + si] = c < 3 ? dg + acc[3 + c] : acc[3 + c];
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) g[c * D.Vt + si] = st.og[c][lane] + acc[c];
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) k[c * D.Vt + si] = st.og[3 + c][lane] + acc[3 + c];
+                    }
                 }
             }
             __syncwarp();                       // lanes done with stage b and the corner slots

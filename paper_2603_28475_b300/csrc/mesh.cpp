@@ -92,6 +92,22 @@ bool build_pad_mesh(int nv, int nt, int nf, int nm, const float* rest, const int
         for (int k = 0; k < 4; ++k) vl[c[k]] += vol[t] / 4.0;
     }
     for (int i = 0; i < nv; ++i) M.vlump[i] = static_cast<float>(vl[i]);
+    {
+        // b_k = row k-1 of Dm^-1 for corners 1..3, b_0 = -(sum of the rows)
+        std::vector<double> wd(nv, 0.0);
+        for (int t = 0; t < nt; ++t) {
+            const int* c = tets + 4 * static_cast<size_t>(t);
+            const double* Bi = &Binv[9 * static_cast<size_t>(t)];
+            double b0[3] = {-(Bi[0] + Bi[3] + Bi[6]), -(Bi[1] + Bi[4] + Bi[7]), -(Bi[2] + Bi[5] + Bi[8])};
+            wd[c[0]] += vol[t] * (b0[0] * b0[0] + b0[1] * b0[1] + b0[2] * b0[2]);
+            for (int k = 1; k < 4; ++k) {
+                const double* r = Bi + 3 * (k - 1);
+                wd[c[k]] += vol[t] * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+            }
+        }
+        M.wdiag.assign(nv, 0.0f);
+        for (int i = 0; i < nv; ++i) M.wdiag[i] = static_cast<float>(wd[i]);
+    }
 
     // canonical surface: boundary faces (sorted ids), sorted lexicographically
     std::vector<std::array<int, 3>> faces;
@@ -274,16 +290,18 @@ bool build_pad_mesh(int nv, int nt, int nf, int nm, const float* rest, const int
     M.vuser.assign(nv, 0);
     for (int v = 0; v < nv; ++v) M.vuser[vint[v]] = v;
     {
-        std::vector<float> X2(3 * static_cast<size_t>(nv)), vl2(nv);
+        std::vector<float> X2(3 * static_cast<size_t>(nv)), vl2(nv), wd2(nv);
         std::vector<uint8_t> fx2(nv);
         for (int j = 0; j < nv; ++j) {
             int u = M.vuser[j];
             for (int r = 0; r < 3; ++r) X2[3 * j + r] = M.X[3 * u + r];
             vl2[j] = M.vlump[u];
+            wd2[j] = M.wdiag[u];
             fx2[j] = M.fixed[u];
         }
         M.X.swap(X2);
         M.vlump.swap(vl2);
+        M.wdiag.swap(wd2);
         M.fixed.swap(fx2);
     }
     for (int& v : M.sv) v = vint[v];

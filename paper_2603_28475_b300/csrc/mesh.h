@@ -21,6 +21,9 @@ struct PadMesh {
     std::vector<int> vuser;           // [n_v] internal id -> input vertex id
     std::vector<float> X;             // [n_v*3] rest positions
     std::vector<float> vlump;         // [n_v] lumped rest volume (sum of V/4); mass = rho * vlump
+    std::vector<float> wdiag;         // [n_v] sum over the vertex's corners of V |b|^2 (b: the corner's
+                                      // row of the shape matrix); the elastic block's static diagonal
+                                      // is h^2 mu wdiag
     std::vector<uint8_t> fixed;       // [n_v] 1 = Dirichlet
     // tets in patch order, kPatchTets slots per patch
     std::vector<float> B;             // [9][n_slots] Dm^-1 (row-major entries), SoA

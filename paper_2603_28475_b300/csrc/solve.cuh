@@ -67,6 +67,7 @@ struct Dev {
     const float* X;           // [3][XVt] rest positions
     int XVt;
     const float* vlump;       // [XVt]
+    const float* wdiag;       // [XVt] static diagonal of the elastic blocks / (h^2 mu)
     const uint8_t* fixed;     // [XVt]
     const int* vuser;         // [XVt] internal vertex -> input vertex id (mesh-local)
     const float* B;           // [9][Tt], Tt = total tet slots
