@@ -1259,61 +1259,95 @@ struct Dots {
 
 // Completes g and the blocks at u + alpha p (inertia, Dirichlet), applies
 // the preconditioner and reduces the Dai-Kou dot products.
+// The vertex passes issue every load of two vertices before any store or
+// branch (the Dirichlet flag is read as a value), so that each thread keeps
+// its memory requests in flight together; vertices are visited in the same
+// per-thread order (i, i + kThreads, ...) as a one-by-one loop, so the sums
+// do not change.
+constexpr int kVertUnroll = 2;
+
 __device__ __noinline__ Dots finalize(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, int gb, int go, bool dots) {
     FSum sv[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     float gi[1] = {0.f};
     int bad = 0;
     const float rho = P.rho;
-    for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
-        int si = P.v_off + i;
-        float* g = D.g[gb];
-        if (D.fixed[M.xv_off + i]) {
+    float* g = D.g[gb];
+    const float* gold = D.g[go];
+    const float* blk = D.blk[gb];
+    const size_t Vt = D.Vt;
+    for (int i0 = threadIdx.x; i0 < M.n_v; i0 += kVertUnroll * kThreads) {
+        float mm[kVertUnroll], pv[kVertUnroll][3], du[kVertUnroll][3], gg[kVertUnroll][3], go3[kVertUnroll][3];
+        float K[kVertUnroll][6];
+        bool fx[kVertUnroll], ok[kVertUnroll];
+#pragma unroll
+        for (int u = 0; u < kVertUnroll; ++u) {
+            const int i = i0 + u * kThreads;
+            ok[u] = i < M.n_v;
+            const int ii = ok[u] ? i : i0;             // in-bounds index for the loads
+            const size_t si = (size_t)P.v_off + ii;
+            fx[u] = D.fixed[M.xv_off + ii] != 0;
+            mm[u] = rho * D.vlump[M.xv_off + ii];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                g[c * D.Vt + si] = 0.f;
-                D.z[c * D.Vt + si] = 0.f;
+                const size_t sc = c * Vt + si;
+                pv[u][c] = D.p[sc];
+                du[u][c] = (D.uh[sc] - D.uhat[sc]) + D.ul[sc];
+                gg[u][c] = g[sc];
+                go3[u][c] = dots ? gold[sc] : 0.f;
             }
-            continue;
-        }
-        float m = rho * D.vlump[M.xv_off + i];
-        float g1[3], pv[3], K[6];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            int sc = c * D.Vt + si;
-            pv[c] = D.p[sc];
-            float du = (D.uh[sc] - D.uhat[sc]) + D.ul[sc] + alpha * pv[c];
-            g1[c] = g[sc] + m * du;
-            g[sc] = g1[c];
+            for (int c = 0; c < 6; ++c) K[u][c] = blk[c * Vt + si];
         }
 #pragma unroll
-        for (int c = 0; c < 6; ++c) K[c] = D.blk[gb][c * D.Vt + si];
-        K[0] += m; K[1] += m; K[2] += m;
-        float Ki[6];
-        if (P.precond == 0) {
-            if (!sym_inverse(K, Ki)) bad = 1;
-        } else {
-            Ki[0] = 1.f / K[0]; Ki[1] = 1.f / K[1]; Ki[2] = 1.f / K[2];
-            Ki[3] = Ki[4] = Ki[5] = 0.f;
-        }
-        float z[3];
-        sym_apply(Ki, g1, z);
+        for (int u = 0; u < kVertUnroll; ++u) {
+            if (!ok[u]) continue;
+            const size_t si = (size_t)P.v_off + i0 + u * kThreads;
+            if (fx[u]) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            D.z[c * D.Vt + si] = z[c];
-            gi[0] = fmaxf(gi[0], fabsf(g1[c]));
-        }
-        if (!(isfinite(g1[0]) && isfinite(g1[1]) && isfinite(g1[2]))) bad = 1;
-        if (dots) {
-            float y[3], Py[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) y[c] = g1[c] - D.g[go][c * D.Vt + si];
-            sym_apply(Ki, y, Py);
+                for (int c = 0; c < 3; ++c) {
+                    g[c * Vt + si] = 0.f;
+                    D.z[c * Vt + si] = 0.f;
+                }
+                continue;
+            }
+            const float m = mm[u];
+            float g1[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                fsum_add(sv[0], __fmul_rn(z[c], y[c]));
-                fsum_add(sv[1], __fmul_rn(y[c], Py[c]));
-                fsum_add(sv[2], __fmul_rn(pv[c], g1[c]));
-                fsum_add(sv[3], __fmul_rn(y[c], pv[c]));
+                g1[c] = gg[u][c] + m * (du[u][c] + alpha * pv[u][c]);
+                g[c * Vt + si] = g1[c];
+            }
+            float Kv[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) Kv[c] = K[u][c];
+            Kv[0] += m; Kv[1] += m; Kv[2] += m;
+            float Ki[6];
+            if (P.precond == 0) {
+                if (!sym_inverse(Kv, Ki)) bad = 1;
+            } else {
+                Ki[0] = 1.f / Kv[0]; Ki[1] = 1.f / Kv[1]; Ki[2] = 1.f / Kv[2];
+                Ki[3] = Ki[4] = Ki[5] = 0.f;
+            }
+            float z[3];
+            sym_apply(Ki, g1, z);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                D.z[c * Vt + si] = z[c];
+                gi[0] = fmaxf(gi[0], fabsf(g1[c]));
+            }
+            if (!(isfinite(g1[0]) && isfinite(g1[1]) && isfinite(g1[2]))) bad = 1;
+            if (dots) {
+                float y[3], Py[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) y[c] = g1[c] - go3[u][c];
+                sym_apply(Ki, y, Py);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    fsum_add(sv[0], __fmul_rn(z[c], y[c]));
+                    fsum_add(sv[1], __fmul_rn(y[c], Py[c]));
+                    fsum_add(sv[2], __fmul_rn(pv[u][c], g1[c]));
+                    fsum_add(sv[3], __fmul_rn(y[c], pv[u][c]));
+                }
             }
         }
     }
@@ -1342,33 +1376,58 @@ __device__ __noinline__ DirOut direction(const Dev& D, const PadDev& P, const Me
     float pn[1] = {0.f};
     const float rho = P.rho;
     const float bf = (float)beta;
-    for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
-        int si = P.v_off + i;
-        bool fx = D.fixed[M.xv_off + i] != 0;
-        float m = rho * D.vlump[M.xv_off + i];
-        float n2 = 0.f;
+    const float* g = D.g[gb];
+    const size_t Vt = D.Vt;
+    for (int i0 = threadIdx.x; i0 < M.n_v; i0 += kVertUnroll * kThreads) {
+        float mm[kVertUnroll], pv[kVertUnroll][3], zv[kVertUnroll][3], gv[kVertUnroll][3];
+        float uh[kVertUnroll][3], ul[kVertUnroll][3];
+        bool fx[kVertUnroll], ok[kVertUnroll];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            int sc = c * D.Vt + si;
-            float pv = D.p[sc];
-            if (move && !fx) {
-                float t = alpha * pv;
-                float hi = D.uh[sc], lo = D.ul[sc];
-                float s = hi + t;
-                float bb = s - hi;
-                float err = (hi - (s - bb)) + (t - bb);
-                lo += err;
-                float nh = s + lo;
-                D.ul[sc] = lo - (nh - s);
-                D.uh[sc] = nh;
+        for (int u = 0; u < kVertUnroll; ++u) {
+            const int i = i0 + u * kThreads;
+            ok[u] = i < M.n_v;
+            const int ii = ok[u] ? i : i0;
+            const size_t si = (size_t)P.v_off + ii;
+            fx[u] = D.fixed[M.xv_off + ii] != 0;
+            mm[u] = rho * D.vlump[M.xv_off + ii];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const size_t sc = c * Vt + si;
+                pv[u][c] = D.p[sc];
+                zv[u][c] = D.z[sc];
+                gv[u][c] = g[sc];
+                uh[u][c] = move ? D.uh[sc] : 0.f;
+                ul[u][c] = move ? D.ul[sc] : 0.f;
             }
-            float np = fx ? 0.f : (-D.z[sc] + bf * pv);
-            D.p[sc] = np;
-            n2 += np * np;
-            fsum_add(sgp, __fmul_rn(D.g[gb][sc], np));
         }
-        fsum_add(smp, __fmul_rn(m, n2));
-        pn[0] = fmaxf(pn[0], sqrtf(n2));
+#pragma unroll
+        for (int u = 0; u < kVertUnroll; ++u) {
+            if (!ok[u]) continue;
+            const size_t si = (size_t)P.v_off + i0 + u * kThreads;
+            float n2 = 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const size_t sc = c * Vt + si;
+                if (move && !fx[u]) {
+                    // u += alpha p as a double-float sum (hi, lo)
+                    float t = alpha * pv[u][c];
+                    float hi = uh[u][c], lo = ul[u][c];
+                    float sm = hi + t;
+                    float bb = sm - hi;
+                    float err = (hi - (sm - bb)) + (t - bb);
+                    lo += err;
+                    float nh = sm + lo;
+                    D.ul[sc] = lo - (nh - sm);
+                    D.uh[sc] = nh;
+                }
+                float np = fx[u] ? 0.f : (-zv[u][c] + bf * pv[u][c]);
+                D.p[sc] = np;
+                n2 += np * np;
+                fsum_add(sgp, __fmul_rn(gv[u][c], np));
+            }
+            fsum_add(smp, __fmul_rn(mm[u], n2));
+            pn[0] = fmaxf(pn[0], sqrtf(n2));
+        }
     }
     double v[2] = {fsum_value(sgp), fsum_value(smp)};
     block_sum<2>(v);
