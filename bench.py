@@ -352,7 +352,7 @@ def run_ours(args, rank, world):
                             "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                             "kernel": "tac::solve_kernel", "bytes_per_launch": bytes_per_launch,
                             "launch_ms": launch_ms},
-               "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
+               "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 3 * args.steps,
                "clocks": clk.summary(),
                "converged_fraction": conv_job / (args.steps * args.envs * world),
                "iters_per_pad_frame": {"p50": float(np.percentile(its, 50)), "p99": float(np.percentile(its, 99)),
