@@ -383,6 +383,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     LagRec* lag = dalloc<LagRec>(K, pc, rc);
     float* slotbuf = dalloc<float>(K, 9 * 6 * pc, rc);
     double* bpair = dalloc<double>(K, pc, rc);
+    Feature<double>* fcache = dalloc<Feature<double>>(K, pc, rc);
     int* ent = dalloc<int>(K, 6 * pc, rc);
     int* cvl = dalloc<int>(K, 6 * pc + 1, rc);
     int* cvo = dalloc<int>(K, 6 * pc + 1, rc);
@@ -510,7 +511,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     D.uh = st3[0]; D.ul = st3[1]; D.u0h = st3[2]; D.u0l = st3[3]; D.vel = st3[4]; D.uhat = st3[5];
     D.p = st3[6]; D.z = st3[7];
     D.g[0] = g0; D.g[1] = g1; D.blk[0] = k0; D.blk[1] = k1;
-    D.pairs = pairs; D.lag = lag; D.slotbuf = slotbuf; D.bpair = bpair; D.ent = ent; D.cvl = cvl; D.cvo = cvo; D.cnt = cnt;
+    D.pairs = pairs; D.lag = lag; D.slotbuf = slotbuf; D.bpair = bpair; D.fcache = fcache; D.ent = ent; D.cvl = cvl; D.cvo = cvo; D.cnt = cnt;
     D.ilist = ilist; D.stats = stats; D.norms = norms; D.queue = queue;
     D.pad_nlag = pad_nlag; D.adj_x = adj_x; D.adj_r = adj_r;
     D.status = nullptr; D.iters = nullptr;

@@ -106,6 +106,18 @@ __device__ __forceinline__ double barrier_b2(double d, double dh) {
     return -2.0 * log(d / dh) - 4.0 * t / d + t * t / (d * d);
 }
 
+// b, b' and b'' together from one logarithm and one reciprocal (float64 is a
+// narrow pipe; the three separate forms above cost three of each)
+struct Barrier3 {
+    double b, b1, b2;
+};
+__device__ __forceinline__ Barrier3 barrier_all(double d, double dh) {
+    if (d >= dh) return Barrier3{0.0, 0.0, 0.0};
+    const double t = d - dh, L = log(d / dh), id = 1.0 / d;
+    const double ti = t * id;
+    return Barrier3{-t * t * L, -2.0 * t * L - t * ti, -2.0 * L - 4.0 * ti + ti * ti};
+}
+
 // ---------------------------------------------------------------------------
 // Contact features. A pair has 4 slots; r = sum_s w_s v_s is the vector
 // between the closest points (indenter -> gel), d = |r|. Within the active

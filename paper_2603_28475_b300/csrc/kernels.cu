@@ -72,6 +72,7 @@ struct Shared {
     int pad;
     int flag;
     int expired;
+    int fok;                    // D.fcache holds the float64 features of the current point and pair set
 };
 
 // one CTA-wide scratch object (dynamic shared memory, sizeof(Shared) bytes at
@@ -133,6 +134,7 @@ __device__ __forceinline__ void load_pad(const Dev& D, int pad) {
         S.P = D.pads[pad];
         S.M = D.meshes[S.P.mesh];
         S.E = D.envs[S.P.env];
+        S.fok = 0;
     }
     __syncthreads();
 }
@@ -766,6 +768,7 @@ template <class Src>
 __device__ __noinline__ int bp_build(const Src& src, const Dev& D, const MeshDev& M, const EnvDev& E, int* ilist, double r,
                         int4* out, int cap) {
     const int tid = threadIdx.x;
+    if (tid == 0) S.fok = 0;             // a new candidate list invalidates cached features
     const float rlo = (float)(r * (1.0 - 1e-5)), rhi = (float)(r * (1.0 + 1e-5));
     const float rc = (float)(r * (1.0 + 1e-4)) + 1e-12f;     // conservative culling radius
     // 1. indenter AABB
@@ -980,6 +983,8 @@ __device__ __noinline__ void pair_php(const Dev& D, const PadDev& P, const MeshD
     double acc = 0.0, amin = 1e300;
     const int4* pr = D.pairs + P.pair_off;
     double* bcur = D.bpair + P.pair_off;
+    const Feature<double>* fc = D.fcache + P.pair_off;
+    const bool cached = S.fok != 0;
     const double dh = P.dhat, kap = P.kappa;
     for (int k = threadIdx.x; k < np; k += kThreads) {
         int gsl[4], isl[4];
@@ -1007,13 +1012,18 @@ __device__ __noinline__ void pair_php(const Dev& D, const PadDev& P, const MeshD
         } else {
             V3<double> X[4];
             load_slots<double>(D, P, M, gsl, isl, 0.0f, s, X);
-            Feature<double> f = pair_feature<double>(q.x, X);
+            Feature<double> f;
+            if (cached && fc[k].nf >= 0)
+                f = fc[k];              // computed by the accepted trial at this point
+            else
+                f = pair_feature<double>(q.x, X);
             d = f.d;
             if (d < dh) {
                 double d1, d2;
                 feat_dir_derivs(f, X, dl, d1, d2);
-                acc += kap * (barrier_b2(d, dh) * d1 * d1 + barrier_b1(d, dh) * d2);
-                bv = barrier_b(d, dh);
+                const Barrier3 bb = barrier_all(d, dh);
+                acc += kap * (bb.b2 * d1 * d1 + bb.b1 * d2);
+                bv = bb.b;
             }
         }
         bcur[k] = bv;
@@ -1065,6 +1075,7 @@ __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const Mes
     int badl = 0;
     const int4* pr = D.pairs + P.pair_off;
     const double* bcur = D.bpair + P.pair_off;
+    Feature<double>* fc = D.fcache + P.pair_off;
     float* sb = D.slotbuf + (size_t)9 * 6 * P.pair_off;
     const double dh = P.dhat, kap = P.kappa;
     const bool trial = alpha != 0.0f;
@@ -1083,10 +1094,12 @@ __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const Mes
             for (int c = 0; c < 9; ++c) out[a][c] = 0.f;
         if ((double)d1f > kNearBand * dh) {
             acc += kap * b0;                    // b = 0 at the trial point
+            fc[k].nf = -1;
         } else {
             V3<double> X1[4];
             load_slots<double>(D, P, M, gsl, isl, alpha, s, X1);
             Feature<double> f1 = pair_feature<double>(q.x, X1);
+            fc[k] = f1;
             if (!(f1.d > 0.0)) {
                 badl = 1;
             } else if (f1.d >= dh) {
@@ -1095,7 +1108,8 @@ __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const Mes
                 V3<double> r = feat_r(f1, X1);
                 double inv = 1.0 / f1.d;
                 V3<double> rh = inv * r;
-                double b1 = kap * barrier_b1(f1.d, dh), b2 = kap * barrier_b2(f1.d, dh);
+                const Barrier3 bb = barrier_all(f1.d, dh);
+                double b1 = kap * bb.b1, b2 = kap * bb.b2;
                 double gdp = 0.0;
 #pragma unroll
                 for (int sl = 0; sl < 3; ++sl)
@@ -1114,7 +1128,7 @@ __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const Mes
                         out[sl][7] = (float)(kw * rh.x * rh.z);
                         out[sl][8] = (float)(kw * rh.y * rh.z);
                     }
-                if (trial) acc += kap * (b0 - barrier_b(f1.d, dh)) + (double)alpha * b1 * gdp;
+                if (trial) acc += kap * (b0 - bb.b) + (double)alpha * b1 * gdp;
             }
         }
 #pragma unroll
@@ -1175,6 +1189,9 @@ __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const Mes
                 for (int c = 0; c < 6; ++c) e[3 + c] = (float)(kw * Hn[c]);
             }
     }
+    // the features just written are those of the point the caller continues
+    // from when this trial is accepted (or of the current point, alpha = 0)
+    if (threadIdx.x == 0) S.fok = 1;
     double v[1] = {acc};
     block_sum<1>(v);
     rem = v[0];
