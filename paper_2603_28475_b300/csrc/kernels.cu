@@ -380,46 +380,81 @@ struct TetOut {
     double acc2;      // mu-sensitivity (pass 3)
 };
 
+// The tet passes read their arrays through these pointers, taken from the
+// batch and pad descriptors once per pass: the descriptors are reached through
+// references, and their fields would otherwise be reloaded after every store.
+struct TetPtrs {
+    const float* B;             // Dm^-1 of the pad's mesh (stride Tt between entries)
+    const uint32_t* lc;         // local vertex ids
+    const uint32_t* sl;         // corner slots
+    const float* uh;            // state of the pad (stride Vt between components)
+    const float* ul;
+    const float* p;
+    float* g;
+    float* blk;
+    const float* wd;            // static block diagonal of the mesh's vertices
+    const int* pv;              // patch vertex entries
+    const uint16_t* pc;         // patch CSR offsets
+    size_t Tt, Vt;
+};
+
+__device__ __forceinline__ TetPtrs tet_ptrs(const Dev& D, const PadDev& P, const MeshDev& M, int gb) {
+    TetPtrs T;
+    T.B = D.B + M.tet_off;
+    T.lc = D.lconn + M.tet_off;
+    T.sl = D.slot + M.tet_off;
+    T.uh = D.uh + P.v_off;
+    T.ul = D.ul + P.v_off;
+    T.p = D.p + P.v_off;
+    T.g = D.g[gb] + P.v_off;
+    T.blk = D.blk[gb] + P.v_off;
+    T.wd = D.wdiag + M.xv_off;
+    T.pv = D.pvert + M.pvert_off;
+    T.pc = D.pcsr + M.pcsr_off;
+    T.Tt = D.Tt;
+    T.Vt = D.Vt;
+    return T;
+}
+
 // asynchronous copy of one warp patch into a stage; lane k copies tet slot k
 // and, when the patch has a vertex entry k (gvf >= 0), that vertex's data.
 // The scatter passes also copy the vertex's sums so far when this is not its
 // first patch: patches of one colour class share no vertex and earlier
 // classes are complete, so those sums are final when the copy is issued.
 template <int PASS>
-__device__ __forceinline__ void issue_patch(const Dev& D, const PadDev& P, const MeshDev& M, int pi, int gvf,
-                                            PatchStage& st, int lane, int gb) {
+__device__ __forceinline__ void issue_patch(const TetPtrs& T, int pi, int gvf, PatchStage& st, int lane) {
     {
-        size_t t = (size_t)M.tet_off + (size_t)kPatchTets * pi + lane;
+        size_t t = (size_t)kPatchTets * pi + lane;
 #pragma unroll
-        for (int e = 0; e < 9; ++e) cp_async4(&st.B[e][lane], D.B + (size_t)e * D.Tt + t);
-        cp_async4(&st.lc[lane], D.lconn + t);
-        cp_async4(&st.sl[lane], D.slot + t);
+        for (int e = 0; e < 9; ++e) cp_async4(&st.B[e][lane], T.B + (size_t)e * T.Tt + t);
+        cp_async4(&st.lc[lane], T.lc + t);
+        cp_async4(&st.sl[lane], T.sl + t);
     }
     if (gvf >= 0) {
-        int si = P.v_off + (gvf & kVertMask);
+        const int lv = gvf & kVertMask;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            cp_async4(&st.uh[c][lane], D.uh + (size_t)c * D.Vt + si);
-            cp_async4(&st.ul[c][lane], D.ul + (size_t)c * D.Vt + si);
-            cp_async4(&st.p[c][lane], D.p + (size_t)c * D.Vt + si);
+            cp_async4(&st.uh[c][lane], T.uh + (size_t)c * T.Vt + lv);
+            cp_async4(&st.ul[c][lane], T.ul + (size_t)c * T.Vt + lv);
+            cp_async4(&st.p[c][lane], T.p + (size_t)c * T.Vt + lv);
         }
         if ((PASS == 1 || PASS == 2) && !(gvf & kFirstFlag)) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) cp_async4(&st.og[c][lane], D.g[gb] + (size_t)c * D.Vt + si);
+            for (int c = 0; c < 3; ++c) cp_async4(&st.og[c][lane], T.g + (size_t)c * T.Vt + lv);
             if (PASS == 1) {
 #pragma unroll
-                for (int c = 0; c < 6; ++c) cp_async4(&st.og[3 + c][lane], D.blk[gb] + (size_t)c * D.Vt + si);
+                for (int c = 0; c < 6; ++c) cp_async4(&st.og[3 + c][lane], T.blk + (size_t)c * T.Vt + lv);
             }
         } else if (PASS == 1) {
             // first patch of the vertex: the blocks' static diagonal enters here
-            cp_async4(&st.og[3][lane], D.wdiag + M.xv_off + (gvf & kVertMask));
+            cp_async4(&st.og[3][lane], T.wd + lv);
         }
     }
     cp_async_commit();
 }
 
-__device__ __forceinline__ int patch_vert(const Dev& D, const MeshDev& M, int pi, int lane) {
-    return __ldg(D.pvert + M.pvert_off + kPatchVerts * pi + lane);
+__device__ __forceinline__ int patch_vert(const TetPtrs& T, int pi, int lane) {
+    return __ldg(T.pv + kPatchVerts * pi + lane);
 }
 
 // pass 0: p^T H_e p at u; pass 1: gradient, diagonal blocks and remainder at
@@ -439,20 +474,23 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
     const int lane = tid & 31, warp = tid >> 5;
     WarpScratch& W = S.w[warp];
     const float mu = P.mu, lam = P.lam, h2 = P.h * P.h;
+    const TetPtrs T = tet_ptrs(D, P, M, gb);
+    const int* colour = D.colour + M.col_off;
+    const int n_patch = M.n_patch;
     constexpr bool kScatter = (PASS == 1 || PASS == 2);
     const int ncls = kScatter ? M.n_col : 1;
     for (int cls = 0; cls < ncls; ++cls) {
-        const int p_begin = kScatter ? __ldg(D.colour + M.col_off + cls) : 0;
-        const int p_end = kScatter ? __ldg(D.colour + M.col_off + cls + 1) : M.n_patch;
+        const int p_begin = kScatter ? __ldg(colour + cls) : 0;
+        const int p_end = kScatter ? __ldg(colour + cls + 1) : n_patch;
         int pi = p_begin + warp;
         int b = 0;
         // vertex entries of this lane: current patch (gvf_c), the next one
         // (gvf_n, loaded one patch ahead so that issuing its copy does not wait)
         int gvf_c = -1, gvf_n = -1;
         if (pi < p_end) {
-            gvf_c = patch_vert(D, M, pi, lane);
-            issue_patch<PASS>(D, P, M, pi, gvf_c, W.st[0], lane, gb);
-            if (pi + kWarps < p_end) gvf_n = patch_vert(D, M, pi + kWarps, lane);
+            gvf_c = patch_vert(T, pi, lane);
+            issue_patch<PASS>(T, pi, gvf_c, W.st[0], lane);
+            if (pi + kWarps < p_end) gvf_n = patch_vert(T, pi + kWarps, lane);
         }
         while (pi < p_end) {
             const int pn = pi + kWarps;
@@ -460,13 +498,13 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
             __syncwarp();                       // stage b complete for every lane
             int s0 = 0, s1 = 0;
             if (kScatter) {
-                s0 = __ldg(D.pcsr + M.pcsr_off + kPatchCsr * pi + lane);
-                s1 = __ldg(D.pcsr + M.pcsr_off + kPatchCsr * pi + lane + 1);
+                s0 = __ldg(T.pc + kPatchCsr * pi + lane);
+                s1 = __ldg(T.pc + kPatchCsr * pi + lane + 1);
             }
             int gvf_nn = -1;
             if (pn < p_end) {
-                issue_patch<PASS>(D, P, M, pn, gvf_n, W.st[b ^ 1], lane, gb);
-                if (pn + kWarps < p_end) gvf_nn = patch_vert(D, M, pn + kWarps, lane);
+                issue_patch<PASS>(T, pn, gvf_n, W.st[b ^ 1], lane);
+                if (pn + kWarps < p_end) gvf_nn = patch_vert(T, pn + kWarps, lane);
             }
             const PatchStage& st = W.st[b];
             const uint32_t lc = st.lc[lane];
@@ -613,10 +651,8 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
                     for (int q = s0; q < s1; ++q)
 #pragma unroll
                         for (int c = 0; c < 3; ++c) acc[c] += W.stg[c][q];
-                    float* g = D.g[gb];
-                    int si = P.v_off + gv;
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) g[c * D.Vt + si] = first ? acc[c] : st.og[c][lane] + acc[c];
+                    for (int c = 0; c < 3; ++c) T.g[c * T.Vt + gv] = first ? acc[c] : st.og[c][lane] + acc[c];
                 }
             }
             if (PASS == 1) {
@@ -634,20 +670,17 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
                         acc[3] += q0 * q0; acc[4] += q1 * q1; acc[5] += q2 * q2;
                         acc[6] += q0 * q1; acc[7] += q0 * q2; acc[8] += q1 * q2;
                     }
-                    int si = P.v_off + gv;
-                    float* g = D.g[gb];
-                    float* k = D.blk[gb];
                     if (first) {
                         const float dg = h2 * mu * st.og[3][lane];
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) g[c * D.Vt + si] = acc[c];
+                        for (int c = 0; c < 3; ++c) T.g[c * T.Vt + gv] = acc[c];
 #pragma unroll
-                        for (int c = 0; c < 6; ++c) k[c * D.Vt + si] = c < 3 ? dg + acc[3 + c] : acc[3 + c];
+                        for (int c = 0; c < 6; ++c) T.blk[c * T.Vt + gv] = c < 3 ? dg + acc[3 + c] : acc[3 + c];
                     } else {
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) g[c * D.Vt + si] = st.og[c][lane] + acc[c];
+                        for (int c = 0; c < 3; ++c) T.g[c * T.Vt + gv] = st.og[c][lane] + acc[c];
 #pragma unroll
-                        for (int c = 0; c < 6; ++c) k[c * D.Vt + si] = st.og[3 + c][lane] + acc[3 + c];
+                        for (int c = 0; c < 6; ++c) T.blk[c * T.Vt + gv] = st.og[3 + c][lane] + acc[3 + c];
                     }
                 }
             }
@@ -1288,42 +1321,51 @@ __device__ __noinline__ Dots finalize(const Dev& D, const PadDev& P, const MeshD
     float gi[1] = {0.f};
     int bad = 0;
     const float rho = P.rho;
-    float* g = D.g[gb];
-    const float* gold = D.g[go];
-    const float* blk = D.blk[gb];
+    // pointers of the pad's state, read once (see TetPtrs)
     const size_t Vt = D.Vt;
-    for (int i0 = threadIdx.x; i0 < M.n_v; i0 += kVertUnroll * kThreads) {
+    float* g = D.g[gb] + P.v_off;
+    const float* gold = D.g[go] + P.v_off;
+    const float* blk = D.blk[gb] + P.v_off;
+    const float* uhp = D.uh + P.v_off;
+    const float* ulp = D.ul + P.v_off;
+    const float* uhatp = D.uhat + P.v_off;
+    const float* pp = D.p + P.v_off;
+    float* zp = D.z + P.v_off;
+    const uint8_t* fxp = D.fixed + M.xv_off;
+    const float* vlp = D.vlump + M.xv_off;
+    const int n_v = M.n_v;
+    const bool blockp = P.precond == 0;
+    for (int i0 = threadIdx.x; i0 < n_v; i0 += kVertUnroll * kThreads) {
         float mm[kVertUnroll], pv[kVertUnroll][3], du[kVertUnroll][3], gg[kVertUnroll][3], go3[kVertUnroll][3];
         float K[kVertUnroll][6];
         bool fx[kVertUnroll], ok[kVertUnroll];
 #pragma unroll
         for (int u = 0; u < kVertUnroll; ++u) {
             const int i = i0 + u * kThreads;
-            ok[u] = i < M.n_v;
+            ok[u] = i < n_v;
             const int ii = ok[u] ? i : i0;             // in-bounds index for the loads
-            const size_t si = (size_t)P.v_off + ii;
-            fx[u] = D.fixed[M.xv_off + ii] != 0;
-            mm[u] = rho * D.vlump[M.xv_off + ii];
+            fx[u] = fxp[ii] != 0;
+            mm[u] = rho * vlp[ii];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const size_t sc = c * Vt + si;
-                pv[u][c] = D.p[sc];
-                du[u][c] = (D.uh[sc] - D.uhat[sc]) + D.ul[sc];
+                const size_t sc = c * Vt + ii;
+                pv[u][c] = pp[sc];
+                du[u][c] = (uhp[sc] - uhatp[sc]) + ulp[sc];
                 gg[u][c] = g[sc];
                 go3[u][c] = dots ? gold[sc] : 0.f;
             }
 #pragma unroll
-            for (int c = 0; c < 6; ++c) K[u][c] = blk[c * Vt + si];
+            for (int c = 0; c < 6; ++c) K[u][c] = blk[c * Vt + ii];
         }
 #pragma unroll
         for (int u = 0; u < kVertUnroll; ++u) {
             if (!ok[u]) continue;
-            const size_t si = (size_t)P.v_off + i0 + u * kThreads;
+            const size_t si = (size_t)i0 + u * kThreads;
             if (fx[u]) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     g[c * Vt + si] = 0.f;
-                    D.z[c * Vt + si] = 0.f;
+                    zp[c * Vt + si] = 0.f;
                 }
                 continue;
             }
@@ -1339,7 +1381,7 @@ __device__ __noinline__ Dots finalize(const Dev& D, const PadDev& P, const MeshD
             for (int c = 0; c < 6; ++c) Kv[c] = K[u][c];
             Kv[0] += m; Kv[1] += m; Kv[2] += m;
             float Ki[6];
-            if (P.precond == 0) {
+            if (blockp) {
                 if (!sym_inverse(Kv, Ki)) bad = 1;
             } else {
                 Ki[0] = 1.f / Kv[0]; Ki[1] = 1.f / Kv[1]; Ki[2] = 1.f / Kv[2];
@@ -1349,7 +1391,7 @@ __device__ __noinline__ Dots finalize(const Dev& D, const PadDev& P, const MeshD
             sym_apply(Ki, g1, z);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                D.z[c * Vt + si] = z[c];
+                zp[c * Vt + si] = z[c];
                 gi[0] = fmaxf(gi[0], fabsf(g1[c]));
             }
             if (!(isfinite(g1[0]) && isfinite(g1[1]) && isfinite(g1[2]))) bad = 1;
@@ -1393,34 +1435,41 @@ __device__ __noinline__ DirOut direction(const Dev& D, const PadDev& P, const Me
     float pn[1] = {0.f};
     const float rho = P.rho;
     const float bf = (float)beta;
-    const float* g = D.g[gb];
+    // pointers of the pad's state, read once (see TetPtrs)
     const size_t Vt = D.Vt;
-    for (int i0 = threadIdx.x; i0 < M.n_v; i0 += kVertUnroll * kThreads) {
+    const float* g = D.g[gb] + P.v_off;
+    float* uhp = D.uh + P.v_off;
+    float* ulp = D.ul + P.v_off;
+    float* pp = D.p + P.v_off;
+    const float* zp = D.z + P.v_off;
+    const uint8_t* fxp = D.fixed + M.xv_off;
+    const float* vlp = D.vlump + M.xv_off;
+    const int n_v = M.n_v;
+    for (int i0 = threadIdx.x; i0 < n_v; i0 += kVertUnroll * kThreads) {
         float mm[kVertUnroll], pv[kVertUnroll][3], zv[kVertUnroll][3], gv[kVertUnroll][3];
         float uh[kVertUnroll][3], ul[kVertUnroll][3];
         bool fx[kVertUnroll], ok[kVertUnroll];
 #pragma unroll
         for (int u = 0; u < kVertUnroll; ++u) {
             const int i = i0 + u * kThreads;
-            ok[u] = i < M.n_v;
+            ok[u] = i < n_v;
             const int ii = ok[u] ? i : i0;
-            const size_t si = (size_t)P.v_off + ii;
-            fx[u] = D.fixed[M.xv_off + ii] != 0;
-            mm[u] = rho * D.vlump[M.xv_off + ii];
+            fx[u] = fxp[ii] != 0;
+            mm[u] = rho * vlp[ii];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const size_t sc = c * Vt + si;
-                pv[u][c] = D.p[sc];
-                zv[u][c] = D.z[sc];
+                const size_t sc = c * Vt + ii;
+                pv[u][c] = pp[sc];
+                zv[u][c] = zp[sc];
                 gv[u][c] = g[sc];
-                uh[u][c] = move ? D.uh[sc] : 0.f;
-                ul[u][c] = move ? D.ul[sc] : 0.f;
+                uh[u][c] = move ? uhp[sc] : 0.f;
+                ul[u][c] = move ? ulp[sc] : 0.f;
             }
         }
 #pragma unroll
         for (int u = 0; u < kVertUnroll; ++u) {
             if (!ok[u]) continue;
-            const size_t si = (size_t)P.v_off + i0 + u * kThreads;
+            const size_t si = (size_t)i0 + u * kThreads;
             float n2 = 0.f;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -1434,11 +1483,11 @@ __device__ __noinline__ DirOut direction(const Dev& D, const PadDev& P, const Me
                     float err = (hi - (sm - bb)) + (t - bb);
                     lo += err;
                     float nh = sm + lo;
-                    D.ul[sc] = lo - (nh - sm);
-                    D.uh[sc] = nh;
+                    ulp[sc] = lo - (nh - sm);
+                    uhp[sc] = nh;
                 }
                 float np = fx[u] ? 0.f : (-zv[u][c] + bf * pv[u][c]);
-                D.p[sc] = np;
+                pp[sc] = np;
                 n2 += np * np;
                 fsum_add(sgp, __fmul_rn(gv[u][c], np));
             }
