@@ -50,10 +50,16 @@ struct PatchStage {
     float og[9][32];            // scatter passes: the vertices' sums so far (gradient, blocks)
 };
 
+// Corner slot s of a patch lives at s + s / 32 in the corner stage: a
+// vertex's run starts near 4 x its local id, so without the padding word per
+// 32 slots the lanes 8 apart would read the same bank in the scatter.
+constexpr int kStagePad = kStage + kStage / 32;
+__device__ __forceinline__ int stg_pos(int s) { return s + (s >> 5); }
+
 // per-warp scratch of the tet passes
 struct WarpScratch {
     PatchStage st[2];           // double buffer: the warp's next patch loads while this one computes
-    float stg[6][kStage];       // corner values of the current patch: force (3) and, in the gradient
+    float stg[6][kStagePad];    // corner values of the current patch: force (3) and, in the gradient
                                 // pass, s = sqrt(hV coef) c whose outer product is the block's
                                 // non-static part
 };
@@ -584,7 +590,7 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
                         int slot = (int)((sl >> (8 * k)) & 0xff);
     #pragma unroll
                         for (int c = 0; c < 3; ++c)
-                            W.stg[c][slot] = (k == 0) ? -(Hc[0][c] + Hc[1][c] + Hc[2][c]) : Hc[k - 1][c];
+                            W.stg[c][stg_pos(slot)] = (k == 0) ? -(Hc[0][c] + Hc[1][c] + Hc[2][c]) : Hc[k - 1][c];
                     }
                 } else {
                     if (!(f.J > 0.0f)) out.bad = 1;
@@ -630,7 +636,7 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
                         float cc[3];
     #pragma unroll
                         for (int r = 0; r < 3; ++r) cc[r] = f.cof[3 * r] * bv[0] + f.cof[3 * r + 1] * bv[1] + f.cof[3 * r + 2] * bv[2];
-                        int slot = (int)((sl >> (8 * k)) & 0xff);
+                        int slot = stg_pos((int)((sl >> (8 * k)) & 0xff));
                         out.fmax = fmaxf(out.fmax, fmaxf(fabsf(fo[0]), fmaxf(fabsf(fo[1]), fabsf(fo[2]))));
                         W.stg[0][slot] = fo[0];
                         W.stg[1][slot] = fo[1];
@@ -650,7 +656,7 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
                     float acc[3] = {0.f, 0.f, 0.f};
                     for (int q = s0; q < s1; ++q)
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) acc[c] += W.stg[c][q];
+                        for (int c = 0; c < 3; ++c) acc[c] += W.stg[c][stg_pos(q)];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) T.g[c * T.Vt + gv] = first ? acc[c] : st.og[c][lane] + acc[c];
                 }
@@ -664,8 +670,9 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
 #pragma unroll
                     for (int c = 0; c < 9; ++c) acc[c] = 0.f;
                     for (int q = s0; q < s1; ++q) {
-                        const float f0 = W.stg[0][q], f1 = W.stg[1][q], f2 = W.stg[2][q];
-                        const float q0 = W.stg[3][q], q1 = W.stg[4][q], q2 = W.stg[5][q];
+                        const int qp = stg_pos(q);
+                        const float f0 = W.stg[0][qp], f1 = W.stg[1][qp], f2 = W.stg[2][qp];
+                        const float q0 = W.stg[3][qp], q1 = W.stg[4][qp], q2 = W.stg[5][qp];
                         acc[0] += f0; acc[1] += f1; acc[2] += f2;
                         acc[3] += q0 * q0; acc[4] += q1 * q1; acc[5] += q2 * q2;
                         acc[6] += q0 * q1; acc[7] += q0 * q2; acc[8] += q1 * q2;
