@@ -16,6 +16,10 @@ fixed. dg/dtheta:
   * mu_f: the lagged friction gradient is linear in mu_f;
   * pose: central difference (step 1e-7) of the total gradient in each pose
     component, the indenter vertices recomputed from the pose.
+
+``adjoint_frame`` adds the sensitivities to the frame's start (positions,
+velocities, start pose) with the frame's friction lag held fixed, and
+``adjoint_sequence`` chains frames in a reverse sweep.
 """
 from __future__ import annotations
 
@@ -38,13 +42,14 @@ def marker_transpose(pad, dL_dm):
     return g
 
 
-def frame_of(pad, ind, state_prev, pose_next, prm_margin=1.0):
+def frame_of(pad, ind, state_prev, pose_next, prm_margin=1.0, lag=None):
     x_t = state_prev.x
     xhat = x_t + pad.h * state_prev.v
     y_t = G.indenter_world(ind.verts, state_prev.pose)
     y_n = G.indenter_world(ind.verts, pose_next)
-    cand = BP.candidates(x_t, y_t, pad, ind, pad.dhat * (1.0 + prm_margin))
-    lag = En.friction_lag(cand, x_t, y_t, pad, ind)
+    if lag is None:
+        cand = BP.candidates(x_t, y_t, pad, ind, pad.dhat * (1.0 + prm_margin))
+        lag = En.friction_lag(cand, x_t, y_t, pad, ind)
     return En.Frame(pad, ind, x_t, xhat, y_t, y_n, lag)
 
 
@@ -89,4 +94,110 @@ def adjoint(pad, ind, state_prev, state_new, dL_dm, fd_pose=1e-7):
             _, g, _ = En.total(frq, x, 1.0, pairs)
             gs.append(g)
         out[3 + m] = -dot_free((gs[0] - gs[1]) / (2.0 * fd_pose))
+    return out
+
+
+def adjoint_frame(pad, ind, state_prev, state_new, dL_dm=None, dL_dx=None, lag=None, fd_pose=1e-7, fd_x=1e-9):
+    """Adjoint of one frame of a sequence. The frame's friction lag (normal
+    forces, contact normals, closest-point weights, from its start state) is
+    a constant of the frame, as in the frame's solve.
+
+    The right-hand side is the loss gradient with respect to the frame's end
+    positions: the marker readout's transpose of dL_dm [M, 2] plus dL_dx
+    [V, 3] (what later frames contribute), either may be None. Returns
+    (theta [15], dL/dx^t [V, 3], dL/dv^t [V, 3]) with theta = (Lame lambda,
+    Lame mu, mu_f, end pose (6), start pose (6)), each -lambda^T dg/d(.):
+      * the first 9 as in ``adjoint``;
+      * start pose: central difference of g in the start pose (it enters the
+        friction term through the indenter's displacement over the frame);
+      * x^t: central difference of g in each free start coordinate, x-hat =
+        x^t + h v^t moving with it (inertia and the friction displacement);
+      * v^t: g is affine in x-hat with dg/dx-hat = -M, so dL/dv^t = h M lambda.
+    """
+    fr = frame_of(pad, ind, state_prev, state_new.pose, lag=lag)
+    x = state_new.x
+    pairs = BP.candidates(x, fr.y(1.0), pad, ind, 2.0 * pad.dhat)
+    H = NW.assemble(fr, x, 1.0, pairs)
+    fdof = np.repeat(pad.free, 3)
+    b = np.zeros(x.size)
+    if dL_dm is not None:
+        b += marker_transpose(pad, np.asarray(dL_dm, np.float64)).ravel()
+    if dL_dx is not None:
+        b += np.asarray(dL_dx, np.float64).ravel()
+    lam = np.zeros_like(b)
+    lam[fdof] = np.linalg.solve(H[np.ix_(fdof, fdof)], b[fdof])
+    lam = lam.reshape(-1, 3)
+
+    def dot_free(g):
+        return float(np.sum(lam[pad.free] * g[pad.free]))
+
+    theta = np.zeros(15)
+    p_lam = copy.copy(pad)
+    p_lam.mu, p_lam.lam = 0.0, 1.0
+    p_mu = copy.copy(pad)
+    p_mu.mu, p_mu.lam = 1.0, 0.0
+    theta[0] = -dot_free(En.elastic(x, p_lam, blocks=False)[1])
+    theta[1] = -dot_free(En.elastic(x, p_mu, blocks=False)[1])
+    if pad.mu_f > 0 and fr.lag["lam"].size:
+        p_f = copy.copy(pad)
+        p_f.mu_f = 1.0
+        theta[2] = -dot_free(En.friction(fr.lag, x, fr.x_t, fr.y(1.0), fr.y_t, p_f)[1])
+
+    def g_of(x_t=fr.x_t, xhat=fr.xhat, y_t=fr.y_t, y_n=fr.y_next):
+        return En.total(En.Frame(pad, ind, x_t, xhat, y_t, y_n, fr.lag), x, 1.0, pairs)[1]
+
+    pose_n = np.asarray(state_new.pose, np.float64)
+    pose_t = np.asarray(state_prev.pose, np.float64)
+    for m in range(6):
+        gs = []
+        for sgn in (1.0, -1.0):
+            q = pose_n.copy()
+            q[m] += sgn * fd_pose
+            gs.append(g_of(y_n=G.indenter_world(ind.verts, q)))
+        theta[3 + m] = -dot_free((gs[0] - gs[1]) / (2.0 * fd_pose))
+        gs = []
+        for sgn in (1.0, -1.0):
+            q = pose_t.copy()
+            q[m] += sgn * fd_pose
+            gs.append(g_of(y_t=G.indenter_world(ind.verts, q)))
+        theta[9 + m] = -dot_free((gs[0] - gs[1]) / (2.0 * fd_pose))
+    dx0 = np.zeros_like(x)
+    for i in np.nonzero(pad.free)[0]:
+        for c in range(3):
+            gs = []
+            for sgn in (1.0, -1.0):
+                xt = fr.x_t.copy()
+                xh = fr.xhat.copy()
+                xt[i, c] += sgn * fd_x
+                xh[i, c] += sgn * fd_x
+                gs.append(g_of(x_t=xt, xhat=xh))
+            dx0[i, c] = -dot_free((gs[0] - gs[1]) / (2.0 * fd_x))
+    dv0 = pad.h * pad.mass[:, None] * lam
+    dv0[~pad.free] = 0.0
+    return theta, dx0, dv0
+
+
+def adjoint_sequence(pad, ind, states, dL_dms, lags=None):
+    """dL/dtheta for L = sum_f dL_dms[f-1] . markers(x^f) over frames
+    1..F of a run from states[0], each frame's friction lag held fixed
+    (``lags[f-1]`` if given, else the lag of states[f-1]). theta = (Lame
+    lambda, Lame mu, mu_f, end pose of frame 1, ..., end pose of frame F)
+    [3 + 6F]; frame 1's start pose is a constant.
+
+    Reverse sweep: frame f's end state receives the markers' gradient plus
+    a_x + a_v / h from frame f+1 (v^f = (x^f - x^(f-1)) / h); frame f then
+    passes a_x = dL/dx^(f-1) - a_v / h and a_v = dL/dv^(f-1) on."""
+    F = len(states) - 1
+    out = np.zeros(3 + 6 * F)
+    a_x = np.zeros_like(states[0].x)
+    a_v = np.zeros_like(states[0].x)
+    for f in range(F, 0, -1):
+        th, dx0, dv0 = adjoint_frame(pad, ind, states[f - 1], states[f], dL_dms[f - 1], a_x + a_v / pad.h,
+                                     lag=None if lags is None else lags[f - 1])
+        out[0:3] += th[0:3]
+        out[3 + 6 * (f - 1):3 + 6 * f] += th[3:9]
+        if f >= 2:
+            out[3 + 6 * (f - 2):3 + 6 * (f - 1)] += th[9:15]
+        a_x = dx0 - a_v / pad.h
+        a_v = dv0
     return out

@@ -212,10 +212,12 @@ class FrameInfo:
     energy_monotone: bool = True
 
 
-def solve_frame(pad, ind, state, pose_next, prm=Params(), trace=None):
+def solve_frame(pad, ind, state, pose_next, prm=Params(), trace=None, lag=None):
     """Advance one frame from ``state`` to the indenter pose ``pose_next``.
     Returns (new State, FrameInfo). ``trace``, if a list, receives per
-    iteration (x-step size, energy, |g|_inf)."""
+    iteration (x-step size, energy, |g|_inf). ``lag``, if given, replaces
+    the friction lag computed from the frame's start (used to re-solve a
+    frame with the lag of another run held fixed)."""
     info = FrameInfo(g_ref=pad.g_ref)
     h, dhat = pad.h, pad.dhat
     margin = prm.margin_factor * dhat
@@ -225,7 +227,8 @@ def solve_frame(pad, ind, state, pose_next, prm=Params(), trace=None):
     y_t = G.indenter_world(ind.verts, state.pose)
     y_n = G.indenter_world(ind.verts, pose_next)
     cand = BP.candidates(x_t, y_t, pad, ind, r_inf)
-    lag = En.friction_lag(cand, x_t, y_t, pad, ind)
+    if lag is None:
+        lag = En.friction_lag(cand, x_t, y_t, pad, ind)
     fr = En.Frame(pad, ind, x_t, xhat, y_t, y_n, lag)
     Dy = float(np.sqrt(((y_n - y_t) ** 2).sum(axis=1)).max())
     free = pad.free

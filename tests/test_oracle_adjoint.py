@@ -89,3 +89,81 @@ def test_marker_transpose_is_the_adjoint_of_the_readout(setup):
     lhs = float(np.sum(c * SV.markers(pad, pad.rest + u)))
     rhs = float(np.sum(AD.marker_transpose(pad, c) * u))
     assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+# --- sequence adjoint (reverse sweep over frames, each frame's lag held fixed)
+
+def _solve_lag(pad, ind, st_prev, pose, lag):
+    prm = SV.Params(tol=1e-6)
+    st, info = SV.solve_frame(pad, ind, st_prev, pose, prm, lag=lag)
+    assert info.status == SV.CONVERGED
+    fr = AD.frame_of(pad, ind, st_prev, pose, lag=lag)
+    x, _, _ = NW.newton_polish(fr, st.x, 1.0, prm, tol_rel=1e-13)
+    return SV.State(x=x, v=(x - st_prev.x) / pad.h, pose=np.asarray(pose, np.float64))
+
+
+def _run_seq(pad, ind, poses, lags):
+    """Frames 1..F from rest; lags[f-1] is frame f's lag (None: its own)."""
+    states, used = [SV.rest_state(pad, poses[0])], []
+    for f in range(1, len(poses)):
+        lag = lags[f - 1] if lags is not None else AD.frame_of(pad, ind, states[-1], poses[f]).lag
+        used.append(lag)
+        states.append(_solve_lag(pad, ind, states[-1], poses[f], lag))
+    return states, used
+
+
+@pytest.fixture(scope="module")
+def seq_setup():
+    pad, ind, p0, p1, p2 = _scene()
+    p3 = p2 + np.array([0.01, 0.0, -0.01, 0.03 * MM, 0.01 * MM, -0.03 * MM])
+    poses = np.stack([p0, p1, p2, p3])
+    states, lags = _run_seq(pad, ind, poses, None)
+    assert lags[2]["lam"].size > 0                    # friction active in the last frames
+    rng = np.random.default_rng(2)
+    cs = [rng.normal(size=(pad.marker_ids.shape[0], 2)) for _ in range(3)]
+    return pad, ind, poses, states, lags, cs
+
+
+def _seq_loss(pad, states, cs):
+    return float(sum(np.sum(c * SV.markers(pad, s.x)) for c, s in zip(cs, states[1:])))
+
+
+def test_sequence_adjoint_matches_central_differences(seq_setup):
+    """Lame mu, friction and frame 1's end-pose z (which also sets frame 2's
+    start pose and, through frame 1's end state, frames 2 and 3) against
+    central differences of the 3-frame loss re-solved with the base lags.
+    Lame lambda enters the chain exactly as mu does."""
+    pad, ind, poses, states, lags, cs = seq_setup
+    got = AD.adjoint_sequence(pad, ind, states, cs, lags=lags)
+    checks = [("mu", 1), ("mu_f", 2), ("pose", 3 + 5)]
+    fd = {}
+    for attr, k in checks:
+        vals = []
+        if attr == "pose":
+            f, m = divmod(k - 3, 6)
+            h = 1e-6 if m < 3 else 1e-6 * abs(poses[f + 1][m])
+            for sgn in (1.0, -1.0):
+                q = poses.copy()
+                q[f + 1, m] += sgn * h
+                vals.append(_seq_loss(pad, _run_seq(pad, ind, q, lags)[0], cs))
+        else:
+            v0 = getattr(pad, attr)
+            h = 1e-6 * v0
+            for sgn in (1.0, -1.0):
+                pk = copy.copy(pad)
+                setattr(pk, attr, v0 + sgn * h)
+                vals.append(_seq_loss(pk, _run_seq(pk, ind, poses, lags)[0], cs))
+        fd[k] = (vals[0] - vals[1]) / (2 * h)
+    scale = max(abs(v) for v in fd.values())
+    for k, v in fd.items():
+        assert got[k] == pytest.approx(v, rel=1e-3, abs=1e-4 * scale), (k, got[k], v)
+
+
+def test_frame_adjoint_reduces_to_single_frame_form(seq_setup):
+    """With no downstream gradient, the first 9 entries are the single-frame
+    adjoint and dL/dv^t = h M lambda vanishes on Dirichlet vertices."""
+    pad, ind, poses, states, lags, cs = seq_setup
+    th, dx0, dv0 = AD.adjoint_frame(pad, ind, states[1], states[2], cs[1])
+    ref = AD.adjoint(pad, ind, states[1], states[2], cs[1])
+    assert np.allclose(th[:9], ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max())
+    assert np.all(dv0[~pad.free] == 0.0) and np.all(dx0[~pad.free] == 0.0)
