@@ -14,8 +14,9 @@ fixed. dg/dtheta:
     mu (F - F^-T) + lambda ln J F^-T), so dg/dlambda is the elastic gradient
     with (mu, lambda) = (0, 1) and dg/dmu the one with (1, 0);
   * mu_f: the lagged friction gradient is linear in mu_f;
-  * pose: central difference (step 1e-7) of the total gradient in each pose
-    component, the indenter vertices recomputed from the pose.
+  * pose: central difference (steps 1e-7 rad, 1e-10 m) of the total
+    gradient in each pose component, the indenter vertices recomputed from
+    the pose.
 
 ``adjoint_frame`` adds the sensitivities to the frame's start (positions,
 velocities, start pose) with the frame's friction lag held fixed, and
@@ -53,7 +54,17 @@ def frame_of(pad, ind, state_prev, pose_next, prm_margin=1.0, lag=None):
     return En.Frame(pad, ind, x_t, xhat, y_t, y_n, lag)
 
 
-def adjoint(pad, ind, state_prev, state_new, dL_dm, fd_pose=1e-7):
+# central-difference steps in the pose: rotation vector (rad) and translation
+# (m); a translation step must stay far below the contact gaps (~1e-6 m),
+# where the barrier gradient is strongly nonlinear
+FD_ROT, FD_TRANS = 1e-7, 1e-10
+
+
+def _fd_step(m, fd_pose):
+    return fd_pose if m < 3 else fd_pose * (FD_TRANS / FD_ROT)
+
+
+def adjoint(pad, ind, state_prev, state_new, dL_dm, fd_pose=FD_ROT):
     """dL/dtheta [9] = (lambda, mu, mu_f, rotvec(3), translation(3)) for the
     frame from state_prev to state_new (state_new.x the converged x*)."""
     fr = frame_of(pad, ind, state_prev, state_new.pose)
@@ -87,17 +98,18 @@ def adjoint(pad, ind, state_prev, state_new, dL_dm, fd_pose=1e-7):
     pose = np.asarray(state_new.pose, np.float64)
     for m in range(6):
         gs = []
+        hm = _fd_step(m, fd_pose)
         for sgn in (1.0, -1.0):
             q = pose.copy()
-            q[m] += sgn * fd_pose
+            q[m] += sgn * hm
             frq = En.Frame(pad, ind, fr.x_t, fr.xhat, fr.y_t, G.indenter_world(ind.verts, q), fr.lag)
             _, g, _ = En.total(frq, x, 1.0, pairs)
             gs.append(g)
-        out[3 + m] = -dot_free((gs[0] - gs[1]) / (2.0 * fd_pose))
+        out[3 + m] = -dot_free((gs[0] - gs[1]) / (2.0 * hm))
     return out
 
 
-def adjoint_frame(pad, ind, state_prev, state_new, dL_dm=None, dL_dx=None, lag=None, fd_pose=1e-7, fd_x=1e-9):
+def adjoint_frame(pad, ind, state_prev, state_new, dL_dm=None, dL_dx=None, lag=None, fd_pose=FD_ROT, fd_x=1e-10):
     """Adjoint of one frame of a sequence. The frame's friction lag (normal
     forces, contact normals, closest-point weights, from its start state) is
     a constant of the frame, as in the frame's solve.
@@ -149,18 +161,19 @@ def adjoint_frame(pad, ind, state_prev, state_new, dL_dm=None, dL_dx=None, lag=N
     pose_n = np.asarray(state_new.pose, np.float64)
     pose_t = np.asarray(state_prev.pose, np.float64)
     for m in range(6):
+        hm = _fd_step(m, fd_pose)
         gs = []
         for sgn in (1.0, -1.0):
             q = pose_n.copy()
-            q[m] += sgn * fd_pose
+            q[m] += sgn * hm
             gs.append(g_of(y_n=G.indenter_world(ind.verts, q)))
-        theta[3 + m] = -dot_free((gs[0] - gs[1]) / (2.0 * fd_pose))
+        theta[3 + m] = -dot_free((gs[0] - gs[1]) / (2.0 * hm))
         gs = []
         for sgn in (1.0, -1.0):
             q = pose_t.copy()
-            q[m] += sgn * fd_pose
+            q[m] += sgn * hm
             gs.append(g_of(y_t=G.indenter_world(ind.verts, q)))
-        theta[9 + m] = -dot_free((gs[0] - gs[1]) / (2.0 * fd_pose))
+        theta[9 + m] = -dot_free((gs[0] - gs[1]) / (2.0 * hm))
     dx0 = np.zeros_like(x)
     for i in np.nonzero(pad.free)[0]:
         for c in range(3):
