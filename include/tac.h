@@ -166,6 +166,31 @@ int tac_step(tac_handle h, int* pad_status_dev, int* iters_dev, void* stream);
 int tac_adjoint(tac_handle h, const float* dL_dmarkers_dev, double* dL_dtheta_dev, int* status_dev,
                 int* iters_dev, int max_iter, float tol, void* stream);
 
+/* Adjoint of the last frame for a reverse sweep over a sequence of frames
+ * (the multi-frame form of tac_adjoint; same method and stopping rule).
+ * Each frame's friction lag (normal forces, contact normals, closest-point
+ * weights, taken from the frame's start) is a constant of the frame, as it
+ * is in the frame's solve; the frame's start then enters g only through
+ * x-hat = x^t + h v^t (Eq. varopt) and the lagged friction displacement.
+ * dL_dmarkers_dev: device [total_markers*2] float or NULL, as in tac_adjoint.
+ * dL_dx_dev: device [total_verts*3] float or NULL, the loss gradient with
+ *   respect to the frame's end positions beyond the markers (from later
+ *   frames), in the caller vertex order of tac_get_state.
+ * dL_dtheta_dev: device [n_pads*15] double, per pad d L / d(Lame lambda,
+ *   Lame mu, mu_f, end pose rotation vector (3), end pose translation (3),
+ *   start pose rotation vector (3), start pose translation (3)).
+ * dL_dx0_dev, dL_dv0_dev: device [total_verts*3] float or NULL, caller
+ *   order: dL/dx^t = (M + H_D) lambda and dL/dv^t = h M lambda, H_D the
+ *   lagged friction Hessian; 0 on Dirichlet vertices.
+ * status_dev / iters_dev / max_iter / tol: as in tac_adjoint.
+ * A sweep over frames 1..F gives frame f's end state the gradient
+ *   (markers of frame f) + a_x + a_v / h with a_x, a_v from frame f+1, then
+ *   passes a_x = dL/dx^t - a_v / h and a_v = dL/dv^t to frame f-1 (since
+ *   v^f = (x^f - x^(f-1)) / h). Must follow the tac_step of the frame. */
+int tac_adjoint_frame(tac_handle h, const float* dL_dmarkers_dev, const float* dL_dx_dev, double* dL_dtheta_dev,
+                      float* dL_dx0_dev, float* dL_dv0_dev, int* status_dev, int* iters_dev, int max_iter, float tol,
+                      void* stream);
+
 /* Marker displacement field (u_x, u_y) per marker of every pad, in pad order:
  * out_dev: device [sum_p n_markers(p) * 2] float (Sec. 3.2). */
 int tac_markers(tac_handle h, float* out_dev, void* stream);

@@ -7,8 +7,12 @@ calls tac_adjoint, the implicit-function adjoint of the frame's equilibrium,
 for dL/d(lame, mu_f, pose). The barrier stiffness and the friction mollifier
 width are held at the values the batch resolved when the function was
 built; the pre-frame state (positions, velocities, start pose) is a
-constant of the frame, so a sequence of frames is differentiated frame by
-frame with each frame's own checkpoint.
+constant of the frame.
+
+TacStepFn / sequence_markers differentiate a sequence: each frame is a
+function of its start state as well, and its backward (tac_adjoint_frame)
+returns the start state's gradient, so torch chains the frames into a
+reverse sweep.
 """
 from __future__ import annotations
 
@@ -73,3 +77,83 @@ def frame_markers(batch, checkpoint, lame, mu_f, pose, base_params=None):
     if base_params is None:
         base_params = batch.get_params()
     return TacFrameFn.apply(lame, mu_f, pose, batch, checkpoint, base_params)
+
+
+def _set_material(batch, base_params, lame, mu_f):
+    prm = []
+    lam_mu = lame.detach().double().cpu().numpy()
+    muf = mu_f.detach().double().cpu().numpy()
+    for k, base in enumerate(base_params):
+        q = copy.copy(base)
+        E, nu = lame_to_young(lam_mu[k, 0], lam_mu[k, 1])
+        q.E, q.nu, q.mu_f = float(E), float(nu), float(muf[k])
+        prm.append(q)
+    batch.set_params(prm)
+
+
+def _vertex_h(batch, base_params):
+    """Per-vertex step size h [total_verts, 1] (caller vertex order)."""
+    h = torch.empty(batch.total_verts, 1, dtype=torch.float32, device=batch.device)
+    vo = batch.vert_offsets
+    for k, base in enumerate(base_params):
+        h[vo[k]:vo[k + 1]] = float(base.h)
+    return h
+
+
+class TacStepFn(torch.autograd.Function):
+    """One frame as a differentiable function of its start state:
+    (markers, x1, v1) = step(lame, mu_f, pose_start, pose_end, x0, v0).
+    Chaining calls differentiates a sequence of frames: backward re-solves
+    the frame from its saved start state (the batch holds one frame) and
+    calls tac_adjoint_frame with the end state's gradient (markers, x1 and
+    v1 = (x1 - x0) / h); the frame's friction lag is a constant of the
+    frame."""
+
+    @staticmethod
+    def _solve(batch, base_params, lame, mu_f, pose_s, pose_e, x0, v0):
+        _set_material(batch, base_params, lame, mu_f)
+        batch.reset(pose_s.detach().float().reshape(batch.n_pads, 6))
+        batch.set_state(x0.detach(), v0.detach())
+        batch.set_indenter(pose_e.detach().float().reshape(batch.n_pads, 6))
+        return batch.step()
+
+    @staticmethod
+    def forward(ctx, lame, mu_f, pose_s, pose_e, x0, v0, batch, base_params, adjoint_tol=1e-6):
+        status, _ = TacStepFn._solve(batch, base_params, lame, mu_f, pose_s, pose_e, x0, v0)
+        x1, v1 = batch.get_state()
+        m = batch.markers().clone()
+        ctx.batch, ctx.base, ctx.tol, ctx.status = batch, base_params, adjoint_tol, status
+        ctx.inputs = (lame.detach(), mu_f.detach(), pose_s.detach(), pose_e.detach(), x0.detach().clone(),
+                      v0.detach().clone())
+        ctx.like = (lame, mu_f, pose_s, pose_e, x0, v0)
+        return m, x1, v1
+
+    @staticmethod
+    def backward(ctx, gm, gx1, gv1):
+        b = ctx.batch
+        lame, mu_f, pose_s, pose_e, x0, v0 = ctx.inputs
+        TacStepFn._solve(b, ctx.base, lame, mu_f, pose_s, pose_e, x0, v0)
+        hv = _vertex_h(b, ctx.base)
+        zero = torch.zeros(b.total_verts, 3, dtype=torch.float32, device=b.device)
+        gx1 = zero if gx1 is None else gx1.to(device=b.device, dtype=torch.float32)
+        gv1 = zero if gv1 is None else gv1.to(device=b.device, dtype=torch.float32)
+        th, dx0, dv0, st, it = b.adjoint_frame(gm, gx1 + gv1 / hv, tol=ctx.tol)
+        gx0 = dx0 - gv1 / hv
+        l_, m_, ps_, pe_, x_, v_ = ctx.like
+        to = lambda t, ref: t.to(device=ref.device, dtype=ref.dtype).reshape(ref.shape)
+        return (to(th[:, 0:2], l_), to(th[:, 2], m_), to(th[:, 9:15], ps_), to(th[:, 3:9], pe_), to(gx0, x_),
+                to(dv0, v_), None, None, None)
+
+
+def sequence_markers(batch, x0, v0, lame, mu_f, poses, base_params=None, adjoint_tol=1e-6):
+    """Marker fields of frames 1..F [F, total_markers, 2] from the start
+    state (x0, v0) as a differentiable function of the Lame pair [n_pads, 2],
+    friction [n_pads] and the poses [F + 1, n_pads, 6] (poses[0] the start
+    pose of frame 1)."""
+    if base_params is None:
+        base_params = batch.get_params()
+    x, v, out = x0, v0, []
+    for f in range(1, poses.shape[0]):
+        m, x, v = TacStepFn.apply(lame, mu_f, poses[f - 1], poses[f], x, v, batch, base_params, adjoint_tol)
+        out.append(m)
+    return torch.stack(out)

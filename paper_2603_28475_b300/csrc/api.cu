@@ -20,8 +20,8 @@ __global__ void broadphase_kernel(const __grid_constant__ Dev D, int pad, const 
                                   int* count);
 __global__ void markers_kernel(const __grid_constant__ Dev D, float* out);
 __global__ void schedule_kernel(const __grid_constant__ Dev D, unsigned long long* key, int* idx, int n2, int* order);
-__global__ void adjoint_kernel(const __grid_constant__ Dev D, const float* dLdm, double* out, int* status, int* iters,
-                               int max_iter, float tol);
+__global__ void adjoint_kernel(const __grid_constant__ Dev D, const float* dLdm, const float* dLdx, double* out,
+                               int out_stride, float* dx0, float* dv0, int* status, int* iters, int max_iter, float tol);
 size_t shared_bytes();
 cudaError_t configure_kernels();
 void set_last_error(const std::string& msg);
@@ -177,6 +177,7 @@ struct tac_batch {
     int* d_u2i = nullptr;                   // caller vertex index -> state index
     float* d_hstep = nullptr;
     float* d_pose_t = nullptr;
+    float* d_pose_s = nullptr;              // start pose of the last tac_step
     float* d_pose_n = nullptr;
     int* d_order = nullptr;                 // processing order, rewritten before each solve
     unsigned long long* d_sched_key = nullptr;
@@ -371,6 +372,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     float* Yt = dalloc<float>(K, 3 * (size_t)yw, rc);
     float* Yn = dalloc<float>(K, 3 * (size_t)yw, rc);
     b->d_pose_t = dalloc<float>(K, 6 * (size_t)n_pads, rc);
+    b->d_pose_s = dalloc<float>(K, 6 * (size_t)n_pads, rc);
     b->d_pose_n = dalloc<float>(K, 6 * (size_t)n_pads, rc);
     float* st3[8];
     for (int k = 0; k < 8; ++k) st3[k] = dalloc<float>(K, 3 * (size_t)Vt, rc);
@@ -499,6 +501,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     CUDA_TRY(cudaMemsetAsync(norms, 0, 4 * (size_t)n_pads * 8, st));
     CUDA_TRY(cudaMemsetAsync(pad_nlag, 0, (size_t)n_pads * 4, st));
     CUDA_TRY(cudaMemsetAsync(b->d_pose_t, 0, 6 * (size_t)n_pads * 4, st));
+    CUDA_TRY(cudaMemsetAsync(b->d_pose_s, 0, 6 * (size_t)n_pads * 4, st));
     CUDA_TRY(cudaMemsetAsync(b->d_pose_n, 0, 6 * (size_t)n_pads * 4, st));
     D.meshes = b->d_meshes;
     D.envs = b->d_envs;
@@ -507,7 +510,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     D.X = X; D.vlump = vlump; D.wdiag = wdiag; D.fixed = fixed; D.vuser = vuser; D.B = B; D.lconn = lconn; D.slot = slot; D.colour = colour;
     D.pvert = pvert; D.pcsr = pcsr; D.sv = sv; D.st = stt; D.se = se;
     D.mk_ids = mk_ids; D.mk_w = mk_w; D.Y = Y; D.it = it; D.ie = ie; D.Yt = Yt; D.Yn = Yn;
-    D.pose_t = b->d_pose_t; D.pose_n = b->d_pose_n;
+    D.pose_t = b->d_pose_t; D.pose_n = b->d_pose_n; D.pose_s = b->d_pose_s;
     D.uh = st3[0]; D.ul = st3[1]; D.u0h = st3[2]; D.u0l = st3[3]; D.vel = st3[4]; D.uhat = st3[5];
     D.p = st3[6]; D.z = st3[7];
     D.g[0] = g0; D.g[1] = g1; D.blk[0] = k0; D.blk[1] = k1;
@@ -543,6 +546,7 @@ int tac_reset(tac_handle h, const float* pose6_dev, void* stream) {
     CUDA_TRY(cudaMemsetAsync(h->dev.vel, 0, n3, st));
     CUDA_TRY(cudaMemcpyAsync(h->d_pose_t, pose6_dev, 6 * (size_t)h->n_pads * 4, cudaMemcpyDeviceToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(h->d_pose_n, pose6_dev, 6 * (size_t)h->n_pads * 4, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(h->d_pose_s, pose6_dev, 6 * (size_t)h->n_pads * 4, cudaMemcpyDeviceToDevice, st));
     return TAC_OK;
 }
 
@@ -566,6 +570,7 @@ int tac_step(tac_handle h, int* pad_status_dev, int* iters_dev, void* stream) {
     D.status = pad_status_dev;
     D.iters = iters_dev;
     CUDA_TRY(cudaMemsetAsync(D.queue, 0, sizeof(int), st));
+    CUDA_TRY(cudaMemcpyAsync(h->d_pose_s, h->d_pose_t, 6 * (size_t)h->n_pads * 4, cudaMemcpyDeviceToDevice, st));
     // longest predicted pad first (its previous solve time, then its size)
     schedule_kernel<<<1, 1024, 0, st>>>(D, h->d_sched_key, h->d_sched_idx, h->sched_n2, h->d_order);
     CUDA_TRY(cudaGetLastError());
@@ -665,7 +670,19 @@ int tac_adjoint(tac_handle h, const float* dL_dmarkers_dev, double* dL_dtheta_de
     if (!h || !dL_dmarkers_dev || !dL_dtheta_dev || max_iter < 0 || !(tol > 0))
         return fail(TAC_ERR_INVALID_ARG, "invalid argument");
     adjoint_kernel<<<h->n_pads, kThreads, shared_bytes(), static_cast<cudaStream_t>(stream)>>>(
-        h->dev, dL_dmarkers_dev, dL_dtheta_dev, status_dev, iters_dev, max_iter, tol);
+        h->dev, dL_dmarkers_dev, nullptr, dL_dtheta_dev, 9, nullptr, nullptr, status_dev, iters_dev, max_iter, tol);
+    CUDA_TRY(cudaGetLastError());
+    return TAC_OK;
+}
+
+int tac_adjoint_frame(tac_handle h, const float* dL_dmarkers_dev, const float* dL_dx_dev, double* dL_dtheta_dev,
+                      float* dL_dx0_dev, float* dL_dv0_dev, int* status_dev, int* iters_dev, int max_iter, float tol,
+                      void* stream) {
+    if (!h || !dL_dtheta_dev || max_iter < 0 || !(tol > 0))
+        return fail(TAC_ERR_INVALID_ARG, "invalid argument");
+    adjoint_kernel<<<h->n_pads, kThreads, shared_bytes(), static_cast<cudaStream_t>(stream)>>>(
+        h->dev, dL_dmarkers_dev, dL_dx_dev, dL_dtheta_dev, 15, dL_dx0_dev, dL_dv0_dev, status_dev, iters_dev,
+        max_iter, tol);
     CUDA_TRY(cudaGetLastError());
     return TAC_OK;
 }

@@ -2038,8 +2038,10 @@ __global__ void markers_kernel(const __grid_constant__ Dev D, float* out) {
 
 // exact Hessian action of the barrier and lagged friction on the direction
 // in p, written as slot values (3 force components, zero blocks)
+// Hessian-vector product of the contact terms with p, into the slot buffer:
+// the barrier part (when barrier is set) and the lagged friction part
 __device__ __noinline__ void pair_hvp(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np, int nl,
-                                      double s) {
+                                      double s, bool barrier = true) {
     const int4* pr = D.pairs + P.pair_off;
     float* sb = D.slotbuf + (size_t)9 * 6 * P.pair_off;
     const double dh = P.dhat, kap = P.kappa;
@@ -2050,7 +2052,7 @@ __device__ __noinline__ void pair_hvp(const Dev& D, const PadDev& P, const MeshD
         float out[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
         V3<float> Xf[4];
         load_slots<float>(D, P, M, gsl, isl, 0.0f, s, Xf);
-        if ((double)pair_feature<float>(q.x, Xf).d <= 2.0 * dh) {
+        if (barrier && (double)pair_feature<float>(q.x, Xf).d <= 2.0 * dh) {
             V3<double> X[4], dl[4];
             load_slots<double>(D, P, M, gsl, isl, 0.0f, s, X);
             Feature<double> f = pair_feature<double>(q.x, X);
@@ -2161,10 +2163,12 @@ __device__ void rotation_jacobian(const float* pose, double dR[3][9]) {
 
 // lambda (in p) against dg/dtheta of the contact terms: out[0] the friction
 // coefficient, out[1..6] the end pose (rotation vector, translation) through
-// the mixed gel / indenter second derivatives
+// the mixed gel / indenter second derivatives, out[7..12] the start pose
+// (dRs its rotation Jacobian), which enters only the lagged friction term,
+// through the indenter's displacement over the frame
 __device__ __noinline__ void pair_theta(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np,
-                                        int nl, const double dR[3][9], double out7[7]) {
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+                                        int nl, const double dR[3][9], const double dRs[3][9], double out13[13]) {
+    double acc[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     const int4* pr = D.pairs + P.pair_off;
     const double dh = P.dhat, kap = P.kappa;
     auto dy_of = [&](int j, int m) -> V3<double> {
@@ -2177,6 +2181,13 @@ __device__ __noinline__ void pair_theta(const Dev& D, const PadDev& P, const Mes
         }
         const float* y = D.Y + 3 * (E.y_off + j);
         const double* A = dR[m];
+        return V3<double>{A[0] * y[0] + A[1] * y[1] + A[2] * y[2], A[3] * y[0] + A[4] * y[1] + A[5] * y[2],
+                          A[6] * y[0] + A[7] * y[1] + A[8] * y[2]};
+    };
+    auto dys_of = [&](int j, int m) -> V3<double> {
+        if (m >= 3) return dy_of(j, m);
+        const float* y = D.Y + 3 * (E.y_off + j);
+        const double* A = dRs[m];
         return V3<double>{A[0] * y[0] + A[1] * y[1] + A[2] * y[2], A[3] * y[0] + A[4] * y[1] + A[5] * y[2],
                           A[6] * y[0] + A[7] * y[1] + A[8] * y[2]};
     };
@@ -2255,11 +2266,30 @@ __device__ __noinline__ void pair_theta(const Dev& D, const PadDev& P, const Mes
 #pragma unroll
                 for (int c = 0; c < 3; ++c) Ha += pd[c] * (f1s * (a[c] - L.n[c] * na) - cs * uu[c] * ua);
                 acc[1 + m] -= cf * Ha;
+                // start pose: the displacement depends on -y^t, so the sign flips
+                V3<double> ds = {0, 0, 0};
+                for (int q = 0; q < 3; ++q)
+                    if (L.iv[q] >= 0) ds = ds + (double)L.iw[q] * dys_of(L.iv[q], m);
+                double b[3] = {ds.x, ds.y, ds.z};
+                double nb = L.n[0] * b[0] + L.n[1] * b[1] + L.n[2] * b[2];
+                double ub = uu[0] * b[0] + uu[1] * b[1] + uu[2] * b[2];
+                double Hb = 0.0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Hb += pd[c] * (f1s * (b[c] - L.n[c] * nb) - cs * uu[c] * ub);
+                acc[7 + m] += cf * Hb;
             }
         }
-    block_sum<7>(acc);
+    double first[8], rest[5];
 #pragma unroll
-    for (int q = 0; q < 7; ++q) out7[q] = acc[q];
+    for (int q = 0; q < 8; ++q) first[q] = acc[q];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) rest[q] = acc[8 + q];
+    block_sum<8>(first);
+    block_sum<5>(rest);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) out13[q] = first[q];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) out13[8 + q] = rest[q];
 }
 
 // z = P r with P the block-Jacobi inverse of (blk[gp] + m I); returns r.z, r.r
@@ -2343,9 +2373,16 @@ __device__ __noinline__ void pcg_vectors(const Dev& D, const PadDev& P, const Me
 
 enum { ADJ_CONVERGED = 0, ADJ_MAXITER = 1, ADJ_BREAKDOWN = 2, ADJ_NONFINITE = 3 };
 
+// Adjoint of the last frame. dLdm (markers) and dLdx (caller-order end
+// positions) form the right-hand side, either may be null. out: per pad
+// out_stride doubles (9: Lame pair, mu_f, end pose; 15: plus the start pose).
+// dx0 / dv0 (caller order, may be null): dL/dx^t = (M + H_D) lambda and
+// dL/dv^t = h M lambda with the frame's friction lag held fixed (H_D the
+// lagged friction Hessian).
 __global__ void __launch_bounds__(kThreads, 2) adjoint_kernel(const __grid_constant__ Dev D, const float* dLdm,
-                                                              double* out, int* status, int* iters, int max_iter,
-                                                              float tol) {
+                                                              const float* dLdx, double* out, int out_stride,
+                                                              float* dx0, float* dv0, int* status, int* iters,
+                                                              int max_iter, float tol) {
     const int pad = blockIdx.x;
     load_pad(D, pad);
     const PadDev& P = S.P;
@@ -2373,7 +2410,16 @@ __global__ void __launch_bounds__(kThreads, 2) adjoint_kernel(const __grid_const
             D.adj_x[c * D.Vt + P.v_off + i] = 0.f;
         }
     __syncthreads();
-    if (threadIdx.x == 0)
+    if (dLdx) {
+        for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
+            if (D.fixed[M.xv_off + i]) continue;
+            const size_t u = (size_t)P.v_off + D.vuser[M.xv_off + i];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) D.adj_r[c * D.Vt + P.v_off + i] = dLdx[3 * u + c];
+        }
+        __syncthreads();
+    }
+    if (dLdm && threadIdx.x == 0)
         for (int m = 0; m < M.n_mk; ++m)
             for (int k = 0; k < 3; ++k) {
                 int v = D.mk_ids[3 * (M.mk_off + m) + k];
@@ -2413,17 +2459,42 @@ __global__ void __launch_bounds__(kThreads, 2) adjoint_kernel(const __grid_const
         for (int c = 0; c < 3; ++c) D.p[c * D.Vt + P.v_off + i] = D.adj_x[c * D.Vt + P.v_off + i];
     __syncthreads();
     TetOut t3 = tet_pass<3>(D, P, M, 0.0f, 0);
-    double dR[3][9];
+    double dR[3][9], dRs[3][9];
     rotation_jacobian(D.pose_t + 6 * pad, dR);
-    double c7[7];
-    pair_theta(D, P, M, E, cc.npairs, cc.nlag, dR, c7);
+    rotation_jacobian(D.pose_s + 6 * pad, dRs);
+    double c13[13];
+    pair_theta(D, P, M, E, cc.npairs, cc.nlag, dR, dRs, c13);
     if (threadIdx.x == 0) {
-        double* o = out + 9 * pad;
+        double* o = out + (size_t)out_stride * pad;
         o[0] = -t3.acc;
         o[1] = -t3.acc2;
-        for (int q = 0; q < 7; ++q) o[2 + q] = -c7[q];
+        for (int q = 0; q < 7; ++q) o[2 + q] = -c13[q];
+        if (out_stride >= 15)
+            for (int q = 0; q < 6; ++q) o[9 + q] = -c13[7 + q];
         if (status) status[pad] = st;
         if (iters) iters[pad] = it;
+    }
+    if (dx0 || dv0) {
+        // H_D lambda: the lagged friction part of the Hessian-vector product
+        // (p holds lambda), gathered into g[1]
+        for (int i = threadIdx.x; i < M.n_v; i += kThreads)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) D.g[1][c * D.Vt + P.v_off + i] = 0.f;
+        __syncthreads();
+        pair_hvp(D, P, M, E, cc.npairs, cc.nlag, 1.0, false);
+        contact_gather(D, P, cc, 1);
+        for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
+            const size_t si = (size_t)P.v_off + i;
+            const size_t u = (size_t)P.v_off + D.vuser[M.xv_off + i];
+            const bool fx = D.fixed[M.xv_off + i] != 0;
+            const float m = P.rho * D.vlump[M.xv_off + i];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float l = D.adj_x[c * D.Vt + si];
+                if (dx0) dx0[3 * u + c] = fx ? 0.f : m * l + D.g[1][c * D.Vt + si];
+                if (dv0) dv0[3 * u + c] = fx ? 0.f : P.h * m * l;
+            }
+        }
     }
 }
 

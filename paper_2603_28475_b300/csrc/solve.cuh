@@ -90,6 +90,7 @@ struct Dev {
     float* Yn;                // [n*3] world at the frame end
     const float* pose_t;      // [n_pads*6]
     const float* pose_n;      // [n_pads*6]
+    const float* pose_s;      // [n_pads*6] start pose of the last solved frame
     // state [c][Vt]
     float *uh, *ul, *u0h, *u0l, *vel, *uhat, *p, *z;
     float* g[2];              // [3][Vt]

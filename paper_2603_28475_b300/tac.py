@@ -19,7 +19,7 @@ TAC_OK = 0
 PAD_STATUS = {0: "converged", 1: "maxiter", 2: "nonfinite", 3: "linesearch", 4: "pair_overflow"}
 
 SYMBOLS = ("tac_create_batch", "tac_destroy_batch", "tac_reset", "tac_set_indenter", "tac_step", "tac_markers",
-           "tac_adjoint",
+           "tac_adjoint", "tac_adjoint_frame",
            "tac_get_state", "tac_set_state", "tac_set_params", "tac_get_params", "tac_broadphase",
            "tac_broadphase_static",
            "tac_debug_eval", "tac_stats",
@@ -63,6 +63,7 @@ def load_library(path=_LIB_PATH):
         "tac_step": [vp, vp, vp, vp],
         "tac_markers": [vp, vp, vp],
         "tac_adjoint": [vp, vp, vp, vp, vp, i, f, vp],
+        "tac_adjoint_frame": [vp, vp, vp, vp, vp, vp, vp, vp, i, f, vp],
         "tac_get_state": [vp, vp, vp, vp],
         "tac_set_state": [vp, vp, vp, vp],
         "tac_set_params": [vp, ctypes.POINTER(Params), i],
@@ -225,6 +226,27 @@ class TacBatch:
                                  _stream(stream)))
         self._hold = g
         return out, st, it
+
+    def adjoint_frame(self, dL_dmarkers=None, dL_dx=None, max_iter=4000, tol=1e-6, stream=None):
+        """Adjoint of the last frame for a reverse sweep (tac_adjoint_frame):
+        returns dL/dtheta [n_pads, 15] (Lame lambda, Lame mu, mu_f, end pose
+        rotation vector and translation, start pose rotation vector and
+        translation), dL/dx^t and dL/dv^t [total_verts, 3] (caller order),
+        and the PCG status and iterations per pad. dL_dmarkers [total_markers,
+        2] and dL_dx [total_verts, 3] (gradient of the end positions beyond
+        the markers) may be None."""
+        gm = None if dL_dmarkers is None else self._f32(dL_dmarkers).reshape(self.total_markers, 2)
+        gx = None if dL_dx is None else self._f32(dL_dx).reshape(self.total_verts, 3)
+        out = torch.empty(self.n_pads, 15, dtype=torch.float64, device=self.device)
+        dx0 = torch.empty(self.total_verts, 3, dtype=torch.float32, device=self.device)
+        dv0 = torch.empty_like(dx0)
+        st = torch.empty(self.n_pads, dtype=torch.int32, device=self.device)
+        it = torch.empty(self.n_pads, dtype=torch.int32, device=self.device)
+        _check(lib().tac_adjoint_frame(self._h, None if gm is None else _ptr(gm), None if gx is None else _ptr(gx),
+                                       _ptr(out), _ptr(dx0), _ptr(dv0), _ptr(st), _ptr(it), int(max_iter),
+                                       float(tol), _stream(stream)))
+        self._hold = (gm, gx)
+        return out, dx0, dv0, st, it
 
     def get_state(self, stream=None):
         x = torch.empty(self.total_verts, 3, dtype=torch.float32, device=self.device)

@@ -117,3 +117,85 @@ def test_autograd_function_gives_the_adjoint(tac, oracle_ref):
     # the marker field of the forward pass is the frame's solution
     assert np.abs(m.detach().cpu().numpy() - SV.markers(pad, s2.x)).max() <= 1e-4 * 2 * MM
     b.close()
+
+
+# --- sequences: tac_adjoint_frame and the differentiable step
+
+def _p3(poses):
+    return poses[2] + np.array([0.01, 0.0, -0.01, 0.03 * MM, 0.01 * MM, -0.03 * MM], np.float32)
+
+
+@pytest.fixture(scope="module")
+def oracle_seq():
+    pd, mat, ind_s, poses = _scene()
+    poses = np.concatenate([poses, _p3(poses)[None]]).astype(np.float32)
+    pad = oracle_pad(pd, mat)
+    ind = G.build_indenter(ind_s.verts, ind_s.tris)
+    P = poses.astype(np.float64)
+    states = [SV.rest_state(pad, P[0])]
+    for f in (1, 2, 3):
+        states.append(_oracle_solve(pad, ind, states[-1], P[f]))
+    rng = np.random.default_rng(3)
+    cs = [rng.normal(size=(pd.markers.shape[0], 2)) for _ in range(3)]
+    gx = rng.normal(size=pad.rest.shape) * 1e-3
+    gx[~pad.free] = 0.0
+    return pad, ind, poses, states, cs, gx
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def test_frame_adjoint_matches_oracle(tac, oracle_seq):
+    """Frame 3 with a downstream gradient on its end positions: all 15
+    parameter sensitivities and the start-state gradients."""
+    pad, ind, poses, states, cs, gx = oracle_seq
+    th_o, dx_o, dv_o = AD.adjoint_frame(pad, ind, states[2], states[3], cs[2], gx)
+    pd, mat, ind_s, _ = _scene()
+    w = S.Workload("adjoint", [pd], [mat], [ind_s], 1, poses[:, None, :])
+    b = tac.batch_from_workload(w, tol=TIGHT)
+    b.reset(torch.tensor(poses[0]).reshape(1, 6))
+    for f in (1, 2, 3):
+        b.set_indenter(torch.tensor(poses[f]).reshape(1, 6))
+        st, _ = b.step()
+        assert int(st.item()) == 0
+    th, dx0, dv0, st, it = b.adjoint_frame(torch.tensor(cs[2], dtype=torch.float32),
+                                           torch.tensor(gx, dtype=torch.float32))
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    got = th.cpu().numpy()[0]
+    scale = np.abs(th_o).max()
+    for k in range(15):
+        assert got[k] == pytest.approx(th_o[k], rel=1e-3, abs=1e-4 * scale), (k, got, th_o)
+    assert _rel(dx0.cpu().numpy().astype(np.float64), dx_o) <= 1e-3
+    assert _rel(dv0.cpu().numpy().astype(np.float64), dv_o) <= 1e-3
+    # without a downstream gradient the first 9 entries are tac_adjoint's
+    th2, _, _, _, _ = b.adjoint_frame(torch.tensor(cs[2], dtype=torch.float32))
+    g9, _, _ = b.adjoint(torch.tensor(cs[2], dtype=torch.float32))
+    assert np.allclose(th2.cpu().numpy()[0, :9], g9.cpu().numpy()[0], rtol=1e-6,
+                       atol=1e-9 * np.abs(g9.cpu().numpy()).max())
+    b.close()
+
+
+def test_sequence_autograd_matches_oracle_sweep(tac, oracle_seq):
+    """Three frames chained with TacStepFn; loss.backward() against the
+    oracle's reverse sweep (Lame pair, friction, end poses of frames 1-3)."""
+    from paper_2603_28475_b300 import autograd as A
+    pad, ind, poses, states, cs, gx = oracle_seq
+    ref = AD.adjoint_sequence(pad, ind, states, cs)
+    pd, mat, ind_s, _ = _scene()
+    w = S.Workload("adjoint", [pd], [mat], [ind_s], 1, poses[:, None, :])
+    b = tac.batch_from_workload(w, tol=TIGHT)
+    b.reset(torch.tensor(poses[0]).reshape(1, 6))
+    x0, v0 = b.get_state()
+    lame = torch.tensor([[pad.lam, pad.mu]], dtype=torch.float64, requires_grad=True)
+    mu_f = torch.tensor([pad.mu_f], dtype=torch.float64, requires_grad=True)
+    P = torch.tensor(poses.astype(np.float64).reshape(4, 1, 6), requires_grad=True)
+    m = A.sequence_markers(b, x0, v0, lame, mu_f, P)
+    loss = sum((torch.tensor(c, dtype=torch.float32, device=m.device) * m[f]).sum() for f, c in enumerate(cs))
+    loss.backward()
+    got = np.concatenate([lame.grad.numpy()[0], mu_f.grad.numpy(), P.grad.numpy()[1:, 0].ravel()])
+    scale = np.abs(ref).max()
+    for k in range(ref.size):
+        assert got[k] == pytest.approx(ref[k], rel=2e-3, abs=2e-4 * scale), (k, got, ref)
+    b.close()
