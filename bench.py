@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time the calibration workload's 16-frame forward and reverse sweep instead")
+    ap.add_argument("--adjoint-envs", type=int, default=256)
+    ap.add_argument("--adjoint-frames", type=int, default=16)
     return ap.parse_args()
 
 
@@ -363,10 +367,79 @@ def run_ours(args, rank, world):
     b.close()
 
 
+def run_adjoint(args):
+    """Calibration workload (256 envs x one 5k-class pad, 16-frame
+    press-and-slide): targets are the marker fields at hidden per-env
+    materials; the loss is the L2 misfit at the nominal material; one step is
+    the forward sequence through TacStepFn plus loss.backward() (the reverse
+    sweep, which re-solves each frame from its checkpoint and runs
+    tac_adjoint_frame). Prints one JSON line (ms per frame)."""
+    import copy
+    import torch
+    from paper_2603_28475_b300 import autograd as A
+    from paper_2603_28475_b300 import scenes as S
+    from paper_2603_28475_b300 import tac
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w, hidden = S.config_calibration(n_envs=args.adjoint_envs, frames=args.adjoint_frames, seed=args.seed)
+    b = tac.batch_from_workload(w, pair_capacity=args.pair_capacity)
+    base = b.get_params()
+    poses = torch.tensor(w.poses.astype(np.float64), device=dev)
+    F = w.n_frames
+    # targets: forward at the hidden materials
+    hp = []
+    for k, q in enumerate(base):
+        r = copy.copy(q)
+        r.E, r.nu, r.mu_f = hidden[k].E, hidden[k].nu, hidden[k].mu_f
+        hp.append(r)
+    b.set_params(hp)
+    b.reset(poses[0].float())
+    targets = []
+    for f in range(1, F + 1):
+        b.set_indenter(poses[f].float())
+        b.step()
+        targets.append(b.markers().clone())
+    targets = torch.stack(targets)
+    b.set_params(base)
+    b.reset(poses[0].float())
+    x0, v0 = b.get_state()
+    lam = np.array([q.E * q.nu / ((1 + q.nu) * (1 - 2 * q.nu)) for q in base])
+    mu = np.array([q.E / (2 * (1 + q.nu)) for q in base])
+    lame = torch.tensor(np.stack([lam, mu], 1), dtype=torch.float64, requires_grad=True)
+    mu_f = torch.tensor([q.mu_f for q in base], dtype=torch.float64, requires_grad=True)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    m = A.sequence_markers(b, x0, v0, lame, mu_f, poses, base_params=base)
+    loss = ((m - targets) ** 2).sum()
+    ev[1].record(stream)
+    loss.backward()
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    fwd, bwd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    out = {"metric": "adjoint calibration step: 16-frame forward + reverse sweep (calibration workload)",
+           "value": (fwd + bwd) / F, "unit": "ms/frame", "higher_is_better": False, "n_gpus": 1,
+           "forward_ms_per_frame": fwd / F, "backward_ms_per_frame": bwd / F,
+           "note": "backward re-solves each frame from its checkpoint, then runs the frame adjoint",
+           "dtype": "f32 (double-float displacements; f64 pair distance, barrier, CCD and reductions)",
+           "data": "synthetic",
+           "config": {"workload": w.name, "envs": w.n_envs, "pads": w.n_pads, "pad_verts": w.pads[0].n_verts,
+                      "frames": F, "friction": 0.5, "targets": "GPU forward at hidden per-env (E, nu, mu_f)"},
+           "loss": float(loss.item()), "grad_norm_lame": float(lame.grad.norm().item()),
+           "grad_norm_mu_f": float(mu_f.grad.norm().item())}
+    print(json.dumps(out), flush=True)
+    b.close()
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.adjoint:
+        if rank == 0:
+            run_adjoint(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

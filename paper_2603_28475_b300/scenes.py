@@ -495,3 +495,46 @@ def config_batched(n_envs=4096, frames=12, seed=0, step=0.05 * MM, classes=(2000
             poses[:, i, 4] = cy
             poses[:, i, 5] = z0 - np.minimum(step * np.arange(frames + 1), depth + DHAT)
     return Workload(f"batched_{n_envs}env_x2pads", pads, mats, inds, 2, poses.astype(np.float32))
+
+
+def config_calibration(n_envs=256, frames=16, seed=0, step=0.05 * MM, mu_f=0.5):
+    """Adjoint calibration workload: ``n_envs`` environments of one
+    5k-vertex-class pad and a cylinder peg (r ~ U[2, 4] mm, rotation vector
+    components ~ U(+-15 deg), xy offset ~ U(+-1 mm)). Each runs a
+    press-and-slide sequence: ``frames // 2`` frames pressing ``step`` per
+    frame from a d-hat gap, then ``frames - frames // 2`` frames sliding
+    ``step`` per frame along a random in-plane direction at constant depth.
+    Returns (workload at the nominal material, hidden per-env materials with
+    E ~ U[0.1, 0.5] MPa, nu ~ U[0.40, 0.49], mu_f ~ U[0.3, 0.9])."""
+    rng = np.random.default_rng(np.random.PCG64(20260 + 4000 + seed))
+    pads, mats, inds, hidden = [], [], [], []
+    poses = np.zeros((frames + 1, n_envs, 6))
+    cyl_cache = {}
+    n_press = frames // 2
+    for e in range(n_envs):
+        r = float(rng.uniform(2 * MM, 4 * MM))
+        key = round(r / (0.05 * MM))
+        if key not in cyl_cache:
+            cyl_cache[key] = cylinder(key * 0.05 * MM, 24 * MM, 64, 8)
+        ind = cyl_cache[key]
+        pad = size_class_pad(5000)
+        pads.append(pad)
+        mats.append(Material(mu_f=mu_f))
+        inds.append(ind)
+        hidden.append(Material(E=float(rng.uniform(0.1e6, 0.5e6)), nu=float(rng.uniform(0.40, 0.49)),
+                               mu_f=float(rng.uniform(0.3, 0.9))))
+        rot = np.deg2rad(rng.uniform(-15, 15, size=3))
+        off = rng.uniform(-1 * MM, 1 * MM, size=2)
+        ang = float(rng.uniform(0, 2 * np.pi))
+        lx, ly, lz = pad.size
+        cx, cy = lx / 2 + off[0], ly / 2 + off[1]
+        z0 = place_above_box(ind.verts, rot, (cx, cy), pad.size, DHAT, ind.tris)
+        k = np.arange(frames + 1)
+        press = step * np.minimum(k, n_press)
+        slide = step * np.maximum(k - n_press, 0)
+        poses[:, e, :3] = rot
+        poses[:, e, 3] = cx + np.cos(ang) * slide
+        poses[:, e, 4] = cy + np.sin(ang) * slide
+        poses[:, e, 5] = z0 - press
+    w = Workload(f"calibration_{n_envs}env", pads, mats, inds, 1, poses.astype(np.float32))
+    return w, hidden
