@@ -421,7 +421,8 @@ def run_adjoint(args):
     out = {"metric": "adjoint calibration step: 16-frame forward + reverse sweep (calibration workload)",
            "value": (fwd + bwd) / F, "unit": "ms/frame", "higher_is_better": False, "n_gpus": 1,
            "forward_ms_per_frame": fwd / F, "backward_ms_per_frame": bwd / F,
-           "note": "backward re-solves each frame from its checkpoint, then runs the frame adjoint",
+           "note": "backward installs each frame from its saved start and end states (tac_set_frame, no re-solve), "
+                   "then runs the frame adjoint",
            "dtype": "f32 (double-float displacements; f64 pair distance, barrier, CCD and reductions)",
            "data": "synthetic",
            "config": {"workload": w.name, "envs": w.n_envs, "pads": w.n_pads, "pad_verts": w.pads[0].n_verts,

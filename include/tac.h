@@ -191,6 +191,20 @@ int tac_adjoint_frame(tac_handle h, const float* dL_dmarkers_dev, const float* d
                       float* dL_dx0_dev, float* dL_dv0_dev, int* status_dev, int* iters_dev, int max_iter, float tol,
                       void* stream);
 
+/* Install a frame that was solved before (by a tac_step from the start
+ * state x0, v0 at pose_start to pose_end, ending at x1) so that tac_adjoint
+ * or tac_adjoint_frame can differentiate it without solving it again, as a
+ * reverse sweep over saved frames needs. The frame's friction lag is
+ * rebuilt from the start state and pose by the steps of tac_step's frame
+ * setup, so it equals the lag of the original solve when that solve started
+ * from this state (a tac_set_state of x0, v0 after a tac_reset at
+ * pose_start). The batch is left at the end state: positions x1, velocities
+ * (x1 - x0) / h, current pose pose_end.
+ * x0_dev, v0_dev, x1_dev: device [total_verts*3] float, caller vertex order;
+ * pose_start_dev, pose_end_dev: device [n_pads*6] float. */
+int tac_set_frame(tac_handle h, const float* x0_dev, const float* v0_dev, const float* pose_start_dev,
+                  const float* x1_dev, const float* pose_end_dev, void* stream);
+
 /* Marker displacement field (u_x, u_y) per marker of every pad, in pad order:
  * out_dev: device [sum_p n_markers(p) * 2] float (Sec. 3.2). */
 int tac_markers(tac_handle h, float* out_dev, void* stream);

@@ -103,11 +103,12 @@ def _vertex_h(batch, base_params):
 class TacStepFn(torch.autograd.Function):
     """One frame as a differentiable function of its start state:
     (markers, x1, v1) = step(lame, mu_f, pose_start, pose_end, x0, v0).
-    Chaining calls differentiates a sequence of frames: backward re-solves
-    the frame from its saved start state (the batch holds one frame) and
-    calls tac_adjoint_frame with the end state's gradient (markers, x1 and
-    v1 = (x1 - x0) / h); the frame's friction lag is a constant of the
-    frame."""
+    Chaining calls differentiates a sequence of frames: backward installs
+    the frame from its saved start and end states (tac_set_frame, which
+    rebuilds the frame's friction lag without solving; the batch holds one
+    frame) and calls tac_adjoint_frame with the end state's gradient
+    (markers, x1 and v1 = (x1 - x0) / h); the frame's friction lag is a
+    constant of the frame."""
 
     @staticmethod
     def _solve(batch, base_params, lame, mu_f, pose_s, pose_e, x0, v0):
@@ -124,15 +125,16 @@ class TacStepFn(torch.autograd.Function):
         m = batch.markers().clone()
         ctx.batch, ctx.base, ctx.tol, ctx.status = batch, base_params, adjoint_tol, status
         ctx.inputs = (lame.detach(), mu_f.detach(), pose_s.detach(), pose_e.detach(), x0.detach().clone(),
-                      v0.detach().clone())
+                      v0.detach().clone(), x1.clone())
         ctx.like = (lame, mu_f, pose_s, pose_e, x0, v0)
         return m, x1, v1
 
     @staticmethod
     def backward(ctx, gm, gx1, gv1):
         b = ctx.batch
-        lame, mu_f, pose_s, pose_e, x0, v0 = ctx.inputs
-        TacStepFn._solve(b, ctx.base, lame, mu_f, pose_s, pose_e, x0, v0)
+        lame, mu_f, pose_s, pose_e, x0, v0, x1 = ctx.inputs
+        _set_material(b, ctx.base, lame, mu_f)
+        b.set_frame(x0, v0, pose_s.detach().float(), x1, pose_e.detach().float())
         hv = _vertex_h(b, ctx.base)
         zero = torch.zeros(b.total_verts, 3, dtype=torch.float32, device=b.device)
         gx1 = zero if gx1 is None else gx1.to(device=b.device, dtype=torch.float32)

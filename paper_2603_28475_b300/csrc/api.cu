@@ -20,6 +20,7 @@ __global__ void broadphase_kernel(const __grid_constant__ Dev D, int pad, const 
                                   int* count);
 __global__ void markers_kernel(const __grid_constant__ Dev D, float* out);
 __global__ void schedule_kernel(const __grid_constant__ Dev D, unsigned long long* key, int* idx, int n2, int* order);
+__global__ void frame_install_kernel(const __grid_constant__ Dev D, const float* x0, const float* v0, const float* x1);
 __global__ void adjoint_kernel(const __grid_constant__ Dev D, const float* dLdm, const float* dLdx, double* out,
                                int out_stride, float* dx0, float* dv0, int* status, int* iters, int max_iter, float tol);
 size_t shared_bytes();
@@ -672,6 +673,21 @@ int tac_adjoint(tac_handle h, const float* dL_dmarkers_dev, double* dL_dtheta_de
     adjoint_kernel<<<h->n_pads, kThreads, shared_bytes(), static_cast<cudaStream_t>(stream)>>>(
         h->dev, dL_dmarkers_dev, nullptr, dL_dtheta_dev, 9, nullptr, nullptr, status_dev, iters_dev, max_iter, tol);
     CUDA_TRY(cudaGetLastError());
+    return TAC_OK;
+}
+
+int tac_set_frame(tac_handle h, const float* x0_dev, const float* v0_dev, const float* pose_start_dev,
+                  const float* x1_dev, const float* pose_end_dev, void* stream) {
+    if (!h || !x0_dev || !v0_dev || !pose_start_dev || !x1_dev || !pose_end_dev)
+        return fail(TAC_ERR_INVALID_ARG, "null argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t pb = 6 * (size_t)h->n_pads * 4;
+    CUDA_TRY(cudaMemcpyAsync(h->d_pose_t, pose_start_dev, pb, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(h->d_pose_n, pose_end_dev, pb, cudaMemcpyDeviceToDevice, st));
+    frame_install_kernel<<<h->n_pads, kThreads, shared_bytes(), st>>>(h->dev, x0_dev, v0_dev, x1_dev);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(h->d_pose_s, pose_start_dev, pb, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(h->d_pose_t, pose_end_dev, pb, cudaMemcpyDeviceToDevice, st));
     return TAC_OK;
 }
 

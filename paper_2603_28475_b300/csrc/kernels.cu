@@ -2371,6 +2371,59 @@ __device__ __noinline__ void pcg_vectors(const Dev& D, const PadDev& P, const Me
     __syncthreads();
 }
 
+// Installs a frame that was solved before, without solving it again, for the
+// adjoint kernels: the start state (x0, v0; caller order [Vt][3]) with the
+// start pose in pose_t, the end pose in pose_n, and the end positions x1.
+// The friction lag is rebuilt from the start state and pose by the same
+// steps as the solve's frame setup (broad phase at the start, lag_build), so
+// that it equals the lag the frame was solved with when x0, v0 and the poses
+// are the ones that solve started from.
+__global__ void __launch_bounds__(kThreads) frame_install_kernel(const __grid_constant__ Dev D, const float* x0,
+                                                                 const float* v0, const float* x1) {
+    const int pad = blockIdx.x;
+    load_pad(D, pad);
+    const PadDev& P = S.P;
+    const MeshDev& M = S.M;
+    const EnvDev& E = S.E;
+    world_indenter(D, P, E, D.pose_t + 6 * pad, D.Yt);
+    world_indenter(D, P, E, D.pose_n + 6 * pad, D.Yn);
+    for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
+        const size_t si = (size_t)P.v_off + i;
+        const size_t u = (size_t)P.v_off + D.vuser[M.xv_off + i];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const size_t sc = c * (size_t)D.Vt + si;
+            const float hi = x0[3 * u + c] - D.X[c * (size_t)D.XVt + M.xv_off + i];
+            const float v = v0[3 * u + c];
+            D.uh[sc] = hi;
+            D.ul[sc] = 0.f;
+            D.vel[sc] = v;
+            D.u0h[sc] = hi;
+            D.u0l[sc] = 0.f;
+            D.uhat[sc] = hi + P.h * v;
+        }
+    }
+    __syncthreads();
+    const double rbp = (P.dhat + P.dhat) * (1.0 + 1e-6);
+    SrcState src{&D, &P, &M, 0.0f};
+    int n = bp_build(src, D, M, E, D.ilist + P.il_off, rbp, D.pairs + P.pair_off, P.pair_cap);
+    int nlag = lag_build(D, P, M, E, min(n, P.pair_cap));
+    if (threadIdx.x == 0) D.pad_nlag[pad] = nlag;
+    __syncthreads();
+    for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
+        const size_t si = (size_t)P.v_off + i;
+        const size_t u = (size_t)P.v_off + D.vuser[M.xv_off + i];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const size_t sc = c * (size_t)D.Vt + si;
+            const float hi = x1[3 * u + c] - D.X[c * (size_t)D.XVt + M.xv_off + i];
+            D.uh[sc] = hi;
+            D.ul[sc] = 0.f;
+            D.vel[sc] = (x1[3 * u + c] - x0[3 * u + c]) / P.h;
+        }
+    }
+}
+
 enum { ADJ_CONVERGED = 0, ADJ_MAXITER = 1, ADJ_BREAKDOWN = 2, ADJ_NONFINITE = 3 };
 
 // Adjoint of the last frame. dLdm (markers) and dLdx (caller-order end
@@ -2538,6 +2591,8 @@ cudaError_t configure_kernels() {
     e = cudaFuncSetAttribute(debug_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(frame_install_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(broadphase_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }

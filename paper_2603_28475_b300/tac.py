@@ -19,7 +19,7 @@ TAC_OK = 0
 PAD_STATUS = {0: "converged", 1: "maxiter", 2: "nonfinite", 3: "linesearch", 4: "pair_overflow"}
 
 SYMBOLS = ("tac_create_batch", "tac_destroy_batch", "tac_reset", "tac_set_indenter", "tac_step", "tac_markers",
-           "tac_adjoint", "tac_adjoint_frame",
+           "tac_adjoint", "tac_adjoint_frame", "tac_set_frame",
            "tac_get_state", "tac_set_state", "tac_set_params", "tac_get_params", "tac_broadphase",
            "tac_broadphase_static",
            "tac_debug_eval", "tac_stats",
@@ -64,6 +64,7 @@ def load_library(path=_LIB_PATH):
         "tac_markers": [vp, vp, vp],
         "tac_adjoint": [vp, vp, vp, vp, vp, i, f, vp],
         "tac_adjoint_frame": [vp, vp, vp, vp, vp, vp, vp, vp, i, f, vp],
+        "tac_set_frame": [vp, vp, vp, vp, vp, vp, vp],
         "tac_get_state": [vp, vp, vp, vp],
         "tac_set_state": [vp, vp, vp, vp],
         "tac_set_params": [vp, ctypes.POINTER(Params), i],
@@ -247,6 +248,17 @@ class TacBatch:
                                        float(tol), _stream(stream)))
         self._hold = (gm, gx)
         return out, dx0, dv0, st, it
+
+    def set_frame(self, x0, v0, pose_start, x1, pose_end, stream=None):
+        """Install a solved frame for the adjoint without re-solving it
+        (tac_set_frame): start state x0, v0 and end positions x1
+        [total_verts, 3], poses [n_pads, 6]."""
+        a = [self._f32(t).reshape(-1, 3) for t in (x0, v0, x1)]
+        ps = self._f32(pose_start).reshape(self.n_pads, 6)
+        pe = self._f32(pose_end).reshape(self.n_pads, 6)
+        _check(lib().tac_set_frame(self._h, _ptr(a[0]), _ptr(a[1]), _ptr(ps), _ptr(a[2]), _ptr(pe),
+                                   _stream(stream)))
+        self._hold = (a, ps, pe)
 
     def get_state(self, stream=None):
         x = torch.empty(self.total_verts, 3, dtype=torch.float32, device=self.device)

@@ -199,3 +199,37 @@ def test_sequence_autograd_matches_oracle_sweep(tac, oracle_seq):
     for k in range(ref.size):
         assert got[k] == pytest.approx(ref[k], rel=2e-3, abs=2e-4 * scale), (k, got, ref)
     b.close()
+
+
+def test_installed_frame_gives_the_same_adjoint(tac, oracle_seq):
+    """tac_set_frame installs frame 3 from its start state, poses and end
+    positions without solving; its adjoint equals the adjoint taken right
+    after the frame's own solve (the end positions differ only by the
+    float32 readback)."""
+    pad, ind, poses, states, cs, gx = oracle_seq
+    pd, mat, ind_s, _ = _scene()
+    w = S.Workload("adjoint", [pd], [mat], [ind_s], 1, poses[:, None, :])
+    b = tac.batch_from_workload(w, tol=TIGHT)
+    P = torch.tensor(poses).reshape(4, 1, 6)
+    b.reset(P[0])
+    for f in (1, 2):
+        b.set_indenter(P[f])
+        b.step()
+    x0, v0 = b.get_state()
+    b.reset(P[2])
+    b.set_state(x0, v0)
+    b.set_indenter(P[3])
+    st, _ = b.step()
+    assert int(st.item()) == 0
+    x1, _ = b.get_state()
+    c = torch.tensor(cs[2], dtype=torch.float32)
+    g = torch.tensor(gx, dtype=torch.float32)
+    thA, dxA, dvA, stA, _ = b.adjoint_frame(c, g)
+    b.set_frame(x0, v0, P[2], x1, P[3])
+    thB, dxB, dvB, stB, _ = b.adjoint_frame(c, g)
+    assert int(stA.item()) == 0 and int(stB.item()) == 0
+    a, bb = thA.cpu().numpy()[0], thB.cpu().numpy()[0]
+    assert np.abs(a - bb).max() <= 1e-4 * np.abs(a).max(), (a, bb)
+    assert _rel(dxB.cpu().numpy().astype(np.float64), dxA.cpu().numpy().astype(np.float64)) <= 1e-4
+    assert _rel(dvB.cpu().numpy().astype(np.float64), dvA.cpu().numpy().astype(np.float64)) <= 1e-4
+    b.close()
