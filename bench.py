@@ -61,6 +61,8 @@ def parse():
                     help="time the calibration workload's 16-frame forward and reverse sweep instead")
     ap.add_argument("--adjoint-envs", type=int, default=256)
     ap.add_argument("--adjoint-frames", type=int, default=16)
+    ap.add_argument("--sweep", action="store_true",
+                    help="throughput over env counts and pad sizes (the large-scale sweep) instead")
     return ap.parse_args()
 
 
@@ -433,6 +435,69 @@ def run_adjoint(args):
     b.close()
 
 
+SWEEP_POINTS = ((64, 2000), (256, 2000), (1024, 2000), (1024, 10000), (64, 50000), (256, 50000),
+                (1024, 50000))
+
+
+def run_sweep(args):
+    """Throughput over environment counts and pad sizes: one pad of ~V
+    vertices per env, a cylinder press with friction 0.5 (scenes.config_sweep).
+    Per point: W warm-up frames, then K timed frames (CUDA events on the
+    stream); converged env-frames/s, ms per frame and counted GB/s of the
+    solve launch. Prints one JSON line with all points."""
+    import torch
+    from paper_2603_28475_b300 import scenes as S
+    from paper_2603_28475_b300 import tac
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    W, K = 2, 2
+    peak, peak_kind = load_peaks()
+    pts = []
+    for envs, nv in SWEEP_POINTS:
+        w = S.config_sweep(envs, nv, frames=W + K, seed=args.seed)
+        cap = max(args.pair_capacity, int(args.pair_capacity * 1.5 * (nv / 10000.0) ** (2.0 / 3.0)))
+        b = tac.batch_from_workload(w, pair_capacity=cap)
+        poses = torch.tensor(w.poses, dtype=torch.float32, device=dev)
+        st = torch.empty(w.n_pads, dtype=torch.int32, device=dev)
+        it = torch.empty(w.n_pads, dtype=torch.int32, device=dev)
+        b.reset(poses[0])
+        for f in range(1, W + 1):
+            b.set_indenter(poses[f])
+            b.step(st, it)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        ms, conv, nbytes, iters = 0.0, 0, 0.0, []
+        for f in range(W + 1, W + K + 1):
+            b.set_indenter(poses[f])
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.step(st, it)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            conv += int((st == 0).sum().item())
+            nbytes += algorithmic_bytes(b.stats().cpu().numpy(), w)
+            iters.append(it.cpu().numpy())
+        its = np.concatenate(iters)
+        gbs = nbytes / (ms / 1e3) / 1e9
+        pts.append({"envs": envs, "pad_verts": w.pads[0].n_verts, "pad_tets": w.pads[0].n_tets,
+                    "pair_capacity": cap, "env_frames_per_s": conv / (ms / 1e3), "ms_per_frame": ms / K,
+                    "converged_fraction": conv / (K * envs), "iters_p50": float(np.percentile(its, 50)),
+                    "counted_gbs": gbs, "frac_of_peak": gbs / peak})
+        b.close()
+        del b
+        torch.cuda.empty_cache()
+        print(json.dumps(pts[-1]), file=sys.stderr, flush=True)
+    out = {"metric": "converged env-frames/s over env counts and pad sizes (large-scale sweep)",
+           "unit": "env-frames/s", "higher_is_better": True, "n_gpus": 1, "warmup": W, "steps": K,
+           "peak": peak, "peak_kind": peak_kind, "data": "synthetic",
+           "dtype": "f32 (double-float displacements; f64 pair distance, barrier, CCD and reductions)",
+           "config": {"workload": "sweep (scenes.config_sweep)", "friction": 0.5, "tol_rel_grad": 1e-6,
+                      "frames": f"{W + 1}..{W + K} of a 0.05 mm/frame press"},
+           "points": pts}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -440,6 +505,10 @@ def main():
     if args.adjoint:
         if rank == 0:
             run_adjoint(args)
+        return
+    if args.sweep:
+        if rank == 0:
+            run_sweep(args)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

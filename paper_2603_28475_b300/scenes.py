@@ -453,9 +453,15 @@ _CLASS_CACHE = {}
 
 def size_class_pad(cls):
     """Hex-split sensor pad of one size class (cached: pads of a class share
-    their host arrays)."""
+    their host arrays). Classes outside SIZE_CLASSES get cells in the
+    sensor's aspect with about ``cls`` vertices."""
     if cls not in _CLASS_CACHE:
-        _CLASS_CACHE[cls] = hex_pad(SENSOR_SIZE, SIZE_CLASSES[cls], marker_shape=(9, 7))
+        if cls in SIZE_CLASSES:
+            cells = SIZE_CLASSES[cls]
+        else:
+            k = (cls / (4.65 * 3.575)) ** (1 / 3)
+            cells = (max(2, round(4.65 * k)), max(2, round(3.575 * k)), max(2, round(k)))
+        _CLASS_CACHE[cls] = hex_pad(SENSOR_SIZE, cells, marker_shape=(9, 7))
     return _CLASS_CACHE[cls]
 
 
@@ -538,3 +544,36 @@ def config_calibration(n_envs=256, frames=16, seed=0, step=0.05 * MM, mu_f=0.5):
         poses[:, e, 5] = z0 - press
     w = Workload(f"calibration_{n_envs}env", pads, mats, inds, 1, poses.astype(np.float32))
     return w, hidden
+
+
+def config_sweep(n_envs, n_verts, frames=8, seed=0, step=0.05 * MM, mu_f=0.5):
+    """Throughput sweep workload: ``n_envs`` environments of one pad of about
+    ``n_verts`` vertices (hex-split sensor pad) and a cylinder peg
+    (r ~ U[2, 4] mm, rotation vector components ~ U(+-15 deg), xy offset
+    ~ U(+-1 mm)), pressed ``step`` per frame from a d-hat gap to a depth
+    ~ U[0, 1.2] mm, then held; friction ``mu_f``."""
+    rng = np.random.default_rng(np.random.PCG64(20260 + 5000 + seed))
+    pads, mats, inds = [], [], []
+    poses = np.zeros((frames + 1, n_envs, 6))
+    cyl_cache = {}
+    pad = size_class_pad(n_verts)
+    for e in range(n_envs):
+        r = float(rng.uniform(2 * MM, 4 * MM))
+        key = round(r / (0.05 * MM))
+        if key not in cyl_cache:
+            cyl_cache[key] = cylinder(key * 0.05 * MM, 24 * MM, 64, 8)
+        ind = cyl_cache[key]
+        pads.append(pad)
+        mats.append(Material(mu_f=mu_f))
+        inds.append(ind)
+        rot = np.deg2rad(rng.uniform(-15, 15, size=3))
+        off = rng.uniform(-1 * MM, 1 * MM, size=2)
+        depth = float(rng.uniform(0, 1.2 * MM))
+        lx, ly, lz = pad.size
+        cx, cy = lx / 2 + off[0], ly / 2 + off[1]
+        z0 = place_above_box(ind.verts, rot, (cx, cy), pad.size, DHAT, ind.tris)
+        poses[:, e, :3] = rot
+        poses[:, e, 3] = cx
+        poses[:, e, 4] = cy
+        poses[:, e, 5] = z0 - np.minimum(step * np.arange(frames + 1), depth + DHAT)
+    return Workload(f"sweep_{n_envs}env_{pad.n_verts}v", pads, mats, inds, 1, poses.astype(np.float32))
