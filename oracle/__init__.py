@@ -13,7 +13,7 @@ Newton check) are taken with the truncated Taylor arithmetic of
 
 Modules
   geometry   -- rest shape (Dm^-1, volume), lumped mass, surface primitives,
-                marker barycentric mapping, indenter placement
+                marker mappings (barycentric, kNN-IDW), indenter placement
   taylor     -- second-order forward-mode arithmetic (value, d/dt, d2/dt2)
   energy     -- the incremental potential of Eq. (ipc_energy): inertia,
                 Neo-Hookean elasticity, log-barrier over PT / EE pairs,

@@ -91,6 +91,37 @@ def marker_map(rest, surf_tris, markers_xy):
     return ids, w
 
 
+def marker_map_knn(rest, markers_xy, k=4):
+    """kNN inverse-distance mapping of markers onto rest mesh nodes (Sec. 3.2:
+    the k nearest initial nodes, the marker displacement interpolated from
+    them with weights). Readings: the candidate nodes are those of the rest
+    top face (rest z equal to the maximum rest z, the face the markers lie
+    on); distance is the 2-D distance in that face, ranked by the squared
+    distance dx^2 + dy^2 with ties to the smaller node id; the k nearest take
+    weights w_i proportional to 1/d_i, normalised to sum to 1 (summed in
+    rank order); a marker at zero distance from its nearest node takes that
+    node alone. Returns (node ids [M, k], weights [M, k])."""
+    X = np.asarray(rest, dtype=np.float64)
+    top = np.flatnonzero(X[:, 2] == X[:, 2].max())
+    if top.size < k:
+        raise ValueError("fewer top-face nodes than marker neighbours")
+    nm = len(markers_xy)
+    ids = np.zeros((nm, k), dtype=np.int64)
+    w = np.zeros((nm, k))
+    for m, q in enumerate(np.asarray(markers_xy, dtype=np.float64)):
+        dx, dy = X[top, 0] - q[0], X[top, 1] - q[1]
+        d2 = dx * dx + dy * dy
+        order = np.lexsort((top, d2))[:k]
+        ids[m] = top[order]
+        d = np.sqrt(d2[order])
+        if d[0] == 0.0:
+            w[m, 0] = 1.0
+        else:
+            inv = 1.0 / d
+            w[m] = inv / inv.sum()
+    return ids, w
+
+
 def indenter_world(verts, pose):
     """World (pad-frame) indenter vertices y = R(rotvec) Y + t for a pose
     (rotvec[3], t[3])."""
@@ -138,12 +169,15 @@ class IndenterModel:
     edges: np.ndarray
 
 
-def build_pad(rest, tets, fixed, markers_xy, E, nu, rho, h, dhat, mu_f, kappa=None, eps_v=None):
+def build_pad(rest, tets, fixed, markers_xy, E, nu, rho, h, dhat, mu_f, kappa=None, eps_v=None,
+              marker_mode="bary"):
     """Precompute a pad. Conventions: kappa (barrier stiffness) defaults to
     KAPPA_SCALE * h^2 E l-bar, eps_v (friction mollifier width, a
     displacement) to 1e-3 m/s * h, and the gradient scale of the stopping
     rule is g_ref = h^2 E l-bar dhat (the elastic gradient of a dhat-sized
-    displacement over one element)."""
+    displacement over one element). marker_mode "bary" maps each marker to
+    its rest top-face triangle (marker_map), "knn" to its 4 nearest rest
+    nodes with inverse-distance weights (marker_map_knn)."""
     rest = np.asarray(rest, dtype=np.float64)
     tets = np.asarray(tets, dtype=np.int64)
     Dm_inv, vol = rest_shape(rest, tets)
@@ -153,7 +187,12 @@ def build_pad(rest, tets, fixed, markers_xy, E, nu, rho, h, dhat, mu_f, kappa=No
     free = np.ones(rest.shape[0], dtype=bool)
     free[np.asarray(fixed, dtype=np.int64)] = False
     st, se, sv = surface(tets)
-    mids, mw = marker_map(rest, st, markers_xy)
+    if marker_mode == "bary":
+        mids, mw = marker_map(rest, st, markers_xy)
+    elif marker_mode == "knn":
+        mids, mw = marker_map_knn(rest, markers_xy)
+    else:
+        raise ValueError(f"unknown marker_mode {marker_mode!r}")
     mu, lam = lame(E, nu)
     lbar = mean_surface_edge(rest, se)
     if kappa is None or kappa <= 0:

@@ -12,7 +12,10 @@ with the step rule of Eq. (step_size). Readings where the paper is silent:
     (dropped when p^T H p <= 0); then Armijo backtracking (c = 1e-4, halve
     up to 20 times). The Armijo test E(x + a p) <= E(x) + c a g^T p is
     evaluated in its equivalent remainder form R(a) <= (1 - c) a |g^T p|,
-    R(a) = E(x + a p) - E(x) - a g^T p summed element by element;
+    R(a) = E(x + a p) - E(x) - a g^T p summed element by element.
+    ``step="literal"`` is Eq. (step_size) as printed: alpha = min(alpha_upper,
+    alpha_bar), no CCD bound and no energy test; a trial state outside E's
+    domain (an inverted tet, a closed gap) is still halved;
   * direction restart (beta = 0) when |y^T p| is negligible or the new p
     is not a descent direction;
   * stopping: max_i |g_i| (free DOFs) <= tol * g_ref, g_ref = max(h^2 E
@@ -56,6 +59,7 @@ class Params:
     max_substeps: int = 1000
     margin_factor: float = 1.0        # m = margin_factor * dhat
     precond: str = "block"
+    step: str = "bounded"             # "literal": alpha = min(alpha_upper, alpha_bar), no CCD, no Armijo
 
 
 @dataclasses.dataclass
@@ -271,8 +275,9 @@ def solve_frame(pad, ind, state, pose_next, prm=Params(), trace=None, lag=None):
             if pn == 0.0 or gTp >= 0.0:
                 p = -apply_P(P, g)
                 pn, gTp = vnorm_max(p), float(np.sum(g * p))
+            literal = prm.step == "literal"
             a_up = dhat / (2.0 * pn)
-            a_ccd = ccd_bound(fr, x, p, s, cand, prm.eta)
+            a_ccd = np.inf if literal else ccd_bound(fr, x, p, s, cand, prm.eta)
             jet = En.total_line(fr, x, p, s, cand)
             pHp = float(jet.dd)
             a_bar = -gTp / pHp if pHp > 0 else np.inf
@@ -281,12 +286,16 @@ def solve_frame(pad, ind, state, pose_next, prm=Params(), trace=None, lag=None):
                 cand = BP.candidates(x, fr.y(s), pad, ind, r_inf)
                 info.rebuilds += 1
                 M = 0.0
-                a_ccd = ccd_bound(fr, x, p, s, cand, prm.eta)
+                if not literal:
+                    a_ccd = ccd_bound(fr, x, p, s, cand, prm.eta)
                 alpha = min(a_up, a_ccd, a_bar)
             accepted = False
             for _ in range(prm.max_halvings + 1):
                 R = remainder(fr, x, p, alpha, s, cand)
-                if R <= (1.0 - prm.armijo_c) * alpha * (-gTp):
+                # the literal rule (Eq. step_size) takes alpha as it is; only
+                # a trial state outside the energy's domain (an inverted tet
+                # or a closed gap, where E is +inf) is halved
+                if (np.isfinite(R) if literal else R <= (1.0 - prm.armijo_c) * alpha * (-gTp)):
                     accepted = True
                     break
                 alpha *= 0.5
