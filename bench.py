@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--adjoint-frames", type=int, default=16)
     ap.add_argument("--sweep", action="store_true",
                     help="throughput over env counts and pad sizes (the large-scale sweep) instead")
+    ap.add_argument("--variants", action="store_true",
+                    help="iterations and throughput of the paper-literal variants on the batched workload instead")
     return ap.parse_args()
 
 
@@ -498,6 +500,68 @@ def run_sweep(args):
     print(json.dumps(out), flush=True)
 
 
+VARIANTS = (("block_jacobi_bounded_step", dict()),
+            ("scalar_jacobi", dict(precond=1)),
+            ("literal_step", dict(step=1)),
+            ("scalar_jacobi_literal_step", dict(precond=1, step=1)))
+
+
+def run_variants(args):
+    """The paper-literal variants (scalar Jacobi preconditioner; Eq.
+    (step_size) as printed, without CCD bound or energy test) against the
+    chosen forms on the batched workload: W warm-up frames, then K timed
+    frames per variant (CUDA events on the stream). Per variant: converged
+    env-frames/s, ms per frame, converged fraction, PNCG iterations per pad
+    (mean, p50, p99) and step halvings per pad-frame. Prints one JSON line."""
+    import torch
+    from paper_2603_28475_b300 import tac
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    W, K = args.warmup, args.steps
+    w = workload(args.envs, W + K + 1, args.seed)
+    poses = torch.tensor(w.poses, dtype=torch.float32, device=dev)
+    res = []
+    for name, modes in VARIANTS:
+        b = tac.batch_from_workload(w, pair_capacity=args.pair_capacity, **modes)
+        st = torch.empty(w.n_pads, dtype=torch.int32, device=dev)
+        it = torch.empty(w.n_pads, dtype=torch.int32, device=dev)
+        b.reset(poses[0])
+        for f in range(1, W + 1):
+            b.set_indenter(poses[f])
+            b.step(st, it)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        ms, conv, iters, halv, status = 0.0, 0, [], [], []
+        for f in range(W + 1, W + K + 1):
+            b.set_indenter(poses[f])
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.step(st, it)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            conv += int(np.all(st.cpu().numpy().reshape(-1, w.pads_per_env) == 0, axis=1).sum())
+            iters.append(it.cpu().numpy())
+            halv.append(b.stats().cpu().numpy()[:, 3])
+            status.append(st.cpu().numpy())
+        its, hv, sts = np.concatenate(iters), np.concatenate(halv), np.concatenate(status)
+        res.append({"variant": name, "modes": modes, "env_frames_per_s": conv / (ms / 1e3),
+                    "ms_per_frame": ms / K, "converged_env_fraction": conv / (K * w.n_envs),
+                    "status_counts": {str(k): int(v) for k, v in zip(*np.unique(sts, return_counts=True))},
+                    "iters_mean": float(its.mean()), "iters_p50": float(np.percentile(its, 50)),
+                    "iters_p99": float(np.percentile(its, 99)), "halvings_per_pad_frame": float(hv.mean())})
+        b.close()
+        del b
+        torch.cuda.empty_cache()
+        print(json.dumps(res[-1]), file=sys.stderr, flush=True)
+    out = {"metric": "converged env-frames/s and PNCG iterations per variant (batched press)",
+           "unit": "env-frames/s", "higher_is_better": True, "n_gpus": 1, "warmup": W, "steps": K,
+           "data": "synthetic", "config": {"workload": f"batched press, {args.envs} envs x 2 pads (2k/5k/10k)",
+                                           "tol_rel_grad": 1e-6, "pair_capacity": args.pair_capacity},
+           "variants": res}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -509,6 +573,10 @@ def main():
     if args.sweep:
         if rank == 0:
             run_sweep(args)
+        return
+    if args.variants:
+        if rank == 0:
+            run_variants(args)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

@@ -93,11 +93,22 @@ typedef struct {
  *                 substep); see tac_pad_norms for the float32 floor
  *  tol_advance    looser tolerance of the intermediate indenter substeps
  *  max_iter       PNCG iteration cap per frame
- *  precond_mode   0 = 3x3 block Jacobi, 1 = scalar Jacobi diag(H)^-1 */
+ *  precond_mode   0 = 3x3 block Jacobi, 1 = scalar Jacobi diag(H)^-1
+ *                 (the literal preconditioner of Supp. A)
+ *  step_mode      0 = alpha = min(alpha_upper, alpha_ccd, alpha_bar) with an
+ *                 Armijo test (c = 1e-4, up to 20 halvings); 1 = Eq.
+ *                 (step_size) as printed, alpha = min(alpha_upper, alpha_bar)
+ *                 with no CCD bound and no energy test (a trial state that
+ *                 inverts a tet or closes a gap is halved)
+ *  marker_mode    0 = barycentric on the rest top-face triangle holding the
+ *                 marker; 1 = the 4 rest top-face nodes nearest to the marker
+ *                 (2-D distance, ties to the smaller id) with weights
+ *                 proportional to 1/d (Sec. 3.2's kNN mapping). Fixed at
+ *                 creation: tac_set_params rejects a change */
 typedef struct {
     float E, nu, rho, h, dhat, kappa, mu_f, eps_v;
     float tol_rel_grad, tol_advance;
-    int max_iter, precond_mode;
+    int max_iter, precond_mode, step_mode, marker_mode;
 } tac_params;
 
 /* Batch options. pair_capacity: candidate pairs stored per pad (0 = 16384).
@@ -296,6 +307,16 @@ int tac_stats(tac_handle h, long long* stats_dev, void* stream);
  * max(tol * g_ref, 256 * 2^-24 * F): a float32 gradient is not resolved
  * below a few hundred ulps of the forces summed into it. */
 int tac_pad_norms(tac_handle h, double* norms_dev, void* stream);
+
+/* Host only (no device work, no handle): the marker map that tac_create_batch
+ * builds for this pad under marker_mode (see tac_params). ids_host and w_host
+ * are caller-owned host arrays of [n_markers*4]: marker m reads vertices
+ * ids_host[4m..4m+3] (input vertex ids) with weights w_host[4m..4m+3]; the
+ * barycentric map fills three slots and gives the fourth weight 0 (its id
+ * repeats the first). Validates the mesh like tac_create_batch
+ * (TAC_ERR_INVALID_MESH with a message). tac_markers and the adjoint's
+ * right-hand side read the pads through this map. */
+int tac_marker_map(const tac_pad_desc* pad, int marker_mode, int* ids_host, float* w_host);
 
 /* Sizes: total vertices, total markers, candidate capacity per pad, and the
  * number of CTAs of one tac_step launch (resident CTAs of the device, at most

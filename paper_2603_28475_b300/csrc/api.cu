@@ -205,12 +205,14 @@ void fill_pad_params(tac_batch* b, int p) {
     P.tol_adv = q.tol_advance;
     P.max_iter = q.max_iter;
     P.precond = q.precond_mode;
+    P.step = q.step_mode;
     b->hstep[p] = q.h;
 }
 
 bool params_ok(const tac_params& q) {
     return q.E > 0 && q.nu > -1 && q.nu < 0.5f && q.rho > 0 && q.h > 0 && q.dhat > 0 && q.mu_f >= 0 &&
-           q.tol_rel_grad > 0 && q.tol_advance > 0 && q.max_iter >= 0 && (q.precond_mode == 0 || q.precond_mode == 1);
+           q.tol_rel_grad > 0 && q.tol_advance > 0 && q.max_iter >= 0 && (q.precond_mode == 0 || q.precond_mode == 1) &&
+           (q.step_mode == 0 || q.step_mode == 1) && (q.marker_mode == 0 || q.marker_mode == 1);
 }
 
 }  // namespace
@@ -246,7 +248,8 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
         const tac_pad_desc& d = pads[p];
         std::vector<const void*> key = {d.rest_xyz, d.tets, d.fixed_idx, d.marker_xy,
                                         (const void*)(intptr_t)d.n_verts, (const void*)(intptr_t)d.n_tets,
-                                        (const void*)(intptr_t)d.n_fixed, (const void*)(intptr_t)d.n_markers};
+                                        (const void*)(intptr_t)d.n_fixed, (const void*)(intptr_t)d.n_markers,
+                                        (const void*)(intptr_t)params[p].marker_mode};
         auto it = share ? seen.find(key) : seen.end();
         if (it != seen.end()) {
             b->pad_mesh.push_back(it->second);
@@ -254,7 +257,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
         }
         PadMesh M;
         if (!build_pad_mesh(d.n_verts, d.n_tets, d.n_fixed, d.n_markers, d.rest_xyz, d.tets, d.fixed_idx,
-                            d.marker_xy, M, err)) {
+                            d.marker_xy, params[p].marker_mode, M, err)) {
             delete b;
             return fail(TAC_ERR_INVALID_MESH, "pad " + std::to_string(p) + ": " + err);
         }
@@ -365,8 +368,8 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     int* sv = dalloc<int>(K, sv_tot, rc);
     int* stt = dalloc<int>(K, 3 * (size_t)st_tot, rc);
     int* se = dalloc<int>(K, 2 * (size_t)se_tot, rc);
-    int* mk_ids = dalloc<int>(K, 3 * (size_t)mk_tot, rc);
-    float* mk_w = dalloc<float>(K, 3 * (size_t)mk_tot, rc);
+    int* mk_ids = dalloc<int>(K, kMarkerSlots * (size_t)mk_tot, rc);
+    float* mk_w = dalloc<float>(K, kMarkerSlots * (size_t)mk_tot, rc);
     float* Y = dalloc<float>(K, 3 * (size_t)y_tot, rc);
     int* it = dalloc<int>(K, 3 * (size_t)t_tot, rc);
     int* ie = dalloc<int>(K, 2 * (size_t)e_tot, rc);
@@ -616,6 +619,9 @@ int tac_set_params(tac_handle h, const tac_params* per_pad, int n) {
     if (!h || !per_pad || n != h->n_pads) return fail(TAC_ERR_INVALID_ARG, "need n_pads parameter sets");
     for (int p = 0; p < n; ++p)
         if (!params_ok(per_pad[p])) return fail(TAC_ERR_INVALID_ARG, "invalid parameters for pad " + std::to_string(p));
+    for (int p = 0; p < n; ++p)
+        if (per_pad[p].marker_mode != h->params[p].marker_mode)
+            return fail(TAC_ERR_INVALID_ARG, "marker_mode is fixed at creation (pad " + std::to_string(p) + ")");
     h->params.assign(per_pad, per_pad + n);
     for (int p = 0; p < n; ++p) fill_pad_params(h, p);
     CUDA_TRY(cudaDeviceSynchronize());
@@ -707,6 +713,22 @@ int tac_pad_norms(tac_handle h, double* norms_dev, void* stream) {
     if (!h || !norms_dev) return fail(TAC_ERR_INVALID_ARG, "null argument");
     CUDA_TRY(cudaMemcpyAsync(norms_dev, h->dev.norms, 4 * (size_t)h->n_pads * 8, cudaMemcpyDeviceToDevice,
                              static_cast<cudaStream_t>(stream)));
+    return TAC_OK;
+}
+
+int tac_marker_map(const tac_pad_desc* pad, int marker_mode, int* ids_host, float* w_host) {
+    if (!pad || !ids_host || !w_host) return fail(TAC_ERR_INVALID_ARG, "null argument");
+    if (marker_mode != 0 && marker_mode != 1) return fail(TAC_ERR_INVALID_ARG, "unknown marker mode");
+    PadMesh M;
+    std::string err;
+    if (!build_pad_mesh(pad->n_verts, pad->n_tets, pad->n_fixed, pad->n_markers, pad->rest_xyz, pad->tets,
+                        pad->fixed_idx, pad->marker_xy, marker_mode, M, err))
+        return fail(TAC_ERR_INVALID_MESH, err);
+    // the mesh stores internal vertex ids; report input ids
+    for (size_t k = 0; k < M.mk_ids.size(); ++k) {
+        ids_host[k] = M.vuser[M.mk_ids[k]];
+        w_host[k] = M.mk_w[k];
+    }
     return TAC_OK;
 }
 

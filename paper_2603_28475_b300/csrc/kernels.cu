@@ -6,6 +6,9 @@
 //    then Armijo backtracking on E(x + alpha p) - E(x) <= c alpha g^T p,
 //    evaluated as alpha g(x + alpha p)^T p - R'(alpha) with R' the
 //    element-wise second-order remainder expanded at the trial point;
+//    the pad's step mode 1 is Eq. (step_size) as printed: alpha =
+//    min(alpha_upper, alpha_bar), no CCD bound and no energy test (a trial
+//    state outside E's domain is still halved);
 //  * beta of Eq. (dk_direction); restart when y^T p is negligible or the new
 //    direction is not a descent direction;
 //  * the indenter moves on the straight per-vertex path between its frame
@@ -1749,6 +1752,8 @@ __device__ void solve_pad(const Dev& D, int pad) {
             clk.lap(PH_PAIR_PHP);
             double pHp = tp.acc + php_c + dir.pMp;
             double a_bar = pHp > 0.0 ? -dir.gTp / pHp : 1e300;
+            const bool literal = P.step == 1;   // Eq. (step_size) as printed: no CCD bound
+            if (literal) a_ccd = 1e300;
             double alpha = fmin(fmin(a_up, a_ccd), a_bar);
             if (Mb + alpha * dir.pn > margin) {
                 SrcState src{&D, &P, &M, (float)s};
@@ -1762,6 +1767,7 @@ __device__ void solve_pad(const Dev& D, int pad) {
                 double dummy;
                 pair_php(D, P, M, E, cc.npairs, cc.nlag, s, dummy, a_ccd);
                 ctr.pair_evals += cc.npairs;
+                if (literal) a_ccd = 1e300;
                 alpha = fmin(fmin(a_up, a_ccd), a_bar);
                 clk.lap(PH_BROAD);
             }
@@ -1786,7 +1792,8 @@ __device__ void solve_pad(const Dev& D, int pad) {
                     double a = (double)af;
                     double R = tt.acc + remc + 0.5 * a * a * dir.pMp;
                     double dE = a * dt.pg1 - R;
-                    if (dE <= kArmijoC * a * dir.gTp) {
+                    // the literal rule takes any trial state inside E's domain
+                    if (literal || dE <= kArmijoC * a * dir.gTp) {
                         accepted = true;
                         alpha = a;
                         fmax = tt.fmax;
@@ -2020,11 +2027,11 @@ __global__ void markers_kernel(const __grid_constant__ Dev D, float* out) {
     const MeshDev M = D.meshes[P.mesh];
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M.n_mk) return;
-    const int* id = D.mk_ids + 3 * (M.mk_off + m);
-    const float* w = D.mk_w + 3 * (M.mk_off + m);
+    const int* id = D.mk_ids + kMarkerSlots * (M.mk_off + m);
+    const float* w = D.mk_w + kMarkerSlots * (M.mk_off + m);
     for (int c = 0; c < 2; ++c) {
         float a = 0.f;
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < kMarkerSlots; ++k) {
             int sc = c * D.Vt + P.v_off + id[k];
             a += w[k] * (D.uh[sc] + D.ul[sc]);
         }
@@ -2474,9 +2481,9 @@ __global__ void __launch_bounds__(kThreads, 2) adjoint_kernel(const __grid_const
     }
     if (dLdm && threadIdx.x == 0)
         for (int m = 0; m < M.n_mk; ++m)
-            for (int k = 0; k < 3; ++k) {
-                int v = D.mk_ids[3 * (M.mk_off + m) + k];
-                float w = D.mk_w[3 * (M.mk_off + m) + k];
+            for (int k = 0; k < kMarkerSlots; ++k) {
+                int v = D.mk_ids[kMarkerSlots * (M.mk_off + m) + k];
+                float w = D.mk_w[kMarkerSlots * (M.mk_off + m) + k];
                 if (D.fixed[M.xv_off + v]) continue;
                 for (int c = 0; c < 2; ++c)
                     D.adj_r[c * D.Vt + P.v_off + v] += w * dLdm[2 * (P.mk_out + m) + c];

@@ -18,6 +18,10 @@ constexpr int kPatchVerts = 32;
 constexpr int kPatchCsr = kPatchVerts + 1;
 constexpr uint32_t kNoTet = 0xffffffffu;
 
+// Marker map: every marker reads kMarkerSlots weighted mesh vertices (a
+// barycentric map fills three and gives the fourth weight 0).
+constexpr int kMarkerSlots = 4;
+
 // Flags carried in the high bits of a patch's vertex entry (entries >= 0).
 constexpr int kFirstFlag = 1 << 30;   // first patch (in processing order) touching the vertex
 constexpr int kLastFlag = 1 << 29;    // last patch touching the vertex

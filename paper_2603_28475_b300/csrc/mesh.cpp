@@ -42,8 +42,97 @@ char msgbuf[256];
 
 }  // namespace
 
+bool build_marker_map(int nv, const float* rest, const std::vector<int>& surf, int nm, const float* markers,
+                      int mode, std::vector<int>& ids, std::vector<float>& w, std::string& err) {
+    if (mode != 0 && mode != 1) {
+        err = "unknown marker mode";
+        return false;
+    }
+    ids.assign(kMarkerSlots * static_cast<size_t>(nm), 0);
+    w.assign(kMarkerSlots * static_cast<size_t>(nm), 0.0f);
+    if (nm == 0) return true;
+    float ztop = rest[2];
+    for (int i = 0; i < nv; ++i) ztop = std::max(ztop, rest[3 * i + 2]);
+    if (mode == 0) {
+        // the top-face triangle maximising the marker's smallest barycentric
+        // coordinate (the containing triangle; first in canonical order on a tie)
+        std::vector<int> top;
+        const size_t nst = surf.size() / 3;
+        for (size_t k = 0; k < nst; ++k) {
+            const int* f = &surf[3 * k];
+            if (rest[3 * f[0] + 2] == ztop && rest[3 * f[1] + 2] == ztop && rest[3 * f[2] + 2] == ztop)
+                top.push_back(static_cast<int>(k));
+        }
+        for (int m = 0; m < nm; ++m) {
+            double qx = markers[2 * m], qy = markers[2 * m + 1];
+            double best = -1e300, bw[3] = {0, 0, 0};
+            int bk = -1;
+            for (int k : top) {
+                const int* f = &surf[3 * static_cast<size_t>(k)];
+                double ax = rest[3 * f[0]], ay = rest[3 * f[0] + 1];
+                double v0x = rest[3 * f[1]] - ax, v0y = rest[3 * f[1] + 1] - ay;
+                double v1x = rest[3 * f[2]] - ax, v1y = rest[3 * f[2] + 1] - ay;
+                double v2x = qx - ax, v2y = qy - ay;
+                double den = v0x * v1y - v1x * v0y;
+                double l1 = (v2x * v1y - v1x * v2y) / den;
+                double l2 = (v0x * v2y - v2x * v0y) / den;
+                double l0 = 1.0 - l1 - l2;
+                double sc = std::min(l0, std::min(l1, l2));
+                if (sc > best) {
+                    best = sc;
+                    bk = k;
+                    bw[0] = l0;
+                    bw[1] = l1;
+                    bw[2] = l2;
+                }
+            }
+            if (bk < 0 || best < -1e-9) {
+                std::snprintf(msgbuf, sizeof msgbuf, "marker %d is not on the top face", m);
+                err = msgbuf;
+                return false;
+            }
+            for (int r = 0; r < 3; ++r) {
+                ids[kMarkerSlots * m + r] = surf[3 * static_cast<size_t>(bk) + r];
+                w[kMarkerSlots * m + r] = static_cast<float>(bw[r]);
+            }
+            ids[kMarkerSlots * m + 3] = ids[kMarkerSlots * m];   // weight 0
+        }
+        return true;
+    }
+    // kNN inverse distance (Sec. 3.2): the kMarkerSlots top-face nodes nearest
+    // to the marker in the face's 2-D distance, ranked by (dx^2 + dy^2, id);
+    // weights 1/d normalised in rank order; a node at distance 0 takes all
+    std::vector<int> top;
+    for (int i = 0; i < nv; ++i)
+        if (rest[3 * i + 2] == ztop) top.push_back(i);
+    if (static_cast<int>(top.size()) < kMarkerSlots) {
+        err = "fewer top-face nodes than marker neighbours";
+        return false;
+    }
+    std::vector<std::pair<double, int>> key(top.size());
+    for (int m = 0; m < nm; ++m) {
+        double qx = markers[2 * m], qy = markers[2 * m + 1];
+        for (size_t k = 0; k < top.size(); ++k) {
+            int i = top[k];
+            double dx = static_cast<double>(rest[3 * i]) - qx, dy = static_cast<double>(rest[3 * i + 1]) - qy;
+            key[k] = {dx * dx + dy * dy, i};
+        }
+        std::partial_sort(key.begin(), key.begin() + kMarkerSlots, key.end());
+        double inv[kMarkerSlots], sum = 0.0;
+        bool on_node = key[0].first == 0.0;
+        for (int r = 0; r < kMarkerSlots; ++r) {
+            ids[kMarkerSlots * m + r] = key[r].second;
+            inv[r] = on_node ? 0.0 : 1.0 / std::sqrt(key[r].first);
+            sum += inv[r];
+        }
+        for (int r = 0; r < kMarkerSlots; ++r)
+            w[kMarkerSlots * m + r] = on_node ? (r == 0 ? 1.0f : 0.0f) : static_cast<float>(inv[r] / sum);
+    }
+    return true;
+}
+
 bool build_pad_mesh(int nv, int nt, int nf, int nm, const float* rest, const int* tets,
-                    const int* fixed, const float* markers, PadMesh& M, std::string& err) {
+                    const int* fixed, const float* markers, int marker_mode, PadMesh& M, std::string& err) {
     if (nv <= 0 || nt <= 0 || nf < 0 || nm < 0 || !rest || !tets || (nf && !fixed) || (nm && !markers)) {
         err = "pad descriptor has a non-positive size or a null array";
         return false;
@@ -157,50 +246,7 @@ bool build_pad_mesh(int nv, int nt, int nf, int nm, const float* rest, const int
     std::sort(M.sv.begin(), M.sv.end());
     M.sv.erase(std::unique(M.sv.begin(), M.sv.end()), M.sv.end());
 
-    // markers: top-face triangle maximising the smallest barycentric coordinate
-    float ztop = rest[2];
-    for (int i = 0; i < nv; ++i) ztop = std::max(ztop, rest[3 * i + 2]);
-    std::vector<int> top;
-    for (size_t k = 0; k < surf.size(); ++k) {
-        const auto& f = surf[k];
-        if (rest[3 * f[0] + 2] == ztop && rest[3 * f[1] + 2] == ztop && rest[3 * f[2] + 2] == ztop)
-            top.push_back(static_cast<int>(k));
-    }
-    M.mk_ids.assign(3 * static_cast<size_t>(nm), 0);
-    M.mk_w.assign(3 * static_cast<size_t>(nm), 0.0f);
-    for (int m = 0; m < nm; ++m) {
-        double qx = markers[2 * m], qy = markers[2 * m + 1];
-        double best = -1e300, bw[3] = {0, 0, 0};
-        int bk = -1;
-        for (int k : top) {
-            const auto& f = surf[k];
-            double ax = rest[3 * f[0]], ay = rest[3 * f[0] + 1];
-            double v0x = rest[3 * f[1]] - ax, v0y = rest[3 * f[1] + 1] - ay;
-            double v1x = rest[3 * f[2]] - ax, v1y = rest[3 * f[2] + 1] - ay;
-            double v2x = qx - ax, v2y = qy - ay;
-            double den = v0x * v1y - v1x * v0y;
-            double l1 = (v2x * v1y - v1x * v2y) / den;
-            double l2 = (v0x * v2y - v2x * v0y) / den;
-            double l0 = 1.0 - l1 - l2;
-            double sc = std::min(l0, std::min(l1, l2));
-            if (sc > best) {
-                best = sc;
-                bk = k;
-                bw[0] = l0;
-                bw[1] = l1;
-                bw[2] = l2;
-            }
-        }
-        if (bk < 0 || best < -1e-9) {
-            std::snprintf(msgbuf, sizeof msgbuf, "marker %d is not on the top face", m);
-            err = msgbuf;
-            return false;
-        }
-        for (int r = 0; r < 3; ++r) {
-            M.mk_ids[3 * m + r] = surf[bk][r];
-            M.mk_w[3 * m + r] = static_cast<float>(bw[r]);
-        }
-    }
+    if (!build_marker_map(nv, rest, M.st, nm, markers, marker_mode, M.mk_ids, M.mk_w, err)) return false;
 
     // Morton codes on the rest bounding box (10 bits per axis)
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};

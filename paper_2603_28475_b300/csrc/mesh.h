@@ -40,8 +40,8 @@ struct PadMesh {
     std::vector<int> se;              // [n_se*2] surface edges, canonical order of the input ids
     double lbar = 0.0;                // mean rest surface edge length
     // markers
-    std::vector<int> mk_ids;          // [n_mk*3]
-    std::vector<float> mk_w;          // [n_mk*3]
+    std::vector<int> mk_ids;          // [n_mk*kMarkerSlots]
+    std::vector<float> mk_w;          // [n_mk*kMarkerSlots]
     int n_patch() const { return static_cast<int>(patch.size() / 4); }
     int n_slots() const { return n_patch() * kPatchTets; }
     int n_colour() const { return static_cast<int>(colour_off.size()) - 1; }
@@ -54,10 +54,18 @@ struct IndenterMesh {
     std::vector<int> edges;           // [n_e*2] distinct (lo, hi), sorted
 };
 
-// Builds a pad; returns false with a message on invalid input.
+// Builds a pad; returns false with a message on invalid input. marker_mode
+// selects the marker map (0 barycentric on the top face, 1 kNN inverse
+// distance over the top-face nodes).
 bool build_pad_mesh(int n_verts, int n_tets, int n_fixed, int n_markers, const float* rest,
-                    const int* tets, const int* fixed, const float* markers, PadMesh& out,
-                    std::string& err);
+                    const int* tets, const int* fixed, const float* markers, int marker_mode,
+                    PadMesh& out, std::string& err);
+
+// The marker map alone, in input vertex ids: ids/w [n_markers*kMarkerSlots].
+// surf: canonical surface triangles (input ids), used by the barycentric map.
+bool build_marker_map(int n_verts, const float* rest, const std::vector<int>& surf, int n_markers,
+                      const float* markers, int marker_mode, std::vector<int>& ids, std::vector<float>& w,
+                      std::string& err);
 
 bool build_indenter_mesh(int n_verts, int n_tris, const float* verts, const int* tris,
                          IndenterMesh& out, std::string& err);

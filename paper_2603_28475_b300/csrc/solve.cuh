@@ -44,6 +44,7 @@ struct PadDev {
     int mk_out;               // marker output offset (markers)
     float mu, lam, rho, h, dhat, kappa, mu_f, eps_v, g_ref, tol, tol_adv;
     int max_iter, precond;
+    int step;                 // 0: alpha bounded by CCD + Armijo test; 1: Eq. (step_size) as printed
 };
 
 struct LagRec {
@@ -80,8 +81,8 @@ struct Dev {
     const int* sv;
     const int* st;            // [n*3]
     const int* se;            // [n*2]
-    const int* mk_ids;        // [n*3]
-    const float* mk_w;        // [n*3]
+    const int* mk_ids;        // [n*kMarkerSlots]
+    const float* mk_w;        // [n*kMarkerSlots]
     // indenters
     const float* Y;           // [n*3] local
     const int* it;            // [n*3]

@@ -23,7 +23,7 @@ SYMBOLS = ("tac_create_batch", "tac_destroy_batch", "tac_reset", "tac_set_indent
            "tac_get_state", "tac_set_state", "tac_set_params", "tac_get_params", "tac_broadphase",
            "tac_broadphase_static",
            "tac_debug_eval", "tac_stats",
-           "tac_pad_norms", "tac_sizes", "tac_last_error")
+           "tac_pad_norms", "tac_sizes", "tac_marker_map", "tac_last_error")
 
 
 class PadDesc(ctypes.Structure):
@@ -41,7 +41,8 @@ class Params(ctypes.Structure):
     _fields_ = [("E", ctypes.c_float), ("nu", ctypes.c_float), ("rho", ctypes.c_float), ("h", ctypes.c_float),
                 ("dhat", ctypes.c_float), ("kappa", ctypes.c_float), ("mu_f", ctypes.c_float),
                 ("eps_v", ctypes.c_float), ("tol_rel_grad", ctypes.c_float), ("tol_advance", ctypes.c_float),
-                ("max_iter", ctypes.c_int), ("precond_mode", ctypes.c_int)]
+                ("max_iter", ctypes.c_int), ("precond_mode", ctypes.c_int), ("step_mode", ctypes.c_int),
+                ("marker_mode", ctypes.c_int)]
 
 
 class Options(ctypes.Structure):
@@ -75,6 +76,7 @@ def load_library(path=_LIB_PATH):
         "tac_stats": [vp, vp, vp],
         "tac_pad_norms": [vp, vp, vp],
         "tac_sizes": [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)],
+        "tac_marker_map": [ctypes.POINTER(PadDesc), i, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -113,9 +115,28 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def make_params(mat, tol=1e-6, tol_advance=1e-2, max_iter=10000, precond=0, kappa=0.0, eps_v=0.0):
+def make_params(mat, tol=1e-6, tol_advance=1e-2, max_iter=10000, precond=0, kappa=0.0, eps_v=0.0, step=0, marker=0):
+    """tac_params of one pad. precond: 0 block Jacobi, 1 scalar Jacobi;
+    step: 0 bounded (CCD + Armijo), 1 Eq. (step_size) as printed; marker: 0
+    barycentric, 1 kNN inverse distance."""
     return Params(E=mat.E, nu=mat.nu, rho=mat.rho, h=mat.h, dhat=mat.dhat, kappa=kappa, mu_f=mat.mu_f,
-                  eps_v=eps_v, tol_rel_grad=tol, tol_advance=tol_advance, max_iter=max_iter, precond_mode=precond)
+                  eps_v=eps_v, tol_rel_grad=tol, tol_advance=tol_advance, max_iter=max_iter, precond_mode=precond,
+                  step_mode=step, marker_mode=marker)
+
+
+def marker_map(pad, marker_mode=0):
+    """The library's marker map of one pad (host only): (ids [M, 4] input
+    vertex ids, weights [M, 4] float32)."""
+    rest = np.ascontiguousarray(pad.rest, dtype=np.float32)
+    tets = np.ascontiguousarray(pad.tets, dtype=np.int32)
+    fixed = np.ascontiguousarray(pad.fixed, dtype=np.int32)
+    mk = np.ascontiguousarray(pad.markers, dtype=np.float32)
+    d = PadDesc(rest.shape[0], tets.shape[0], fixed.shape[0], mk.shape[0], rest.ctypes.data, tets.ctypes.data,
+                fixed.ctypes.data if fixed.size else 0, mk.ctypes.data if mk.size else 0)
+    ids = np.zeros((mk.shape[0], 4), dtype=np.int32)
+    w = np.zeros((mk.shape[0], 4), dtype=np.float32)
+    _check(lib().tac_marker_map(ctypes.byref(d), int(marker_mode), ids.ctypes.data, w.ctypes.data))
+    return ids, w
 
 
 class TacBatch:
@@ -330,8 +351,8 @@ def broadphase_static(x, surf_verts, surf_tris, surf_edges, y, ind_tris, ind_edg
 
 
 def batch_from_workload(w, tol=1e-6, tol_advance=1e-2, max_iter=10000, precond=0, pair_capacity=0,
-                        share_meshes=True, stream=None):
-    params = [make_params(m, tol=tol, tol_advance=tol_advance, max_iter=max_iter, precond=precond)
-              for m in w.materials]
+                        share_meshes=True, stream=None, step=0, marker=0):
+    params = [make_params(m, tol=tol, tol_advance=tol_advance, max_iter=max_iter, precond=precond, step=step,
+                          marker=marker) for m in w.materials]
     return TacBatch(w.pads, params, w.indenters, w.pads_per_env, pair_capacity=pair_capacity,
                     share_meshes=share_meshes, stream=stream)
