@@ -39,8 +39,10 @@ UNIT = "env-frames/s"
 # corner slots (8 B) once, and per patch vertex the displacement (hi, lo) and
 # the direction (36 B) and, averaged over the two pass kinds, writes the
 # gradient and diagonal block (36 B / 2); a vertex pass moves ~120 B per
-# vertex; a pair evaluation ~64 B per candidate pair.
+# vertex; a pair evaluation ~64 B per candidate pair. A mesh with a Dm^-1
+# table (the structured case) reads no per-tet Dm^-1.
 B_TET = 48.0
+B_DM = 36.0
 B_TET_VERT = 36.0 + 18.0
 B_VERT_PASS = 120.0
 B_PAIR = 64.0
@@ -63,6 +65,8 @@ def parse():
     ap.add_argument("--adjoint-frames", type=int, default=16)
     ap.add_argument("--sweep", action="store_true",
                     help="throughput over env counts and pad sizes (the large-scale sweep) instead")
+    ap.add_argument("--no-dm-table", action="store_true",
+                    help="stream one Dm^-1 per tet even for structured meshes (the unstructured form)")
     ap.add_argument("--variants", action="store_true",
                     help="iterations and throughput of the paper-literal variants on the batched workload instead")
     return ap.parse_args()
@@ -139,12 +143,27 @@ def workload(envs, frames, seed):
     return S.config_batched(n_envs=envs, frames=frames, seed=seed)
 
 
-def algorithmic_bytes(stats, w):
+_TABLED = {}
+
+
+def tabled(pad, dm_table=True):
+    """Whether the library reads this pad's rest shapes from a Dm^-1 table."""
+    if not dm_table:
+        return False
+    key = id(pad.tets)
+    if key not in _TABLED:
+        from paper_2603_28475_b300 import tac
+        _TABLED[key] = tac.mesh_info(pad)["dm_types"] > 0
+    return _TABLED[key]
+
+
+def algorithmic_bytes(stats, w, dm_table=True):
     """Counted bytes of one solve launch from the per-pad counters."""
     tot = 0.0
     for k, pad in enumerate(w.pads):
         it, sub, reb, hal, tp, vp, pe, peak = [float(v) for v in stats[k][:8]]
-        tot += tp * (B_TET * pad.n_tets + B_TET_VERT * pad.n_verts) + vp * B_VERT_PASS * pad.n_verts + pe * B_PAIR
+        bt = B_TET - (B_DM if tabled(pad, dm_table) else 0.0)
+        tot += tp * (bt * pad.n_tets + B_TET_VERT * pad.n_verts) + vp * B_VERT_PASS * pad.n_verts + pe * B_PAIR
     return tot
 
 
@@ -237,7 +256,7 @@ def run_ours(args, rank, world):
     w = workload(args.envs, 2 * frames + 1, args.seed + 1000 * rank)
     n_pads = w.n_pads
     t0 = time.time()
-    b = tac.batch_from_workload(w, pair_capacity=args.pair_capacity)
+    b = tac.batch_from_workload(w, pair_capacity=args.pair_capacity, dm_table=not args.no_dm_table)
     t_create = time.time() - t0
     stream = torch.cuda.current_stream()
     poses = torch.tensor(w.poses, dtype=torch.float32, device=dev)      # [F+1, n_pads, 6]
@@ -283,7 +302,7 @@ def run_ours(args, rank, world):
         conv += int(np.all(s_np == 0, axis=1).sum())
         iter_hist.append(it.cpu().numpy())
         st_np = st.cpu().numpy()
-        bytes_alg += algorithmic_bytes(st_np, w)
+        bytes_alg += algorithmic_bytes(st_np, w, not args.no_dm_table)
         phase += st_np[:, 8:16].sum(axis=0)
         pad_ms_max = max(pad_ms_max, float(st_np[:, 15].max()) / 1e6)
     names = ["tet_pHp", "tet_grad", "pair_pHp", "pair_grad", "vertex", "advance_rebuild", "setup"]
@@ -354,6 +373,7 @@ def run_ours(args, rank, world):
                           "total_verts": b.total_verts, "total_tets": int(sum(p.n_tets for p in w.pads)),
                           "frames": f"{args.warmup + 1}..{args.warmup + args.steps} of a 0.05 mm/frame press",
                           "tol_rel_grad": 1e-6, "friction": 0.5,
+                          "rest_shapes": "per-tet Dm^-1" if args.no_dm_table else "Dm^-1 table (structured meshes)",
                           "l2": f"inputs larger than L2 (solver state {v_state:.1f} GB)",
                           "parallelism": f"{world} rank(s), env-sharded"},
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

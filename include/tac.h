@@ -113,10 +113,19 @@ typedef struct {
 
 /* Batch options. pair_capacity: candidate pairs stored per pad (0 = 16384).
  * share_meshes: pads whose tac_pad_desc points at the same host arrays share
- * one device copy of the static mesh data (1) or each get their own (0). */
+ * one device copy of the static mesh data (1) or each get their own (0).
+ * no_dm_table: 0 (default) lets a mesh whose tets fall into at most 32
+ * rest-shape classes (Dm^-1 equal within 1e-5 of their largest entry; a
+ * regular hex-split grid has 6, one per tet of the cell split: the
+ * structured-mesh case) read each tet's Dm^-1 from a per-mesh table of class
+ * representatives instead of streaming one per tet; 1 always streams the
+ * exact per-tet Dm^-1. The kernels form F = I + Du Dm^-1 from displacements,
+ * so the table leaves the rest state exact and changes the strain of a
+ * deformed tet by at most the class tolerance, relatively. */
 typedef struct {
     int pair_capacity;
     int share_meshes;
+    int no_dm_table;
 } tac_options;
 
 /* Create a batch of n_pads pads, pads_per_env consecutive pads per
@@ -317,6 +326,16 @@ int tac_pad_norms(tac_handle h, double* norms_dev, void* stream);
  * (TAC_ERR_INVALID_MESH with a message). tac_markers and the adjoint's
  * right-hand side read the pads through this map. */
 int tac_marker_map(const tac_pad_desc* pad, int marker_mode, int* ids_host, float* w_host);
+
+/* Host only (no device work, no handle): how tac_create_batch lays out this
+ * pad's mesh: the number of 32-tet warp patches, of colour classes (patches
+ * of one class share no vertex), of rest-shape classes in its Dm^-1 table
+ * (0 when the mesh needs more than 32 and streams one Dm^-1 per tet; see
+ * tac_options.no_dm_table), and the largest deviation of a tet's Dm^-1 from
+ * its class representative, relative to the representative's largest entry
+ * (at most 1e-5 by construction). Any output pointer may be NULL. Validates
+ * the mesh like tac_create_batch (TAC_ERR_INVALID_MESH with a message). */
+int tac_mesh_info(const tac_pad_desc* pad, int* n_patches, int* n_colours, int* n_dm_types, double* dm_dev);
 
 /* Sizes: total vertices, total markers, candidate capacity per pad, and the
  * number of CTAs of one tac_step launch (resident CTAs of the device, at most

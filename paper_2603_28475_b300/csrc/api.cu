@@ -239,6 +239,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     b->hstep.assign(n_pads, 0.f);
     int cap = (opts && opts->pair_capacity > 0) ? opts->pair_capacity : 16384;
     bool share = !opts || opts->share_meshes != 0;
+    bool dm_tab = !opts || opts->no_dm_table == 0;
     b->pair_cap = cap;
     cudaGetDevice(&b->device);
     // host meshes (dedup by identical host arrays when sharing)
@@ -261,6 +262,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
             delete b;
             return fail(TAC_ERR_INVALID_MESH, "pad " + std::to_string(p) + ": " + err);
         }
+        if (dm_tab) build_dm_table(M);
         int id = (int)b->meshes.size();
         b->meshes.push_back(std::move(M));
         b->pad_mesh.push_back(id);
@@ -288,7 +290,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     }
     // layouts
     int XVt = 0, Tt = 0, pv_tot = 0, pc_tot = 0, sv_tot = 0, st_tot = 0, se_tot = 0, mk_tot = 0;
-    int col_tot = 0;
+    int col_tot = 0, dm_tot = 0;
     for (auto& M : b->meshes) {
         MeshDev md{};
         md.xv_off = XVt; md.n_v = M.n_v;
@@ -300,6 +302,8 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
         md.se_off = se_tot; md.n_se = (int)(M.se.size() / 2);
         md.mk_off = mk_tot; md.n_mk = M.n_mk;
         md.col_off = col_tot; md.n_col = M.n_colour();
+        md.dm_off = dm_tot; md.n_dm = M.n_dm_types();
+        dm_tot += md.n_dm;
         col_tot += (int)M.colour_off.size();
         XVt += M.n_v; Tt += M.n_slots(); pv_tot += (int)M.pvert.size();
         pc_tot += (int)M.pcsr.size(); sv_tot += md.n_sv; st_tot += md.n_st; se_tot += md.n_se; mk_tot += M.n_mk;
@@ -361,6 +365,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     float* wdiag = dalloc<float>(K, XVt, rc);
     uint8_t* fixed = dalloc<uint8_t>(K, XVt, rc);
     float* B = dalloc<float>(K, 9 * (size_t)Tt, rc);
+    float* dm_table = dalloc<float>(K, 9 * (size_t)dm_tot, rc);
     uint32_t* lconn = dalloc<uint32_t>(K, Tt, rc);
     uint32_t* slot = dalloc<uint32_t>(K, Tt, rc);
     int* pvert = dalloc<int>(K, pv_tot, rc);
@@ -428,6 +433,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     std::vector<int> hcol;
     std::vector<int> hpv, hsv, hst, hse, hmki, hit, hie;
     std::vector<uint16_t> hpc;
+    std::vector<float> hdm;
     for (size_t m = 0; m < b->meshes.size(); ++m) {
         const PadMesh& M = b->meshes[m];
         const MeshDev& md = b->hmesh[m];
@@ -439,8 +445,12 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
             hvu[md.xv_off + i] = M.vuser[i];
         }
         const int ns = M.n_slots();
+        // a tabled mesh's per-tet Dm^-1 stays zero on the device: nothing reads it
+        const bool tabled = md.n_dm > 0;
+        hdm.insert(hdm.end(), M.dm_table.begin(), M.dm_table.end());
         for (int t = 0; t < ns; ++t) {
-            for (int e = 0; e < 9; ++e) hB[(size_t)e * Tt + md.tet_off + t] = M.B[(size_t)e * ns + t];
+            if (!tabled)
+                for (int e = 0; e < 9; ++e) hB[(size_t)e * Tt + md.tet_off + t] = M.B[(size_t)e * ns + t];
             hlc[md.tet_off + t] = M.lconn[t];
             hsl[md.tet_off + t] = M.slot[t];
         }
@@ -468,6 +478,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     r2 |= up(vlump, hvl.data(), hvl.size() * 4);
     r2 |= up(fixed, hfx.data(), hfx.size());
     r2 |= up(B, hB.data(), hB.size() * 4);
+    r2 |= up(dm_table, hdm.data(), hdm.size() * 4);
     r2 |= up(lconn, hlc.data(), hlc.size() * 4);
     r2 |= up(slot, hsl.data(), hsl.size() * 4);
     r2 |= up(colour, hcol.data(), hcol.size() * 4);
@@ -511,7 +522,7 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     D.envs = b->d_envs;
     D.pads = b->d_pads;
     D.order = order_d;
-    D.X = X; D.vlump = vlump; D.wdiag = wdiag; D.fixed = fixed; D.vuser = vuser; D.B = B; D.lconn = lconn; D.slot = slot; D.colour = colour;
+    D.X = X; D.vlump = vlump; D.wdiag = wdiag; D.fixed = fixed; D.vuser = vuser; D.B = B; D.dm_table = dm_table; D.lconn = lconn; D.slot = slot; D.colour = colour;
     D.pvert = pvert; D.pcsr = pcsr; D.sv = sv; D.st = stt; D.se = se;
     D.mk_ids = mk_ids; D.mk_w = mk_w; D.Y = Y; D.it = it; D.ie = ie; D.Yt = Yt; D.Yn = Yn;
     D.pose_t = b->d_pose_t; D.pose_n = b->d_pose_n; D.pose_s = b->d_pose_s;
@@ -729,6 +740,21 @@ int tac_marker_map(const tac_pad_desc* pad, int marker_mode, int* ids_host, floa
         ids_host[k] = M.vuser[M.mk_ids[k]];
         w_host[k] = M.mk_w[k];
     }
+    return TAC_OK;
+}
+
+int tac_mesh_info(const tac_pad_desc* pad, int* n_patches, int* n_colours, int* n_dm_types, double* dm_dev) {
+    if (!pad) return fail(TAC_ERR_INVALID_ARG, "null argument");
+    PadMesh M;
+    std::string err;
+    if (!build_pad_mesh(pad->n_verts, pad->n_tets, pad->n_fixed, pad->n_markers, pad->rest_xyz, pad->tets,
+                        pad->fixed_idx, pad->marker_xy, 0, M, err))
+        return fail(TAC_ERR_INVALID_MESH, err);
+    build_dm_table(M);
+    if (n_patches) *n_patches = M.n_patch();
+    if (n_colours) *n_colours = M.n_colour();
+    if (n_dm_types) *n_dm_types = M.n_dm_types();
+    if (dm_dev) *dm_dev = M.dm_dev;
     return TAC_OK;
 }
 

@@ -82,6 +82,7 @@ struct Shared {
     int flag;
     int expired;
     int fok;                    // D.fcache holds the float64 features of the current point and pair set
+    float dm[kMaxDmTypes * 9];  // the current pad's Dm^-1 table (meshes with n_dm > 0)
 };
 
 // one CTA-wide scratch object (dynamic shared memory, sizeof(Shared) bytes at
@@ -146,6 +147,11 @@ __device__ __forceinline__ void load_pad(const Dev& D, int pad) {
         S.fok = 0;
     }
     __syncthreads();
+    const int ndm = S.M.n_dm;
+    if (ndm > 0) {
+        for (int i = threadIdx.x; i < 9 * ndm; i += blockDim.x) S.dm[i] = D.dm_table[9 * S.M.dm_off + i];
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -430,12 +436,14 @@ __device__ __forceinline__ TetPtrs tet_ptrs(const Dev& D, const PadDev& P, const
 // The scatter passes also copy the vertex's sums so far when this is not its
 // first patch: patches of one colour class share no vertex and earlier
 // classes are complete, so those sums are final when the copy is issued.
-template <int PASS>
+template <int PASS, bool TAB>
 __device__ __forceinline__ void issue_patch(const TetPtrs& T, int pi, int gvf, PatchStage& st, int lane) {
     {
         size_t t = (size_t)kPatchTets * pi + lane;
+        if (!TAB) {
 #pragma unroll
-        for (int e = 0; e < 9; ++e) cp_async4(&st.B[e][lane], T.B + (size_t)e * T.Tt + t);
+            for (int e = 0; e < 9; ++e) cp_async4(&st.B[e][lane], T.B + (size_t)e * T.Tt + t);
+        }
         cp_async4(&st.lc[lane], T.lc + t);
         cp_async4(&st.sl[lane], T.sl + t);
     }
@@ -475,8 +483,8 @@ __device__ __forceinline__ int patch_vert(const TetPtrs& T, int pi, int lane) {
 // class. Passes that scatter walk the colour classes in order with one CTA
 // barrier between classes (patches of one class share no vertex); the
 // reduction passes walk all patches without any.
-template <int PASS>
-__device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, int gb) {
+template <int PASS, bool TAB>
+__device__ __noinline__ TetOut tet_pass_impl(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, int gb) {
     TetOut out{0.0, 0, 0.f, 0.0};
     FSum acc{0.f, 0.f}, acc2{0.f, 0.f};
     const int tid = threadIdx.x;
@@ -498,7 +506,7 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
         int gvf_c = -1, gvf_n = -1;
         if (pi < p_end) {
             gvf_c = patch_vert(T, pi, lane);
-            issue_patch<PASS>(T, pi, gvf_c, W.st[0], lane);
+            issue_patch<PASS, TAB>(T, pi, gvf_c, W.st[0], lane);
             if (pi + kWarps < p_end) gvf_n = patch_vert(T, pi + kWarps, lane);
         }
         while (pi < p_end) {
@@ -512,16 +520,23 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
             }
             int gvf_nn = -1;
             if (pn < p_end) {
-                issue_patch<PASS>(T, pn, gvf_n, W.st[b ^ 1], lane);
+                issue_patch<PASS, TAB>(T, pn, gvf_n, W.st[b ^ 1], lane);
                 if (pn + kWarps < p_end) gvf_nn = patch_vert(T, pn + kWarps, lane);
             }
             const PatchStage& st = W.st[b];
             const uint32_t lc = st.lc[lane];
             if (lc != kNoTet) {
-                int l0 = lc & 255, l1 = (lc >> 8) & 255, l2 = (lc >> 16) & 255, l3 = lc >> 24;
+                int l0 = lc & kLocalMask, l1 = (lc >> 8) & kLocalMask, l2 = (lc >> 16) & kLocalMask,
+                    l3 = (lc >> 24) & kLocalMask;
                 float Bm[9];
+                if (TAB) {
+                    const float* bt = S.dm + 9 * dm_type_of(lc);
     #pragma unroll
-                for (int e = 0; e < 9; ++e) Bm[e] = st.B[e][lane];
+                    for (int e = 0; e < 9; ++e) Bm[e] = bt[e];
+                } else {
+    #pragma unroll
+                    for (int e = 0; e < 9; ++e) Bm[e] = st.B[e][lane];
+                }
                 float Du[9], Dp[9];
     #pragma unroll
                 for (int r = 0; r < 3; ++r) {
@@ -712,6 +727,13 @@ __device__ __noinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const Mes
     block_max_f<1>(fm);
     out.fmax = fm[0];
     return out;
+}
+
+// the pass for a mesh with a Dm^-1 table (the tets' rest shapes come from
+// shared memory) or with per-tet Dm^-1 (streamed with the patch)
+template <int PASS>
+__device__ __forceinline__ TetOut tet_pass(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, int gb) {
+    return M.n_dm > 0 ? tet_pass_impl<PASS, true>(D, P, M, alpha, gb) : tet_pass_impl<PASS, false>(D, P, M, alpha, gb);
 }
 
 // ---------------------------------------------------------------------------

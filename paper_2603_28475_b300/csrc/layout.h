@@ -11,6 +11,12 @@
 
 #include <cstdint>
 
+#if defined(__CUDACC__)
+#define TAC_HD __host__ __device__
+#else
+#define TAC_HD
+#endif
+
 namespace tac {
 
 constexpr int kPatchTets = 32;
@@ -21,6 +27,19 @@ constexpr uint32_t kNoTet = 0xffffffffu;
 // Marker map: every marker reads kMarkerSlots weighted mesh vertices (a
 // barycentric map fills three and gives the fourth weight 0).
 constexpr int kMarkerSlots = 4;
+
+// Rest-shape table: a mesh with at most kMaxDmTypes distinct Dm^-1 (a regular
+// hex-split grid has 6, one per tet of the cell split) keeps them in a table
+// and tags each tet with its table index in the spare high bits of its local
+// vertex ids (3 bits of byte 0, 2 bits of byte 1; local ids take 5 bits).
+constexpr int kMaxDmTypes = 32;
+constexpr uint32_t kLocalMask = 31u;
+TAC_HD inline uint32_t dm_type_bits(int t) {
+    return (static_cast<uint32_t>(t & 7) << 5) | (static_cast<uint32_t>((t >> 3) & 3) << 13);
+}
+TAC_HD inline int dm_type_of(uint32_t lc) {
+    return static_cast<int>(((lc >> 5) & 7u) | (((lc >> 13) & 3u) << 3));
+}
 
 // Flags carried in the high bits of a patch's vertex entry (entries >= 0).
 constexpr int kFirstFlag = 1 << 30;   // first patch (in processing order) touching the vertex

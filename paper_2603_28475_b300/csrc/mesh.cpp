@@ -5,6 +5,7 @@
 #include <array>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <numeric>
 
 namespace tac {
@@ -128,6 +129,49 @@ bool build_marker_map(int nv, const float* rest, const std::vector<int>& surf, i
         for (int r = 0; r < kMarkerSlots; ++r)
             w[kMarkerSlots * m + r] = on_node ? (r == 0 ? 1.0f : 0.0f) : static_cast<float>(inv[r] / sum);
     }
+    return true;
+}
+
+bool build_dm_table(PadMesh& M) {
+    // greedy classes in slot order: a tet joins the first class whose
+    // representative (its first member's Dm^-1) agrees with its own entry by
+    // entry within kDmTableTol of the representative's largest entry
+    const size_t ns = static_cast<size_t>(M.n_slots());
+    std::vector<std::array<float, 9>> rep;
+    std::vector<float> rep_scale;
+    std::vector<int> tag(ns, -1);
+    double dev = 0.0;
+    for (size_t t = 0; t < ns; ++t) {
+        if (M.lconn[t] == kNoTet) continue;
+        std::array<float, 9> b;
+        for (int e = 0; e < 9; ++e) b[e] = M.B[e * ns + t];
+        int found = -1;
+        double fdev = 0.0;
+        for (size_t k = 0; k < rep.size() && found < 0; ++k) {
+            double worst = 0.0;
+            for (int e = 0; e < 9; ++e) worst = std::max(worst, std::fabs(static_cast<double>(b[e]) - rep[k][e]));
+            if (worst <= kDmTableTol * rep_scale[k]) {
+                found = static_cast<int>(k);
+                fdev = worst / rep_scale[k];
+            }
+        }
+        if (found < 0) {
+            if (static_cast<int>(rep.size()) == kMaxDmTypes) return false;
+            float sc = 0.f;
+            for (int e = 0; e < 9; ++e) sc = std::max(sc, std::fabs(b[e]));
+            rep.push_back(b);
+            rep_scale.push_back(sc);
+            found = static_cast<int>(rep.size()) - 1;
+        }
+        dev = std::max(dev, fdev);
+        tag[t] = found;
+    }
+    M.dm_table.assign(9 * rep.size(), 0.0f);
+    for (size_t k = 0; k < rep.size(); ++k)
+        for (int e = 0; e < 9; ++e) M.dm_table[9 * k + e] = rep[k][e];
+    for (size_t t = 0; t < ns; ++t)
+        if (tag[t] >= 0) M.lconn[t] |= dm_type_bits(tag[t]);
+    M.dm_dev = dev;
     return true;
 }
 

@@ -27,6 +27,9 @@ struct PadMesh {
     std::vector<uint8_t> fixed;       // [n_v] 1 = Dirichlet
     // tets in patch order, kPatchTets slots per patch
     std::vector<float> B;             // [9][n_slots] Dm^-1 (row-major entries), SoA
+    std::vector<float> dm_table;      // [n_types*9] rest-shape classes when there are at most
+                                      // kMaxDmTypes (then lconn carries each tet's class); empty otherwise
+    double dm_dev = 0.0;              // largest entry deviation of a tet from its class (relative)
     std::vector<uint32_t> lconn;      // [n_slots] 4 x 8-bit local vertex ids (kNoTet: unused slot)
     std::vector<uint32_t> slot;       // [n_slots] 4 x 8-bit corner slots in the patch CSR
     std::vector<int> patch;           // [n_patch*4] tet_begin, vert_begin, n_t | n_v << 16, csr_begin (host)
@@ -42,6 +45,7 @@ struct PadMesh {
     // markers
     std::vector<int> mk_ids;          // [n_mk*kMarkerSlots]
     std::vector<float> mk_w;          // [n_mk*kMarkerSlots]
+    int n_dm_types() const { return static_cast<int>(dm_table.size() / 9); }
     int n_patch() const { return static_cast<int>(patch.size() / 4); }
     int n_slots() const { return n_patch() * kPatchTets; }
     int n_colour() const { return static_cast<int>(colour_off.size()) - 1; }
@@ -60,6 +64,19 @@ struct IndenterMesh {
 bool build_pad_mesh(int n_verts, int n_tets, int n_fixed, int n_markers, const float* rest,
                     const int* tets, const int* fixed, const float* markers, int marker_mode,
                     PadMesh& out, std::string& err);
+
+// Groups the tet slots into rest-shape classes: Dm^-1 that agree entry by
+// entry within kDmTableTol of the class representative's largest entry (a
+// regular grid whose float32 coordinates differ from exact multiples of the
+// cell size by rounding gives one class per tet of the cell split). With at
+// most kMaxDmTypes classes, fills dm_table with the representatives, tags
+// every slot's lconn with its class and returns true; otherwise leaves the
+// mesh unchanged and returns false. The kernels form F = I + Du Dm^-1 from
+// displacements, so a class representative perturbs the strain of a
+// deformed tet by at most that relative amount and leaves the rest state
+// exact.
+constexpr double kDmTableTol = 1e-5;
+bool build_dm_table(PadMesh& M);
 
 // The marker map alone, in input vertex ids: ids/w [n_markers*kMarkerSlots].
 // surf: canonical surface triangles (input ids), used by the barycentric map.

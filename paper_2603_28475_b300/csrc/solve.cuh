@@ -29,6 +29,7 @@ struct MeshDev {
     int pvert_off, pcsr_off;
     int sv_off, n_sv, st_off, n_st, se_off, n_se;
     int mk_off, n_mk;
+    int dm_off, n_dm;         // Dm^-1 table entries [dm_off, dm_off + n_dm) (n_dm = 0: per-tet B)
 };
 
 struct EnvDev {
@@ -71,7 +72,8 @@ struct Dev {
     const float* wdiag;       // [XVt] static diagonal of the elastic blocks / (h^2 mu)
     const uint8_t* fixed;     // [XVt]
     const int* vuser;         // [XVt] internal vertex -> input vertex id (mesh-local)
-    const float* B;           // [9][Tt], Tt = total tet slots
+    const float* B;           // [9][Tt], Tt = total tet slots (zero for meshes with a Dm^-1 table)
+    const float* dm_table;    // [sum n_dm * 9] distinct Dm^-1 of tabled meshes
     int Tt;
     const uint32_t* lconn;    // [Tt]
     const uint32_t* slot;     // [Tt] 4 x 8-bit corner slots

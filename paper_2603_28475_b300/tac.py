@@ -23,7 +23,7 @@ SYMBOLS = ("tac_create_batch", "tac_destroy_batch", "tac_reset", "tac_set_indent
            "tac_get_state", "tac_set_state", "tac_set_params", "tac_get_params", "tac_broadphase",
            "tac_broadphase_static",
            "tac_debug_eval", "tac_stats",
-           "tac_pad_norms", "tac_sizes", "tac_marker_map", "tac_last_error")
+           "tac_pad_norms", "tac_sizes", "tac_marker_map", "tac_mesh_info", "tac_last_error")
 
 
 class PadDesc(ctypes.Structure):
@@ -46,7 +46,7 @@ class Params(ctypes.Structure):
 
 
 class Options(ctypes.Structure):
-    _fields_ = [("pair_capacity", ctypes.c_int), ("share_meshes", ctypes.c_int)]
+    _fields_ = [("pair_capacity", ctypes.c_int), ("share_meshes", ctypes.c_int), ("no_dm_table", ctypes.c_int)]
 
 
 def load_library(path=_LIB_PATH):
@@ -77,6 +77,8 @@ def load_library(path=_LIB_PATH):
         "tac_pad_norms": [vp, vp, vp],
         "tac_sizes": [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)],
         "tac_marker_map": [ctypes.POINTER(PadDesc), i, vp, vp],
+        "tac_mesh_info": [ctypes.POINTER(PadDesc), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
+                          ctypes.POINTER(d)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -124,15 +126,30 @@ def make_params(mat, tol=1e-6, tol_advance=1e-2, max_iter=10000, precond=0, kapp
                   step_mode=step, marker_mode=marker)
 
 
+def _host_desc(pad):
+    arrs = (np.ascontiguousarray(pad.rest, dtype=np.float32), np.ascontiguousarray(pad.tets, dtype=np.int32),
+            np.ascontiguousarray(pad.fixed, dtype=np.int32), np.ascontiguousarray(pad.markers, dtype=np.float32))
+    rest, tets, fixed, mk = arrs
+    d = PadDesc(rest.shape[0], tets.shape[0], fixed.shape[0], mk.shape[0], rest.ctypes.data, tets.ctypes.data,
+                fixed.ctypes.data if fixed.size else 0, mk.ctypes.data if mk.size else 0)
+    return d, arrs
+
+
+def mesh_info(pad):
+    """Host-side layout of one pad's mesh: dict(patches, colours, dm_types,
+    dm_dev) (dm_types 0: per-tet Dm^-1; dm_dev: largest relative deviation
+    of a tet's Dm^-1 from its table class)."""
+    d, keep = _host_desc(pad)
+    a, b, c, e = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().tac_mesh_info(ctypes.byref(d), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(e)))
+    del keep
+    return {"patches": a.value, "colours": b.value, "dm_types": c.value, "dm_dev": e.value}
+
+
 def marker_map(pad, marker_mode=0):
     """The library's marker map of one pad (host only): (ids [M, 4] input
     vertex ids, weights [M, 4] float32)."""
-    rest = np.ascontiguousarray(pad.rest, dtype=np.float32)
-    tets = np.ascontiguousarray(pad.tets, dtype=np.int32)
-    fixed = np.ascontiguousarray(pad.fixed, dtype=np.int32)
-    mk = np.ascontiguousarray(pad.markers, dtype=np.float32)
-    d = PadDesc(rest.shape[0], tets.shape[0], fixed.shape[0], mk.shape[0], rest.ctypes.data, tets.ctypes.data,
-                fixed.ctypes.data if fixed.size else 0, mk.ctypes.data if mk.size else 0)
+    d, (rest, tets, fixed, mk) = _host_desc(pad)
     ids = np.zeros((mk.shape[0], 4), dtype=np.int32)
     w = np.zeros((mk.shape[0], 4), dtype=np.float32)
     _check(lib().tac_marker_map(ctypes.byref(d), int(marker_mode), ids.ctypes.data, w.ctypes.data))
@@ -147,7 +164,8 @@ class TacBatch:
     ``params``: list of ``Params``; ``indenters``: list of objects with
     verts/tris (one per environment)."""
 
-    def __init__(self, pads, params, indenters, pads_per_env=1, pair_capacity=0, share_meshes=True, stream=None):
+    def __init__(self, pads, params, indenters, pads_per_env=1, pair_capacity=0, share_meshes=True, stream=None,
+                 dm_table=True):
         if not torch.cuda.is_available():
             raise TacError("TacBatch needs a CUDA device")
         self._keep = []
@@ -185,7 +203,7 @@ class TacBatch:
             self._keep.append(cached)
             idesc[e] = IndenterDesc(cached[0].shape[0], cached[1].shape[0], cached[0].ctypes.data, cached[1].ctypes.data)
         prm = (Params * n)(*params)
-        opts = Options(pair_capacity, 1 if share_meshes else 0)
+        opts = Options(pair_capacity, 1 if share_meshes else 0, 0 if dm_table else 1)
         h = ctypes.c_void_p()
         _check(lib().tac_create_batch(pd, prm, n, idesc, ne, pads_per_env, ctypes.byref(opts), _stream(stream),
                                       ctypes.byref(h)))
@@ -351,8 +369,8 @@ def broadphase_static(x, surf_verts, surf_tris, surf_edges, y, ind_tris, ind_edg
 
 
 def batch_from_workload(w, tol=1e-6, tol_advance=1e-2, max_iter=10000, precond=0, pair_capacity=0,
-                        share_meshes=True, stream=None, step=0, marker=0):
+                        share_meshes=True, stream=None, step=0, marker=0, dm_table=True):
     params = [make_params(m, tol=tol, tol_advance=tol_advance, max_iter=max_iter, precond=precond, step=step,
                           marker=marker) for m in w.materials]
     return TacBatch(w.pads, params, w.indenters, w.pads_per_env, pair_capacity=pair_capacity,
-                    share_meshes=share_meshes, stream=stream)
+                    share_meshes=share_meshes, stream=stream, dm_table=dm_table)
