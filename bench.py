@@ -67,6 +67,8 @@ def parse():
                     help="throughput over env counts and pad sizes (the large-scale sweep) instead")
     ap.add_argument("--no-dm-table", action="store_true",
                     help="stream one Dm^-1 per tet even for structured meshes (the unstructured form)")
+    ap.add_argument("--calibrate", action="store_true",
+                    help="CMA-ES (population 12, 80 generations) and adjoint-gradient calibration instead")
     ap.add_argument("--variants", action="store_true",
                     help="iterations and throughput of the paper-literal variants on the batched workload instead")
     return ap.parse_args()
@@ -582,6 +584,56 @@ def run_variants(args):
     print(json.dumps(out), flush=True)
 
 
+def run_calibrate(args):
+    """Baseline calibration (Eq. loss_function) on synthetic recordings: 3
+    press-and-slide scenes (2k-class pad, cylinder pegs, 8 frames) at hidden
+    theta* = (E, nu, rho, mu_f). CMA-ES with the paper's settings
+    (normalised parameters, population 12, 80 generations; each generation
+    one batch of 36 pads) over all four parameters and over (E, nu, mu_f)
+    with rho at its nominal value; Adam on (E, nu, mu_f) with adjoint
+    gradients (40 iterations, forward + reverse sweep each) for comparison.
+    Prints one JSON line with the loss curves and times."""
+    import torch
+    from paper_2603_28475_b300 import calibrate as C
+    from paper_2603_28475_b300 import scenes as S
+    torch.cuda.set_device(0)
+    w, _ = S.config_calibration(n_envs=3, frames=8, seed=args.seed, pad_verts=2000)
+    base = S.Material(E=1.05e5, nu=0.4485, rho=3000.0, mu_f=1.375)      # the centre of the ranges
+    truth = {"E": 1.4e5, "nu": 0.46, "rho": 1100.0, "mu_f": 0.9}
+    runs = {}
+    for names, gens in ((C.PARAMS, 80), (("E", "nu", "mu_f"), 80)):
+        cal = C.Calibration(w, 12, base if "rho" in names else S.Material(**{**base.__dict__, "rho": truth["rho"]}),
+                            names=names)
+        tgt = cal.targets([truth[n] for n in names])
+        best, h = C.calibrate_cmaes(cal, tgt, generations=gens, sigma0=0.3, seed=args.seed)
+        cal.close()
+        runs["cmaes_" + "_".join(names)] = {
+            "params": list(names), "generations": gens, "popsize": 12, "best": dict(zip(names, best.tolist())),
+            "rel_error": {n: abs(b / truth[n] - 1) for n, b in zip(names, best)},
+            "best_loss": h.best_loss[::max(1, gens // 20)] + [h.best_loss[-1]],
+            "pad_frames_solved": h.frames_solved[-1], "seconds": h.seconds[-1],
+            "ms_per_generation": 1e3 * h.seconds[-1] / gens}
+    names = ("E", "nu", "mu_f")
+    base_r = S.Material(**{**base.__dict__, "rho": truth["rho"]})
+    cal = C.Calibration(w, 12, base_r, names=names)
+    tgt = cal.targets([truth[n] for n in names])
+    kappa = cal.kappa[:w.n_pads]
+    cal.close()
+    th, h = C.calibrate_adjoint(w, base_r, tgt, iterations=40, lr=0.05, kappa=kappa)
+    runs["adjoint_adam_E_nu_mu_f"] = {
+        "params": list(names), "iterations": 40, "best": dict(zip(names, th.tolist())),
+        "rel_error": {n: abs(b / truth[n] - 1) for n, b in zip(names, th)},
+        "loss": h.mean_loss[::2] + [h.mean_loss[-1]], "pad_frames_solved": h.frames_solved[-1],
+        "seconds": h.seconds[-1], "ms_per_iteration": 1e3 * h.seconds[-1] / 40}
+    out = {"metric": "baseline calibration on synthetic recordings: loss curves and time (CMA-ES vs adjoint)",
+           "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+           "dtype": "f32 (double-float displacements; f64 pair distance, barrier, CCD and reductions)",
+           "config": {"workload": w.name + " (2k-class pad, 3 scenes, 8 frames)", "truth": truth,
+                      "start": "centre of the parameter ranges", "ranges": C.RANGES},
+           "runs": runs}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -597,6 +649,10 @@ def main():
     if args.variants:
         if rank == 0:
             run_variants(args)
+        return
+    if args.calibrate:
+        if rank == 0:
+            run_calibrate(args)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

@@ -503,9 +503,9 @@ def config_batched(n_envs=4096, frames=12, seed=0, step=0.05 * MM, classes=(2000
     return Workload(f"batched_{n_envs}env_x2pads", pads, mats, inds, 2, poses.astype(np.float32))
 
 
-def config_calibration(n_envs=256, frames=16, seed=0, step=0.05 * MM, mu_f=0.5):
+def config_calibration(n_envs=256, frames=16, seed=0, step=0.05 * MM, mu_f=0.5, pad_verts=5000):
     """Adjoint calibration workload: ``n_envs`` environments of one
-    5k-vertex-class pad and a cylinder peg (r ~ U[2, 4] mm, rotation vector
+    ``pad_verts``-vertex-class pad (default 5k) and a cylinder peg (r ~ U[2, 4] mm, rotation vector
     components ~ U(+-15 deg), xy offset ~ U(+-1 mm)). Each runs a
     press-and-slide sequence: ``frames // 2`` frames pressing ``step`` per
     frame from a d-hat gap, then ``frames - frames // 2`` frames sliding
@@ -523,7 +523,7 @@ def config_calibration(n_envs=256, frames=16, seed=0, step=0.05 * MM, mu_f=0.5):
         if key not in cyl_cache:
             cyl_cache[key] = cylinder(key * 0.05 * MM, 24 * MM, 64, 8)
         ind = cyl_cache[key]
-        pad = size_class_pad(5000)
+        pad = size_class_pad(pad_verts)
         pads.append(pad)
         mats.append(Material(mu_f=mu_f))
         inds.append(ind)
