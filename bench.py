@@ -271,6 +271,9 @@ def run_ours(args, rank, world):
         b.step(status, iters)
         b.markers(mk)
     torch.cuda.synchronize()
+    # the state after the warm-up: the end-to-end leg re-runs the same frames from it
+    ck_x, ck_v = b.get_state()
+    ck_x, ck_v = ck_x.clone(), ck_v.clone()
     # timed frames: inputs resident in HBM
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     conv, iter_hist, stats_all = 0, [], []
@@ -338,10 +341,12 @@ def run_ours(args, rank, world):
         dev_pose = torch.empty(n_pads, 6, dtype=torch.float32, device=dev)
         n_e2e = args.steps
         conv_e = 0
+        b.reset(poses[args.warmup])
+        b.set_state(ck_x, ck_v)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         for s in range(n_e2e):
-            f = args.warmup + args.steps + 1 + s
+            f = args.warmup + 1 + s
             dev_pose.copy_(host_poses[f], non_blocking=True)
             b.set_indenter(dev_pose)
             b.step(status, iters)
@@ -351,7 +356,9 @@ def run_ours(args, rank, world):
             torch.cuda.synchronize()
             conv_e += int(np.all(host_st.numpy().reshape(-1, w.pads_per_env) == 0, axis=1).sum())
         dt_e = time.perf_counter() - t1
-        e2e = {"value": conv_e / dt_e * world, "unit": UNIT, "h2d_bytes_per_step": n_pads * 6 * 4,
+        e2e = {"value": conv_e / dt_e * world, "unit": UNIT,
+               "frames": "the device-timed frames again, from the state after the warm-up",
+               "h2d_bytes_per_step": n_pads * 6 * 4,
                "d2h_bytes_per_step": b.total_markers * 2 * 4 + n_pads * 4}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
