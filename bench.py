@@ -172,7 +172,8 @@ def algorithmic_bytes(stats, w, dm_table=True):
 def kernel_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("kernels.cu", "device_math.cuh", "solve.cuh"):
+    # the kernels and the mesh layout they stream (patches, colours, tables)
+    for f in ("kernels.cu", "device_math.cuh", "solve.cuh", "layout.h", "mesh.cpp"):
         with open(os.path.join(ROOT, "paper_2603_28475_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -29,6 +29,7 @@ constexpr double kArmijoC = 1e-4;
 constexpr int kMaxHalvings = 20;
 constexpr int kMaxSubsteps = 1000;
 constexpr int kWarps = kThreads / 32;
+static_assert(kWarps == kCtaWarps, "the host balances colour classes for this many warps");
 // a float32 gradient is resolved only down to a few hundred ulps of the
 // largest per-corner force that enters it: 256 * 2^-24
 constexpr float kFloat32Floor = 256.0f / 16777216.0f;

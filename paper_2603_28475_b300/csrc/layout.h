@@ -23,6 +23,9 @@ constexpr int kPatchTets = 32;
 constexpr int kPatchVerts = 32;
 constexpr int kPatchCsr = kPatchVerts + 1;
 constexpr uint32_t kNoTet = 0xffffffffu;
+// warps of one solve CTA: the scatter passes take a colour class's patches
+// in rounds of kCtaWarps (one patch per warp)
+constexpr int kCtaWarps = 8;
 
 // Marker map: every marker reads kMarkerSlots weighted mesh vertices (a
 // barycentric map fills three and gives the fourth weight 0).

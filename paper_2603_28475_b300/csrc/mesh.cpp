@@ -423,6 +423,67 @@ bool build_pad_mesh(int nv, int nt, int nf, int nm, const float* rest, const int
             ncol = std::max(ncol, c + 1);
         }
     }
+    // 2b. balance the classes: the scatter passes process a class in rounds of
+    // kCtaWarps patches (one per warp) and end it with a CTA barrier, so a
+    // class costs ceil(size / kCtaWarps) rounds. A class whose last round is
+    // partly filled moves the patches of that round into classes with free
+    // slots in their own last round (where none of the patch's vertices is
+    // used); the moves are kept only when all of them succeed, which saves
+    // one round each time. Classes left empty disappear.
+    {
+        const int W = kCtaWarps;
+        std::vector<int> size(ncol, 0);
+        for (int q = 0; q < np0; ++q) size[colour[q]]++;
+        auto fits = [&](int q, int c) {
+            for (int v : pverts[q])
+                for (int o : vpatch[v])
+                    if (o != q && colour[o] == c) return false;
+            return true;
+        };
+        for (bool changed = true; changed;) {
+            changed = false;
+            std::vector<int> cls(ncol);
+            std::iota(cls.begin(), cls.end(), 0);
+            std::stable_sort(cls.begin(), cls.end(), [&](int x, int y) { return size[x] < size[y]; });
+            for (int a : cls) {
+                const int r = size[a] % W;
+                if (size[a] == 0 || r == 0) continue;
+                std::vector<int> mem;
+                for (int q = np0 - 1; q >= 0; --q)
+                    if (colour[q] == a) mem.push_back(q);
+                std::vector<int> moved;
+                for (int q : mem) {
+                    if (static_cast<int>(moved.size()) == r) break;
+                    for (int c = 0; c < ncol; ++c) {
+                        if (c == a || size[c] == 0 || size[c] % W == 0 || !fits(q, c)) continue;
+                        colour[q] = c;
+                        size[c]++;
+                        size[a]--;
+                        moved.push_back(q);
+                        break;
+                    }
+                }
+                if (static_cast<int>(moved.size()) < r) {
+                    for (int q : moved) {
+                        size[colour[q]]--;
+                        colour[q] = a;
+                        size[a]++;
+                    }
+                } else {
+                    changed = true;
+                }
+            }
+        }
+        // renumber the classes left, largest first (ties by old index)
+        std::vector<int> cls;
+        for (int c = 0; c < ncol; ++c)
+            if (size[c] > 0) cls.push_back(c);
+        std::stable_sort(cls.begin(), cls.end(), [&](int x, int y) { return size[x] > size[y]; });
+        std::vector<int> ren(ncol, -1);
+        for (size_t k = 0; k < cls.size(); ++k) ren[cls[k]] = static_cast<int>(k);
+        for (int q = 0; q < np0; ++q) colour[q] = ren[colour[q]];
+        ncol = static_cast<int>(cls.size());
+    }
     // 3. patches in colour-major order; tets laid out in that order
     std::vector<int> porder(np0);
     std::iota(porder.begin(), porder.end(), 0);
