@@ -35,10 +35,11 @@ from . import newton as NW
 
 
 def marker_transpose(pad, dL_dm):
-    """dL/dx from dL/d(markers): the transpose of the barycentric readout."""
+    """dL/dx from dL/d(markers): the transpose of the marker readout, summed
+    over every entry of a marker's map (3 barycentric or k kNN nodes)."""
     g = np.zeros_like(pad.rest)
     for m in range(pad.marker_ids.shape[0]):
-        for k in range(3):
+        for k in range(pad.marker_ids.shape[1]):
             g[pad.marker_ids[m, k], :2] += pad.marker_w[m, k] * dL_dm[m]
     return g
 

@@ -87,8 +87,15 @@ def test_adjoint_matches_central_differences(setup):
         assert got[k] == pytest.approx(fd[k], rel=1e-3, abs=1e-4 * scale), (k, got, fd)
 
 
-def test_marker_transpose_is_the_adjoint_of_the_readout(setup):
+@pytest.mark.parametrize("mode", ["bary", "knn"])
+def test_marker_transpose_is_the_adjoint_of_the_readout(setup, mode):
     pad, ind, s1, s2, p2, c = setup
+    if mode == "knn":
+        pd = S.hex_pad((6 * MM, 6 * MM, 2 * MM), (4, 4, 2), marker_shape=(3, 3))
+        mk = pd.markers + np.array([0.3 * MM, 0.2 * MM])      # off the nodes: four weighted neighbours
+        pad = G.build_pad(pd.rest, pd.tets, pd.fixed, mk, 0.3e6, 0.45, 1100.0, 1 / 60, DH, 0.5,
+                          marker_mode="knn")
+        assert pad.marker_ids.shape[1] == 4 and np.all(pad.marker_w[:, 3] > 0)
     rng = np.random.default_rng(1)
     u = rng.normal(size=pad.rest.shape)
     lhs = float(np.sum(c * SV.markers(pad, pad.rest + u)))
