@@ -93,6 +93,37 @@ def test_adjoint_matches_oracle(tac, oracle_ref):
     b.close()
 
 
+def test_adjoint_with_knn_markers_matches_oracle(tac, oracle_ref):
+    """The adjoint's right-hand side through the kNN marker map (4 weighted
+    nodes per marker, markers moved off the nodes)."""
+    from _cases import f32
+    pad0, ind, s1, s2, _, _ = oracle_ref
+    pd, mat, ind_s, poses = _scene()
+    pd.markers = (pd.markers + np.array([0.3 * MM, 0.2 * MM])).astype(np.float32)
+    pad = G.build_pad(pd.rest, pd.tets, pd.fixed, pd.markers, f32(mat.E), f32(mat.nu), f32(mat.rho), f32(mat.h),
+                      f32(mat.dhat), f32(mat.mu_f), marker_mode="knn")
+    assert np.all(pad.marker_w[:, 3] > 0)
+    c = np.random.default_rng(4).normal(size=(pd.markers.shape[0], 2))
+    ref = AD.adjoint(pad, ind, s1, s2, c)
+    w = S.Workload("adjoint_knn", [pd], [mat], [ind_s], 1, poses[:, None, :])
+    b = tac.batch_from_workload(w, tol=TIGHT, marker=1)
+    b.reset(torch.tensor(poses[0]).reshape(1, 6))
+    for f in (1, 2):
+        b.set_indenter(torch.tensor(poses[f]).reshape(1, 6))
+        st, _ = b.step()
+        assert int(st.item()) == 0
+    mk = b.markers().cpu().numpy().astype(np.float64)
+    assert np.abs(mk - SV.markers(pad, s2.x)).max() <= 1e-4 * 2 * MM
+    g, st, it = b.adjoint(torch.tensor(c, dtype=torch.float32))
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    got = g.cpu().numpy()[0]
+    scale = np.abs(ref).max()
+    for k in range(9):
+        assert got[k] == pytest.approx(ref[k], rel=1e-3, abs=1e-4 * scale), (k, got, ref)
+    b.close()
+
+
 def test_autograd_function_gives_the_adjoint(tac, oracle_ref):
     from paper_2603_28475_b300 import autograd as A
     pad, ind, s1, s2, c, ref = oracle_ref
