@@ -110,10 +110,14 @@ def adjoint(pad, ind, state_prev, state_new, dL_dm, fd_pose=FD_ROT):
     return out
 
 
-def adjoint_frame(pad, ind, state_prev, state_new, dL_dm=None, dL_dx=None, lag=None, fd_pose=FD_ROT, fd_x=1e-10):
+def adjoint_frame(pad, ind, state_prev, state_new, dL_dm=None, dL_dx=None, lag=None, fd_pose=FD_ROT, fd_x=1e-10,
+                  relag=False):
     """Adjoint of one frame of a sequence. The frame's friction lag (normal
     forces, contact normals, closest-point weights, from its start state) is
-    a constant of the frame, as in the frame's solve.
+    a constant of the frame, as in the frame's solve; with ``relag`` the lag
+    is instead a function of the start state and start pose, rebuilt from
+    them (on the frame's start candidate set) in every difference below, so
+    that dL/dx^t and the start-pose entries include the lag's dependence.
 
     The right-hand side is the loss gradient with respect to the frame's end
     positions: the marker readout's transpose of dL_dm [M, 2] plus dL_dx
@@ -127,7 +131,10 @@ def adjoint_frame(pad, ind, state_prev, state_new, dL_dm=None, dL_dx=None, lag=N
         x^t + h v^t moving with it (inertia and the friction displacement);
       * v^t: g is affine in x-hat with dg/dx-hat = -M, so dL/dv^t = h M lambda.
     """
+    if relag and lag is not None:
+        raise ValueError("relag rebuilds the lag from the start state; do not pass one")
     fr = frame_of(pad, ind, state_prev, state_new.pose, lag=lag)
+    cand_t = BP.candidates(fr.x_t, fr.y_t, pad, ind, 2.0 * pad.dhat) if relag else None
     x = state_new.x
     pairs = BP.candidates(x, fr.y(1.0), pad, ind, 2.0 * pad.dhat)
     H = NW.assemble(fr, x, 1.0, pairs)
@@ -157,7 +164,8 @@ def adjoint_frame(pad, ind, state_prev, state_new, dL_dm=None, dL_dx=None, lag=N
         theta[2] = -dot_free(En.friction(fr.lag, x, fr.x_t, fr.y(1.0), fr.y_t, p_f)[1])
 
     def g_of(x_t=fr.x_t, xhat=fr.xhat, y_t=fr.y_t, y_n=fr.y_next):
-        return En.total(En.Frame(pad, ind, x_t, xhat, y_t, y_n, fr.lag), x, 1.0, pairs)[1]
+        lg = En.friction_lag(cand_t, x_t, y_t, pad, ind) if relag else fr.lag
+        return En.total(En.Frame(pad, ind, x_t, xhat, y_t, y_n, lg), x, 1.0, pairs)[1]
 
     pose_n = np.asarray(state_new.pose, np.float64)
     pose_t = np.asarray(state_prev.pose, np.float64)
@@ -191,10 +199,13 @@ def adjoint_frame(pad, ind, state_prev, state_new, dL_dm=None, dL_dx=None, lag=N
     return theta, dx0, dv0
 
 
-def adjoint_sequence(pad, ind, states, dL_dms, lags=None):
+def adjoint_sequence(pad, ind, states, dL_dms, lags=None, relag=False):
     """dL/dtheta for L = sum_f dL_dms[f-1] . markers(x^f) over frames
     1..F of a run from states[0], each frame's friction lag held fixed
-    (``lags[f-1]`` if given, else the lag of states[f-1]). theta = (Lame
+    (``lags[f-1]`` if given, else the lag of states[f-1]) or, with
+    ``relag``, differentiated as a function of the frame's start state and
+    start pose (the total derivative of a run whose frames each lag
+    themselves). theta = (Lame
     lambda, Lame mu, mu_f, end pose of frame 1, ..., end pose of frame F)
     [3 + 6F]; frame 1's start pose is a constant.
 
@@ -207,7 +218,7 @@ def adjoint_sequence(pad, ind, states, dL_dms, lags=None):
     a_v = np.zeros_like(states[0].x)
     for f in range(F, 0, -1):
         th, dx0, dv0 = adjoint_frame(pad, ind, states[f - 1], states[f], dL_dms[f - 1], a_x + a_v / pad.h,
-                                     lag=None if lags is None else lags[f - 1])
+                                     lag=None if lags is None else lags[f - 1], relag=relag)
         out[0:3] += th[0:3]
         out[3 + 6 * (f - 1):3 + 6 * f] += th[3:9]
         if f >= 2:

@@ -172,6 +172,41 @@ def test_sequence_adjoint_matches_central_differences(seq_setup):
         assert got[k] == pytest.approx(v, rel=1e-3, abs=1e-4 * scale), (k, got[k], v)
 
 
+def test_relagged_sequence_adjoint_matches_full_re_solves(seq_setup):
+    """With the lag differentiated (relag), the sweep is the total
+    derivative of a run whose frames each lag themselves: central
+    differences of the 3-frame loss with every frame re-solved from its own
+    start state and its own lag, for friction and frame 1's end-pose x and
+    z translations (which reach frames 2 and 3 through their start states
+    and start poses, and so through their lags)."""
+    pad, ind, poses, states, lags, cs = seq_setup
+    got = AD.adjoint_sequence(pad, ind, states, cs, relag=True)
+    frozen = AD.adjoint_sequence(pad, ind, states, cs, lags=lags)
+    checks = [("mu_f", 2), ("pose", 3 + 3), ("pose", 3 + 5)]
+    fd = {}
+    for attr, k in checks:
+        vals = []
+        if attr == "pose":
+            f, m = divmod(k - 3, 6)
+            h = 1e-6 if m < 3 else 1e-6 * abs(poses[f + 1][m])
+            for sgn in (1.0, -1.0):
+                q = poses.copy()
+                q[f + 1, m] += sgn * h
+                vals.append(_seq_loss(pad, _run_seq(pad, ind, q, None)[0], cs))
+        else:
+            v0 = getattr(pad, attr)
+            h = 1e-6 * v0
+            for sgn in (1.0, -1.0):
+                pk = copy.copy(pad)
+                setattr(pk, attr, v0 + sgn * h)
+                vals.append(_seq_loss(pk, _run_seq(pk, ind, poses, None)[0], cs))
+        fd[k] = (vals[0] - vals[1]) / (2 * h)
+    scale = max(abs(v) for v in fd.values())
+    print({k: (got[k], frozen[k], v) for k, v in fd.items()})
+    for k, v in fd.items():
+        assert got[k] == pytest.approx(v, rel=1e-3, abs=1e-4 * scale), (k, got[k], v)
+
+
 def test_frame_adjoint_reduces_to_single_frame_form(seq_setup):
     """With no downstream gradient, the first 9 entries are the single-frame
     adjoint and dL/dv^t = h M lambda vanishes on Dirichlet vertices."""
