@@ -203,13 +203,20 @@ int tac_adjoint(tac_handle h, const float* dL_dmarkers_dev, double* dL_dtheta_de
  *   order: dL/dx^t = (M + H_D) lambda and dL/dv^t = h M lambda, H_D the
  *   lagged friction Hessian; 0 on Dirichlet vertices.
  * status_dev / iters_dev / max_iter / tol: as in tac_adjoint.
+ * lag_mode: 0 holds the lag fixed as above; 1 differentiates it as a
+ *   function of the frame's start state and start pose, which makes a
+ *   reverse sweep the total derivative of a run whose frames each lag
+ *   themselves. dL/dx^t and the start-pose entries then gain
+ *   -d(lambda^T g)/d(start) through the lag, from float64 central
+ *   differences of each lagged pair's friction force rebuilt from its
+ *   primitives' start positions (1e-10 m, 1e-7 rad).
  * A sweep over frames 1..F gives frame f's end state the gradient
  *   (markers of frame f) + a_x + a_v / h with a_x, a_v from frame f+1, then
  *   passes a_x = dL/dx^t - a_v / h and a_v = dL/dv^t to frame f-1 (since
  *   v^f = (x^f - x^(f-1)) / h). Must follow the tac_step of the frame. */
 int tac_adjoint_frame(tac_handle h, const float* dL_dmarkers_dev, const float* dL_dx_dev, double* dL_dtheta_dev,
                       float* dL_dx0_dev, float* dL_dv0_dev, int* status_dev, int* iters_dev, int max_iter, float tol,
-                      void* stream);
+                      int lag_mode, void* stream);
 
 /* Install a frame that was solved before (by a tac_step from the start
  * state x0, v0 at pose_start to pose_end, ending at x1) so that tac_adjoint

@@ -119,11 +119,11 @@ class TacStepFn(torch.autograd.Function):
         return batch.step()
 
     @staticmethod
-    def forward(ctx, lame, mu_f, pose_s, pose_e, x0, v0, batch, base_params, adjoint_tol=1e-6):
+    def forward(ctx, lame, mu_f, pose_s, pose_e, x0, v0, batch, base_params, adjoint_tol=1e-6, relag=False):
         status, _ = TacStepFn._solve(batch, base_params, lame, mu_f, pose_s, pose_e, x0, v0)
         x1, v1 = batch.get_state()
         m = batch.markers().clone()
-        ctx.batch, ctx.base, ctx.tol, ctx.status = batch, base_params, adjoint_tol, status
+        ctx.batch, ctx.base, ctx.tol, ctx.status, ctx.relag = batch, base_params, adjoint_tol, status, relag
         ctx.inputs = (lame.detach(), mu_f.detach(), pose_s.detach(), pose_e.detach(), x0.detach().clone(),
                       v0.detach().clone(), x1.clone())
         ctx.like = (lame, mu_f, pose_s, pose_e, x0, v0)
@@ -139,23 +139,26 @@ class TacStepFn(torch.autograd.Function):
         zero = torch.zeros(b.total_verts, 3, dtype=torch.float32, device=b.device)
         gx1 = zero if gx1 is None else gx1.to(device=b.device, dtype=torch.float32)
         gv1 = zero if gv1 is None else gv1.to(device=b.device, dtype=torch.float32)
-        th, dx0, dv0, st, it = b.adjoint_frame(gm, gx1 + gv1 / hv, tol=ctx.tol)
+        th, dx0, dv0, st, it = b.adjoint_frame(gm, gx1 + gv1 / hv, tol=ctx.tol, relag=ctx.relag)
         gx0 = dx0 - gv1 / hv
         l_, m_, ps_, pe_, x_, v_ = ctx.like
         to = lambda t, ref: t.to(device=ref.device, dtype=ref.dtype).reshape(ref.shape)
         return (to(th[:, 0:2], l_), to(th[:, 2], m_), to(th[:, 9:15], ps_), to(th[:, 3:9], pe_), to(gx0, x_),
-                to(dv0, v_), None, None, None)
+                to(dv0, v_), None, None, None, None)
 
 
-def sequence_markers(batch, x0, v0, lame, mu_f, poses, base_params=None, adjoint_tol=1e-6):
+def sequence_markers(batch, x0, v0, lame, mu_f, poses, base_params=None, adjoint_tol=1e-6, relag=False):
     """Marker fields of frames 1..F [F, total_markers, 2] from the start
     state (x0, v0) as a differentiable function of the Lame pair [n_pads, 2],
     friction [n_pads] and the poses [F + 1, n_pads, 6] (poses[0] the start
-    pose of frame 1)."""
+    pose of frame 1). relag: each frame's backward differentiates its
+    friction lag as a function of the frame's start state and start pose
+    (the total derivative of the run); otherwise the lag is a constant of
+    its frame."""
     if base_params is None:
         base_params = batch.get_params()
     x, v, out = x0, v0, []
     for f in range(1, poses.shape[0]):
-        m, x, v = TacStepFn.apply(lame, mu_f, poses[f - 1], poses[f], x, v, batch, base_params, adjoint_tol)
+        m, x, v = TacStepFn.apply(lame, mu_f, poses[f - 1], poses[f], x, v, batch, base_params, adjoint_tol, relag)
         out.append(m)
     return torch.stack(out)

@@ -22,7 +22,8 @@ __global__ void markers_kernel(const __grid_constant__ Dev D, float* out);
 __global__ void schedule_kernel(const __grid_constant__ Dev D, unsigned long long* key, int* idx, int n2, int* order);
 __global__ void frame_install_kernel(const __grid_constant__ Dev D, const float* x0, const float* v0, const float* x1);
 __global__ void adjoint_kernel(const __grid_constant__ Dev D, const float* dLdm, const float* dLdx, double* out,
-                               int out_stride, float* dx0, float* dv0, int* status, int* iters, int max_iter, float tol);
+                               int out_stride, float* dx0, float* dv0, int* status, int* iters, int max_iter, float tol,
+                               int relag);
 size_t shared_bytes();
 cudaError_t configure_kernels();
 void set_last_error(const std::string& msg);
@@ -688,7 +689,7 @@ int tac_adjoint(tac_handle h, const float* dL_dmarkers_dev, double* dL_dtheta_de
     if (!h || !dL_dmarkers_dev || !dL_dtheta_dev || max_iter < 0 || !(tol > 0))
         return fail(TAC_ERR_INVALID_ARG, "invalid argument");
     adjoint_kernel<<<h->n_pads, kThreads, shared_bytes(), static_cast<cudaStream_t>(stream)>>>(
-        h->dev, dL_dmarkers_dev, nullptr, dL_dtheta_dev, 9, nullptr, nullptr, status_dev, iters_dev, max_iter, tol);
+        h->dev, dL_dmarkers_dev, nullptr, dL_dtheta_dev, 9, nullptr, nullptr, status_dev, iters_dev, max_iter, tol, 0);
     CUDA_TRY(cudaGetLastError());
     return TAC_OK;
 }
@@ -710,12 +711,12 @@ int tac_set_frame(tac_handle h, const float* x0_dev, const float* v0_dev, const 
 
 int tac_adjoint_frame(tac_handle h, const float* dL_dmarkers_dev, const float* dL_dx_dev, double* dL_dtheta_dev,
                       float* dL_dx0_dev, float* dL_dv0_dev, int* status_dev, int* iters_dev, int max_iter, float tol,
-                      void* stream) {
-    if (!h || !dL_dtheta_dev || max_iter < 0 || !(tol > 0))
+                      int lag_mode, void* stream) {
+    if (!h || !dL_dtheta_dev || max_iter < 0 || !(tol > 0) || (lag_mode != 0 && lag_mode != 1))
         return fail(TAC_ERR_INVALID_ARG, "invalid argument");
     adjoint_kernel<<<h->n_pads, kThreads, shared_bytes(), static_cast<cudaStream_t>(stream)>>>(
         h->dev, dL_dmarkers_dev, dL_dx_dev, dL_dtheta_dev, 15, dL_dx0_dev, dL_dv0_dev, status_dev, iters_dev,
-        max_iter, tol);
+        max_iter, tol, lag_mode);
     CUDA_TRY(cudaGetLastError());
     return TAC_OK;
 }

@@ -1288,6 +1288,9 @@ __device__ __noinline__ int lag_build(const Dev& D, const PadDev& P, const MeshD
             Feature<double> f = pair_feature<double>(q.x, X);
             if (f.d < dh && f.d > 0.0) {
                 keep = 1;
+                L.pq[0] = q.x;
+                L.pq[1] = q.y;
+                L.pq[2] = q.z;
                 V3<double> r = feat_r(f, X);
                 double inv = 1.0 / f.d;
                 L.n[0] = (float)(r.x * inv);
@@ -1579,7 +1582,7 @@ __device__ __noinline__ void move_state(const Dev& D, const PadDev& P, const Mes
 // ---------------------------------------------------------------------------
 // frame setup: indenter world vertices, u0 = u, uhat = u + h v
 
-__device__ void rotation(const float* pose, double R[9]) {
+__device__ void rotation_dd(const double* pose, double R[9]) {
     double rx = pose[0], ry = pose[1], rz = pose[2];
     double th = sqrt(rx * rx + ry * ry + rz * rz);
     double kx = 0, ky = 0, kz = 0, sn = 0, cs1 = 0;
@@ -1595,6 +1598,11 @@ __device__ void rotation(const float* pose, double R[9]) {
             for (int k = 0; k < 3; ++k) kk += K[3 * i + k] * K[3 * k + j];
             R[3 * i + j] = (i == j ? 1.0 : 0.0) + sn * K[3 * i + j] + cs1 * kk;
         }
+}
+
+__device__ void rotation(const float* pose, double R[9]) {
+    const double r[3] = {pose[0], pose[1], pose[2]};
+    rotation_dd(r, R);
 }
 
 __device__ __noinline__ void world_indenter(const Dev& D, const PadDev& P, const EnvDev& E, const float* pose, float* Yw) {
@@ -2456,6 +2464,120 @@ __global__ void __launch_bounds__(kThreads) frame_install_kernel(const __grid_co
 
 enum { ADJ_CONVERGED = 0, ADJ_MAXITER = 1, ADJ_BREAKDOWN = 2, ADJ_NONFINITE = 3 };
 
+// The friction lag's own dependence on the frame start, for the exact
+// multi-frame adjoint. For a lag record, psi = lambda^T g_D(x*; lag) with
+// the lag (normal force -kappa b'(d), normal, gel and indenter closest-point
+// weights) rebuilt in float64 from the frame-start positions of the pair's
+// primitives; the start positions that enter the friction displacement
+// explicitly stay fixed (their part is the H_D lambda term). Central
+// differences of psi (1e-10 m in positions and translation, 1e-7 rad in
+// rotation) give, per record, -dpsi/dx^t of its gel slots, added to the
+// record's slot entries (contact_gather sums them per vertex), and, summed
+// over records into dps, dpsi/d(start pose).
+__device__ __noinline__ void lag_relag(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int nl,
+                                       int pad, double dps[6]) {
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    float* sb = D.slotbuf + (size_t)9 * 6 * P.pair_off;
+    const LagRec* lg = D.lag + P.pair_off;
+    const double dh = P.dhat, kap = P.kappa, eps = P.eps_v, muf = P.mu_f;
+    double pose_s[6], pose_n[6];
+    for (int m = 0; m < 6; ++m) {
+        pose_s[m] = D.pose_s[6 * pad + m];
+        pose_n[m] = D.pose_t[6 * pad + m];
+    }
+    double Rs[9], Rn[9];
+    rotation_dd(pose_s, Rs);
+    rotation_dd(pose_n, Rn);
+    auto world = [&](const double R[9], const double* pose, int j) {
+        const float* y = D.Y + 3 * (E.y_off + j);
+        return V3<double>{R[0] * y[0] + R[1] * y[1] + R[2] * y[2] + pose[3],
+                          R[3] * y[0] + R[4] * y[1] + R[5] * y[2] + pose[4],
+                          R[6] * y[0] + R[7] * y[1] + R[8] * y[2] + pose[5]};
+    };
+    for (int l = threadIdx.x; l < nl; l += kThreads) {
+        const LagRec& L = lg[l];
+        const int4 q = make_int4(L.pq[0], L.pq[1], L.pq[2], 0);
+        int gsl[4], isl[4];
+        pair_slots(D, M, E, q, gsl, isl);
+        V3<double> X0[4], Xe[4], la[4];
+        for (int sl = 0; sl < 4; ++sl) {
+            la[sl] = {0.0, 0.0, 0.0};
+            if (gsl[sl] >= 0) {
+                const int xi = M.xv_off + gsl[sl], si = P.v_off + gsl[sl];
+                double a0[3], a1[3];
+                for (int c = 0; c < 3; ++c) {
+                    const int sc = c * D.Vt + si;
+                    const double Xr = D.X[c * D.XVt + xi];
+                    a0[c] = Xr + ((double)D.u0h[sc] + (double)D.u0l[sc]);
+                    a1[c] = Xr + ((double)D.uh[sc] + (double)D.ul[sc]);
+                }
+                X0[sl] = {a0[0], a0[1], a0[2]};
+                Xe[sl] = {a1[0], a1[1], a1[2]};
+                la[sl] = {D.adj_x[si], D.adj_x[D.Vt + si], D.adj_x[2 * D.Vt + si]};
+            } else {
+                X0[sl] = world(Rs, pose_s, isl[sl]);
+                Xe[sl] = world(Rn, pose_n, isl[sl]);
+            }
+        }
+        // psi at frame-start primitive positions Xp (X0, Xe fixed in the displacement)
+        auto psi = [&](const V3<double> Xp[4]) -> double {
+            Feature<double> f = pair_feature<double>(q.x, Xp);
+            if (!(f.d > 0.0) || f.d >= dh) return 0.0;      // the lag force vanishes there
+            V3<double> r = feat_r(f, Xp);
+            const double inv = 1.0 / f.d;
+            const V3<double> n = inv * r;
+            const double lamn = -kap * barrier_b1(f.d, dh);
+            V3<double> Dl = {0.0, 0.0, 0.0}, lw = {0.0, 0.0, 0.0};
+            for (int sl = 0; sl < 4; ++sl) {
+                // gel slots carry w >= 0, indenter slots w <= 0: sum w (x_e - x_0) is
+                // the gel closest point's displacement minus the indenter's
+                const V3<double> dx = {Xe[sl].x - X0[sl].x, Xe[sl].y - X0[sl].y, Xe[sl].z - X0[sl].z};
+                Dl = {Dl.x + f.w[sl] * dx.x, Dl.y + f.w[sl] * dx.y, Dl.z + f.w[sl] * dx.z};
+                if (gsl[sl] >= 0) lw = {lw.x + f.w[sl] * la[sl].x, lw.y + f.w[sl] * la[sl].y, lw.z + f.w[sl] * la[sl].z};
+            }
+            const double nD = dot(n, Dl);
+            const V3<double> t = {Dl.x - nD * n.x, Dl.y - nD * n.y, Dl.z - nD * n.z};
+            const double sg = sqrt(dot(t, t));
+            return muf * lamn * moll_f1_over_s(sg, eps) * dot(lw, t);
+        };
+        V3<double> Xp[4];
+        for (int sl = 0; sl < 4; ++sl) Xp[sl] = X0[sl];
+        const double hx = 1e-10;
+        for (int sl = 0; sl < 3; ++sl) {
+            if (gsl[sl] < 0) continue;
+            float* e = sb + 9 * (3 * (P.pair_cap + l) + sl);
+            for (int c = 0; c < 3; ++c) {
+                double* xc = c == 0 ? &Xp[sl].x : (c == 1 ? &Xp[sl].y : &Xp[sl].z);
+                const double x0 = *xc;
+                *xc = x0 + hx;
+                const double p1 = psi(Xp);
+                *xc = x0 - hx;
+                const double p2 = psi(Xp);
+                *xc = x0;
+                e[c] += (float)(-(p1 - p2) / (2.0 * hx));
+            }
+        }
+        for (int m = 0; m < 6; ++m) {
+            const double hm = m < 3 ? 1e-7 : 1e-10;
+            double pv[2];
+            for (int sg = 0; sg < 2; ++sg) {
+                double pp[6];
+                for (int k = 0; k < 6; ++k) pp[k] = pose_s[k];
+                pp[m] += sg == 0 ? hm : -hm;
+                double Rp[9];
+                rotation_dd(pp, Rp);
+                for (int sl = 0; sl < 4; ++sl) Xp[sl] = isl[sl] >= 0 ? world(Rp, pp, isl[sl]) : X0[sl];
+                pv[sg] = psi(Xp);
+            }
+            acc[m] += (pv[0] - pv[1]) / (2.0 * hm);
+        }
+    }
+    double v6[6] = {acc[0], acc[1], acc[2], acc[3], acc[4], acc[5]};
+    block_sum<6>(v6);
+    for (int m = 0; m < 6; ++m) dps[m] = v6[m];
+}
+
+
 // Adjoint of the last frame. dLdm (markers) and dLdx (caller-order end
 // positions) form the right-hand side, either may be null. out: per pad
 // out_stride doubles (9: Lame pair, mu_f, end pose; 15: plus the start pose).
@@ -2465,7 +2587,7 @@ enum { ADJ_CONVERGED = 0, ADJ_MAXITER = 1, ADJ_BREAKDOWN = 2, ADJ_NONFINITE = 3 
 __global__ void __launch_bounds__(kThreads, 2) adjoint_kernel(const __grid_constant__ Dev D, const float* dLdm,
                                                               const float* dLdx, double* out, int out_stride,
                                                               float* dx0, float* dv0, int* status, int* iters,
-                                                              int max_iter, float tol) {
+                                                              int max_iter, float tol, int relag) {
     const int pad = blockIdx.x;
     load_pad(D, pad);
     const PadDev& P = S.P;
@@ -2557,14 +2679,23 @@ __global__ void __launch_bounds__(kThreads, 2) adjoint_kernel(const __grid_const
         if (status) status[pad] = st;
         if (iters) iters[pad] = it;
     }
-    if (dx0 || dv0) {
+    if (dx0 || dv0 || relag) {
         // H_D lambda: the lagged friction part of the Hessian-vector product
-        // (p holds lambda), gathered into g[1]
+        // (p holds lambda), gathered into g[1]; with relag the lag's own
+        // dependence on the frame start joins the same slot entries
         for (int i = threadIdx.x; i < M.n_v; i += kThreads)
 #pragma unroll
             for (int c = 0; c < 3; ++c) D.g[1][c * D.Vt + P.v_off + i] = 0.f;
         __syncthreads();
         pair_hvp(D, P, M, E, cc.npairs, cc.nlag, 1.0, false);
+        if (relag && P.mu_f > 0.f) {
+            double dps[6];
+            lag_relag(D, P, M, E, cc.nlag, pad, dps);
+            if (threadIdx.x == 0 && out_stride >= 15) {
+                double* o = out + (size_t)out_stride * pad;
+                for (int q = 0; q < 6; ++q) o[9 + q] -= dps[q];
+            }
+        }
         contact_gather(D, P, cc, 1);
         for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
             const size_t si = (size_t)P.v_off + i;

@@ -56,6 +56,7 @@ struct LagRec {
     int iv[3];                // indenter vertex (env-local id) of each indenter slot, -1 if none
     float iw[3];              // indenter slot weights (>= 0)
     double lam;               // lagged normal force magnitude -kappa b'(d)
+    int pq[3];                // the candidate pair it was built from (type, i, j)
 };
 
 // All device arrays of a batch (SoA with strides noted).

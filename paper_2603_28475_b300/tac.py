@@ -64,7 +64,7 @@ def load_library(path=_LIB_PATH):
         "tac_step": [vp, vp, vp, vp],
         "tac_markers": [vp, vp, vp],
         "tac_adjoint": [vp, vp, vp, vp, vp, i, f, vp],
-        "tac_adjoint_frame": [vp, vp, vp, vp, vp, vp, vp, vp, i, f, vp],
+        "tac_adjoint_frame": [vp, vp, vp, vp, vp, vp, vp, vp, i, f, i, vp],
         "tac_set_frame": [vp, vp, vp, vp, vp, vp, vp],
         "tac_get_state": [vp, vp, vp, vp],
         "tac_set_state": [vp, vp, vp, vp],
@@ -267,14 +267,15 @@ class TacBatch:
         self._hold = g
         return out, st, it
 
-    def adjoint_frame(self, dL_dmarkers=None, dL_dx=None, max_iter=4000, tol=1e-6, stream=None):
+    def adjoint_frame(self, dL_dmarkers=None, dL_dx=None, max_iter=4000, tol=1e-6, relag=False, stream=None):
         """Adjoint of the last frame for a reverse sweep (tac_adjoint_frame):
         returns dL/dtheta [n_pads, 15] (Lame lambda, Lame mu, mu_f, end pose
         rotation vector and translation, start pose rotation vector and
         translation), dL/dx^t and dL/dv^t [total_verts, 3] (caller order),
         and the PCG status and iterations per pad. dL_dmarkers [total_markers,
         2] and dL_dx [total_verts, 3] (gradient of the end positions beyond
-        the markers) may be None."""
+        the markers) may be None. relag differentiates the frame's friction
+        lag as a function of its start state and start pose (lag_mode 1)."""
         gm = None if dL_dmarkers is None else self._f32(dL_dmarkers).reshape(self.total_markers, 2)
         gx = None if dL_dx is None else self._f32(dL_dx).reshape(self.total_verts, 3)
         out = torch.empty(self.n_pads, 15, dtype=torch.float64, device=self.device)
@@ -284,7 +285,7 @@ class TacBatch:
         it = torch.empty(self.n_pads, dtype=torch.int32, device=self.device)
         _check(lib().tac_adjoint_frame(self._h, None if gm is None else _ptr(gm), None if gx is None else _ptr(gx),
                                        _ptr(out), _ptr(dx0), _ptr(dv0), _ptr(st), _ptr(it), int(max_iter),
-                                       float(tol), _stream(stream)))
+                                       float(tol), 1 if relag else 0, _stream(stream)))
         self._hold = (gm, gx)
         return out, dx0, dv0, st, it
 

@@ -232,6 +232,59 @@ def test_sequence_autograd_matches_oracle_sweep(tac, oracle_seq):
     b.close()
 
 
+def test_relagged_frame_adjoint_matches_oracle(tac, oracle_seq):
+    """lag_mode 1: frame 3's adjoint with its friction lag differentiated as
+    a function of the frame's start state and start pose, against the
+    oracle's relagged frame adjoint (which is pinned to full re-solves)."""
+    pad, ind, poses, states, cs, gx = oracle_seq
+    th_o, dx_o, dv_o = AD.adjoint_frame(pad, ind, states[2], states[3], cs[2], gx, relag=True)
+    th_f, dx_f, _ = AD.adjoint_frame(pad, ind, states[2], states[3], cs[2], gx)
+    assert _rel(dx_f, dx_o) > 1e-2                   # the lag term is not negligible here
+    pd, mat, ind_s, _ = _scene()
+    w = S.Workload("adjoint", [pd], [mat], [ind_s], 1, poses[:, None, :])
+    b = tac.batch_from_workload(w, tol=TIGHT)
+    b.reset(torch.tensor(poses[0]).reshape(1, 6))
+    for f in (1, 2, 3):
+        b.set_indenter(torch.tensor(poses[f]).reshape(1, 6))
+        st, _ = b.step()
+        assert int(st.item()) == 0
+    th, dx0, dv0, st, it = b.adjoint_frame(torch.tensor(cs[2], dtype=torch.float32),
+                                           torch.tensor(gx, dtype=torch.float32), relag=True)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    got = th.cpu().numpy()[0]
+    scale = np.abs(th_o).max()
+    for k in range(15):
+        assert got[k] == pytest.approx(th_o[k], rel=1e-3, abs=1e-4 * scale), (k, got, th_o)
+    assert _rel(dx0.cpu().numpy().astype(np.float64), dx_o) <= 1e-3
+    assert _rel(dv0.cpu().numpy().astype(np.float64), dv_o) <= 1e-3
+    b.close()
+
+
+def test_relagged_sequence_autograd_matches_oracle_sweep(tac, oracle_seq):
+    """Three frames chained with TacStepFn(relag); loss.backward() against
+    the oracle's relagged reverse sweep."""
+    from paper_2603_28475_b300 import autograd as A
+    pad, ind, poses, states, cs, gx = oracle_seq
+    ref = AD.adjoint_sequence(pad, ind, states, cs, relag=True)
+    pd, mat, ind_s, _ = _scene()
+    w = S.Workload("adjoint", [pd], [mat], [ind_s], 1, poses[:, None, :])
+    b = tac.batch_from_workload(w, tol=TIGHT)
+    b.reset(torch.tensor(poses[0]).reshape(1, 6))
+    x0, v0 = b.get_state()
+    lame = torch.tensor([[pad.lam, pad.mu]], dtype=torch.float64, requires_grad=True)
+    mu_f = torch.tensor([pad.mu_f], dtype=torch.float64, requires_grad=True)
+    P = torch.tensor(poses.astype(np.float64).reshape(4, 1, 6), requires_grad=True)
+    m = A.sequence_markers(b, x0, v0, lame, mu_f, P, relag=True)
+    loss = sum((torch.tensor(c, dtype=torch.float32, device=m.device) * m[f]).sum() for f, c in enumerate(cs))
+    loss.backward()
+    got = np.concatenate([lame.grad.numpy()[0], mu_f.grad.numpy(), P.grad.numpy()[1:, 0].ravel()])
+    scale = np.abs(ref).max()
+    for k in range(ref.size):
+        assert got[k] == pytest.approx(ref[k], rel=2e-3, abs=2e-4 * scale), (k, got, ref)
+    b.close()
+
+
 def test_installed_frame_gives_the_same_adjoint(tac, oracle_seq):
     """tac_set_frame installs frame 3 from its start state, poses and end
     positions without solving; its adjoint equals the adjoint taken right
