@@ -599,7 +599,8 @@ def run_calibrate(args):
     (normalised parameters, population 12, 80 generations; each generation
     one batch of 36 pads) over all four parameters and over (E, nu, mu_f)
     with rho at its nominal value; Adam on (E, nu, mu_f) with adjoint
-    gradients (40 iterations, forward + reverse sweep each) for comparison.
+    gradients (40 iterations, forward + reverse sweep each; the frames'
+    friction lags differentiated, and held fixed) for comparison.
     Prints one JSON line with the loss curves and times."""
     import torch
     from paper_2603_28475_b300 import calibrate as C
@@ -627,12 +628,14 @@ def run_calibrate(args):
     tgt = cal.targets([truth[n] for n in names])
     kappa = cal.kappa[:w.n_pads]
     cal.close()
-    th, h = C.calibrate_adjoint(w, base_r, tgt, iterations=40, lr=0.05, kappa=kappa)
-    runs["adjoint_adam_E_nu_mu_f"] = {
-        "params": list(names), "iterations": 40, "best": dict(zip(names, th.tolist())),
-        "rel_error": {n: abs(b / truth[n] - 1) for n, b in zip(names, th)},
-        "loss": h.mean_loss[::2] + [h.mean_loss[-1]], "pad_frames_solved": h.frames_solved[-1],
-        "seconds": h.seconds[-1], "ms_per_iteration": 1e3 * h.seconds[-1] / 40}
+    for relag in (True, False):
+        th, h = C.calibrate_adjoint(w, base_r, tgt, iterations=40, lr=0.05, kappa=kappa, relag=relag)
+        runs["adjoint_adam_E_nu_mu_f" + ("" if relag else "_frozen_lag")] = {
+            "params": list(names), "iterations": 40, "lag": "differentiated" if relag else "frozen",
+            "best": dict(zip(names, th.tolist())),
+            "rel_error": {n: abs(b / truth[n] - 1) for n, b in zip(names, th)},
+            "loss": h.mean_loss[::2] + [h.mean_loss[-1]], "pad_frames_solved": h.frames_solved[-1],
+            "seconds": h.seconds[-1], "ms_per_iteration": 1e3 * h.seconds[-1] / 40}
     out = {"metric": "baseline calibration on synthetic recordings: loss curves and time (CMA-ES vs adjoint)",
            "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
            "dtype": "f32 (double-float displacements; f64 pair distance, barrier, CCD and reductions)",

@@ -228,10 +228,12 @@ def calibrate_cmaes(cal, targets, generations=80, sigma0=0.3, x0=None, seed=0, c
     return to_theta(es.best_x, cal.names), h
 
 
-def calibrate_adjoint(scenes, base, targets, iterations=40, lr=0.05, x0=None, kappa=None, pair_capacity=8192):
+def calibrate_adjoint(scenes, base, targets, iterations=40, lr=0.05, x0=None, kappa=None, pair_capacity=8192,
+                      relag=True):
     """Adam on the normalised (E, nu, mu_f) with gradients of Eq.
     loss_function from the frames' implicit adjoints (rho stays at
-    ``base.rho``; the adjoint gives no density gradient). One iteration is
+    ``base.rho``; the adjoint gives no density gradient), each frame's
+    friction lag differentiated unless ``relag`` is False. One iteration is
     the forward sequence plus its reverse sweep on the N scenes. Returns
     (theta, History)."""
     import time
@@ -266,7 +268,7 @@ def calibrate_adjoint(scenes, base, targets, iterations=40, lr=0.05, x0=None, ka
         mu = E / (2 * (1 + nu))
         lame = torch.stack([lam, mu]).reshape(1, 2).expand(N, 2)
         mu_f = muf.reshape(1).expand(N)
-        m = A.sequence_markers(b, x0s, v0s, lame, mu_f, poses, base_params=base_params)
+        m = A.sequence_markers(b, x0s, v0s, lame, mu_f, poses, base_params=base_params, relag=relag)
         d = (m.double() - targets.double().to(m.device)).reshape(F, N, n_mk * 2)
         loss = (d * d).sum(dim=2).mean()
         loss.backward()
