@@ -442,15 +442,20 @@ def run_adjoint(args):
     lame = torch.tensor(np.stack([lam, mu], 1), dtype=torch.float64, requires_grad=True)
     mu_f = torch.tensor([q.mu_f for q in base], dtype=torch.float64, requires_grad=True)
     stream = torch.cuda.current_stream()
+    # warm-up: the first two frames forward and backward, untimed
+    mw = A.sequence_markers(b, x0, v0, lame, mu_f, poses[:3], base_params=base)
+    ((mw - targets[:2]) ** 2).sum().backward()
+    lame.grad, mu_f.grad = None, None
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     torch.cuda.synchronize()
-    ev[0].record(stream)
-    m = A.sequence_markers(b, x0, v0, lame, mu_f, poses, base_params=base)
-    loss = ((m - targets) ** 2).sum()
-    ev[1].record(stream)
-    loss.backward()
-    ev[2].record(stream)
-    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        ev[0].record(stream)
+        m = A.sequence_markers(b, x0, v0, lame, mu_f, poses, base_params=base)
+        loss = ((m - targets) ** 2).sum()
+        ev[1].record(stream)
+        loss.backward()
+        ev[2].record(stream)
+        torch.cuda.synchronize()
     fwd, bwd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
     out = {"metric": "adjoint calibration step: 16-frame forward + reverse sweep (calibration workload)",
            "value": (fwd + bwd) / F, "unit": "ms/frame", "higher_is_better": False, "n_gpus": 1,
@@ -461,6 +466,7 @@ def run_adjoint(args):
            "data": "synthetic",
            "config": {"workload": w.name, "envs": w.n_envs, "pads": w.n_pads, "pad_verts": w.pads[0].n_verts,
                       "frames": F, "friction": 0.5, "targets": "GPU forward at hidden per-env (E, nu, mu_f)"},
+           "clocks": clk.summary(), "warmup": "frames 1-2 forward and backward, untimed",
            "loss": float(loss.item()), "grad_norm_lame": float(lame.grad.norm().item()),
            "grad_norm_mu_f": float(mu_f.grad.norm().item())}
     print(json.dumps(out), flush=True)
