@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--envs", type=int, default=4096)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--pair-capacity", type=int, default=8192)
+    ap.add_argument("--pair-capacity", type=int, default=16384)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
@@ -382,7 +382,7 @@ def run_ours(args, rank, world):
                           "pads_per_env": 2, "size_classes_verts": [2070, 4830, 9918],
                           "total_verts": b.total_verts, "total_tets": int(sum(p.n_tets for p in w.pads)),
                           "frames": f"{args.warmup + 1}..{args.warmup + args.steps} of a 0.05 mm/frame press",
-                          "tol_rel_grad": 1e-6, "friction": 0.5,
+                          "tol_rel_grad": 1e-6, "friction": 0.5, "pair_capacity": args.pair_capacity,
                           "rest_shapes": "per-tet Dm^-1" if args.no_dm_table else "Dm^-1 table (structured meshes)",
                           "l2": f"inputs larger than L2 (solver state {v_state:.1f} GB)",
                           "parallelism": f"{world} rank(s), env-sharded"},

@@ -2,14 +2,14 @@
 
 The batched press (4096 environments x 2 pads of the 2k/5k/10k size classes)
 runs through frame 4 exactly as bench.py sets it up (same generator and seed,
-pair capacity 8192, tolerance 1e-6). Then:
+pair capacity 16384, tolerance 1e-6). Then:
 
 * sampled outputs: for a few pads, the FP64 oracle solves the same frame from
   the GPU's own start state (positions and velocities read back before the
   frame) to the same indenter pose, and the GPU's end positions and markers
   must agree within 1e-4 of the gel thickness;
-* properties over every pad: a converged status for all but a small fraction
-  (the benchmark's own convergence criterion), finite positions, and markers
+* properties over every pad: a converged status (the benchmark's own
+  convergence criterion), finite positions, and markers
   inside the displacement range a 1.2 mm press can produce.
 """
 import numpy as np
@@ -39,7 +39,7 @@ def run():
     from paper_2603_28475_b300 import tac as T
     # the generator call of bench.workload(envs, 2 * (warmup + steps) + 1, seed)
     w = S.config_batched(n_envs=N_ENVS, frames=2 * (3 + 3) + 1, seed=0)
-    b = T.batch_from_workload(w, pair_capacity=8192)
+    b = T.batch_from_workload(w, pair_capacity=16384)
     dev = b.device
     poses = torch.tensor(w.poses, dtype=torch.float32, device=dev)
     st = torch.empty(w.n_pads, dtype=torch.int32, device=dev)
@@ -79,8 +79,9 @@ def _sample(r):
 def test_all_pads_report_and_stay_finite(run):
     st = run["status"]
     assert set(np.unique(st).tolist()) <= {0, 1, 2, 3, 4}
-    # bench.py's convergence criterion; the benchmark frames converge 99.86%
-    assert (st == 0).mean() >= 0.99
+    # bench.py's convergence criterion: with the bench's pair capacity every
+    # pad of the benchmark frames converges
+    assert (st == 0).all(), np.unique(st, return_counts=True)
     assert np.isfinite(run["x1"]).all()
     assert np.isfinite(run["mk"]).all()
     # a press of at most 1.2 mm moves no marker further than that
