@@ -140,6 +140,27 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def rank_seed(seed, rank):
+    """Workload seed of a rank: each rank solves its own envs (weak scaling,
+    no data-path exchange)."""
+    return seed + 1000 * rank
+
+
+def job_totals(ms, conv, world, device=None):
+    """Whole-job (time, converged count) of one timed region: the slowest
+    rank's time and the sum of the ranks' converged envs (an all-reduce over
+    the default process group when world > 1)."""
+    if world <= 1:
+        return float(ms), float(conv)
+    import torch
+    t = torch.tensor([float(ms), float(conv)], dtype=torch.float64, device=device)
+    mx = t.clone()
+    torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+    sm = t.clone()
+    torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
+
+
 def workload(envs, frames, seed):
     from paper_2603_28475_b300 import scenes as S
     return S.config_batched(n_envs=envs, frames=frames, seed=seed)
@@ -256,7 +277,7 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     frames = args.warmup + args.steps
-    w = workload(args.envs, 2 * frames + 1, args.seed + 1000 * rank)
+    w = workload(args.envs, 2 * frames + 1, rank_seed(args.seed, rank))
     n_pads = w.n_pads
     t0 = time.time()
     b = tac.batch_from_workload(w, pair_capacity=args.pair_capacity, dm_table=not args.no_dm_table)
@@ -317,15 +338,7 @@ def run_ours(args, rank, world):
     # behind the queue's last pads
     queue = {"ctas": b.grid_ctas, "busy": float(phase[7] / 1e6 / (b.grid_ctas * sum(solve_ms))),
              "longest_pad_ms": pad_ms_max}
-    if world > 1:
-        t = torch.tensor([total_ms, float(conv)], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-        sm = t.clone()
-        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
-        total_ms_job, conv_job = float(mx[0]), float(sm[1])
-    else:
-        total_ms_job, conv_job = total_ms, float(conv)
+    total_ms_job, conv_job = job_totals(total_ms, conv, world, dev)
     value = conv_job / (total_ms_job / 1e3)
     its = np.concatenate(iter_hist)
     bytes_per_launch = bytes_alg / args.steps
@@ -345,6 +358,8 @@ def run_ours(args, rank, world):
         b.reset(poses[args.warmup])
         b.set_state(ck_x, ck_v)
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         t1 = time.perf_counter()
         for s in range(n_e2e):
             f = args.warmup + 1 + s
@@ -357,7 +372,8 @@ def run_ours(args, rank, world):
             torch.cuda.synchronize()
             conv_e += int(np.all(host_st.numpy().reshape(-1, w.pads_per_env) == 0, axis=1).sum())
         dt_e = time.perf_counter() - t1
-        e2e = {"value": conv_e / dt_e * world, "unit": UNIT,
+        ms_e, conv_e = job_totals(1e3 * dt_e, conv_e, world, dev)
+        e2e = {"value": conv_e / (ms_e / 1e3), "unit": UNIT,
                "frames": "the device-timed frames again, from the state after the warm-up",
                "h2d_bytes_per_step": n_pads * 6 * 4,
                "d2h_bytes_per_step": b.total_markers * 2 * 4 + n_pads * 4}
