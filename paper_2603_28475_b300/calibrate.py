@@ -1,5 +1,5 @@
 """Material calibration on top of the batched solve: the baseline calibration of
-TacAlign (Sec. 3.4, Eq. loss_function and Eq. optimization_problem; Supp. C:
+TacAlign (Sec. 4.2, Eq. loss_function and Eq. optimization_problem; Supp. C:
 the parameters normalised to [0, 1], population 12).
 
 * ``CMAES``: the (mu/mu_w, lambda) covariance matrix adaptation evolution

@@ -1,4 +1,4 @@
-"""The calibration drivers on the GPU (Sec. 3.4, Eq. loss_function; Supp. C).
+"""The calibration drivers on the GPU (Sec. 4.2, Eq. loss_function; Supp. C).
 
 Synthetic recordings are the marker fields at hidden parameters. Checked:
 the batched loss of a population equals Eq. loss_function computed from a
