@@ -340,9 +340,13 @@ int tac_marker_map(const tac_pad_desc* pad, int marker_mode, int* ids_host, floa
  * (0 when the mesh needs more than 32 and streams one Dm^-1 per tet; see
  * tac_options.no_dm_table), and the largest deviation of a tet's Dm^-1 from
  * its class representative, relative to the representative's largest entry
- * (at most 1e-5 by construction). Any output pointer may be NULL. Validates
- * the mesh like tac_create_batch (TAC_ERR_INVALID_MESH with a message). */
-int tac_mesh_info(const tac_pad_desc* pad, int* n_patches, int* n_colours, int* n_dm_types, double* dm_dev);
+ * (at most 1e-5 by construction), the rounds a scatter pass takes (a colour
+ * class costs ceil(patches / 8), one patch per warp) and the number of
+ * vertices that two patches of one class share (0 for a valid layout: the
+ * scatter passes rely on it). Any output pointer may be NULL. Validates the
+ * mesh like tac_create_batch (TAC_ERR_INVALID_MESH with a message). */
+int tac_mesh_info(const tac_pad_desc* pad, int* n_patches, int* n_colours, int* n_dm_types, double* dm_dev,
+                  int* n_rounds, int* n_conflicts);
 
 /* Sizes: total vertices, total markers, candidate capacity per pad, and the
  * number of CTAs of one tac_step launch (resident CTAs of the device, at most

@@ -744,7 +744,8 @@ int tac_marker_map(const tac_pad_desc* pad, int marker_mode, int* ids_host, floa
     return TAC_OK;
 }
 
-int tac_mesh_info(const tac_pad_desc* pad, int* n_patches, int* n_colours, int* n_dm_types, double* dm_dev) {
+int tac_mesh_info(const tac_pad_desc* pad, int* n_patches, int* n_colours, int* n_dm_types, double* dm_dev,
+                  int* n_rounds, int* n_conflicts) {
     if (!pad) return fail(TAC_ERR_INVALID_ARG, "null argument");
     PadMesh M;
     std::string err;
@@ -756,6 +757,23 @@ int tac_mesh_info(const tac_pad_desc* pad, int* n_patches, int* n_colours, int* 
     if (n_colours) *n_colours = M.n_colour();
     if (n_dm_types) *n_dm_types = M.n_dm_types();
     if (dm_dev) *dm_dev = M.dm_dev;
+    // scatter rounds (kCtaWarps patches each) and vertices shared within a class
+    int rounds = 0, conflicts = 0;
+    std::vector<int> seen(M.n_v, -1);
+    for (int c = 0; c < M.n_colour(); ++c) {
+        const int a = M.colour_off[c], e = M.colour_off[c + 1];
+        rounds += (e - a + kCtaWarps - 1) / kCtaWarps;
+        for (int q = a; q < e; ++q)
+            for (int l = 0; l < kPatchVerts; ++l) {
+                const int v = M.pvert[(size_t)q * kPatchVerts + l];
+                if (v < 0) continue;
+                const int id = v & kVertMask;
+                if (seen[id] == c) ++conflicts;
+                seen[id] = c;
+            }
+    }
+    if (n_rounds) *n_rounds = rounds;
+    if (n_conflicts) *n_conflicts = conflicts;
     return TAC_OK;
 }
 

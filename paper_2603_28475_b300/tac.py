@@ -78,7 +78,7 @@ def load_library(path=_LIB_PATH):
         "tac_sizes": [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)],
         "tac_marker_map": [ctypes.POINTER(PadDesc), i, vp, vp],
         "tac_mesh_info": [ctypes.POINTER(PadDesc), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
-                          ctypes.POINTER(d)],
+                          ctypes.POINTER(d), ctypes.POINTER(i), ctypes.POINTER(i)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -137,13 +137,18 @@ def _host_desc(pad):
 
 def mesh_info(pad):
     """Host-side layout of one pad's mesh: dict(patches, colours, dm_types,
-    dm_dev) (dm_types 0: per-tet Dm^-1; dm_dev: largest relative deviation
-    of a tet's Dm^-1 from its table class)."""
+    dm_dev, rounds, conflicts) (dm_types 0: per-tet Dm^-1; dm_dev: largest
+    relative deviation of a tet's Dm^-1 from its table class; rounds: warp
+    rounds of a scatter pass; conflicts: vertices shared within a colour
+    class, 0 for a valid layout)."""
     d, keep = _host_desc(pad)
     a, b, c, e = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
-    _check(lib().tac_mesh_info(ctypes.byref(d), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(e)))
+    r, k = ctypes.c_int(), ctypes.c_int()
+    _check(lib().tac_mesh_info(ctypes.byref(d), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(e),
+                               ctypes.byref(r), ctypes.byref(k)))
     del keep
-    return {"patches": a.value, "colours": b.value, "dm_types": c.value, "dm_dev": e.value}
+    return {"patches": a.value, "colours": b.value, "dm_types": c.value, "dm_dev": e.value, "rounds": r.value,
+            "conflicts": k.value}
 
 
 def marker_map(pad, marker_mode=0):

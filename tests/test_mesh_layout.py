@@ -1,5 +1,10 @@
-"""Host-side mesh layout of the library (no device work): the rest-shape
-table of structured meshes.
+"""Host-side mesh layout of the library (no device work): the colour
+classes of the tet patches and the rest-shape table of structured meshes.
+
+Colour classes: no two patches of one class share a vertex (the scatter
+passes write a class's vertices without synchronisation), and the balanced
+classes take no more warp rounds than the greedy colouring did, within a
+few rounds of the bound ceil(patches / 8).
 
 A regular hex-split grid has one rest shape per tet of the cell split (6).
 Its float32 coordinates are exact multiples of the cell size only up to
@@ -61,3 +66,14 @@ def test_irregular_mesh_streams_per_tet_rest_shapes(tac):
     pd = S.hex_pad((18.6 * MM, 14.3 * MM, 4 * MM), (14, 11, 3), jitter=0.25, renumber=True,
                    rng=np.random.default_rng(5))
     assert tac.mesh_info(pd)["dm_types"] == 0
+
+
+@pytest.mark.parametrize("pd", [S.size_class_pad(2000), S.size_class_pad(5000), S.size_class_pad(10000),
+                                S.hex_pad((18.6 * MM, 14.3 * MM, 4 * MM), (14, 11, 3), jitter=0.25, renumber=True,
+                                          rng=np.random.default_rng(9))],
+                         ids=["2k", "5k", "10k", "jittered_renumbered"])
+def test_colour_classes_share_no_vertex_and_are_balanced(tac, pd):
+    info = tac.mesh_info(pd)
+    assert info["conflicts"] == 0
+    bound = -(-info["patches"] // 8)
+    assert bound <= info["rounds"] <= bound + info["colours"] // 4
