@@ -77,3 +77,20 @@ def test_colour_classes_share_no_vertex_and_are_balanced(tac, pd):
     assert info["conflicts"] == 0
     bound = -(-info["patches"] // 8)
     assert bound <= info["rounds"] <= bound + info["colours"] // 4
+
+
+def test_degenerate_meshes_lay_out(tac):
+    """The smallest mesh (one tet) and a pad without markers."""
+    import types
+    one = types.SimpleNamespace(rest=np.array([[0, 0, 0], [1e-3, 0, 0], [0, 1e-3, 0], [0, 0, 1e-3]], np.float32),
+                                tets=np.array([[0, 1, 2, 3]], np.int32), fixed=np.array([0, 1, 2], np.int32),
+                                markers=np.zeros((0, 2), np.float32))
+    info = tac.mesh_info(one)
+    assert (info["patches"], info["colours"], info["rounds"], info["conflicts"], info["dm_types"]) == (1, 1, 1, 0, 1)
+    assert info["dm_dev"] == 0.0
+    for mode in (0, 1):
+        ids, w = tac.marker_map(one, mode)
+        assert ids.shape == (0, 4) and w.shape == (0, 4)
+    pd = S.size_class_pad(2000)
+    bare = types.SimpleNamespace(rest=pd.rest, tets=pd.tets, fixed=pd.fixed, markers=np.zeros((0, 2), np.float32))
+    assert tac.mesh_info(bare)["conflicts"] == 0
