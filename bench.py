@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "converged tactile frames/s (PNCG-IPC) at 4096 envs; % of HBM roofline"
 UNIT = "env-frames/s"
 
-# algorithmic bytes per unit of work of the solve kernel (see DESIGN.md):
+# algorithmic bytes per unit of work of the solve kernel:
 # a tet pass reads each tet's Dm^-1 (36 B), local connectivity (4 B) and
 # corner slots (8 B) once, and per patch vertex the displacement (hi, lo) and
 # the direction (36 B) and, averaged over the two pass kinds, writes the

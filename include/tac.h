@@ -130,7 +130,13 @@ typedef struct {
 
 /* Create a batch of n_pads pads, pads_per_env consecutive pads per
  * environment (n_pads = n_envs * pads_per_env, at most 2^24), one indenter
- * per environment. params has n_pads entries. opts may be NULL (defaults).
+ * per environment (Sec. 3.3: one sensor pad per finger of an environment,
+ * each touched by the environment's object). The rest shape is what Eq.
+ * (varopt) and Eq. (ipc_energy) are built on: per tet the inverse rest edge
+ * matrix Dm^-1 and rest volume of the Neo-Hookean term, per vertex the
+ * lumped mass rho V / 4 summed over its tets (the mass matrix M of the
+ * inertia term), the gel surface whose vertices, triangles and edges form
+ * the contact primitives of the set C, and the marker weights of Sec. 3.2. params has n_pads entries. opts may be NULL (defaults).
  * Validates every mesh on the host (TAC_ERR_INVALID_MESH with the pad index
  * in tac_last_error), builds the rest shape (Dm^-1, volumes, lumped masses),
  * surface primitives, marker weights and the tet patches, allocates all
@@ -139,11 +145,13 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
                      const tac_indenter_desc* indenters, int n_envs, int pads_per_env,
                      const tac_options* opts, void* stream, tac_handle* out);
 
-/* Free all device and host resources of the batch (synchronises its work). */
+/* Free all device and host resources of the batch (synchronises its work).
+ * A service call; the paper has no counterpart. */
 int tac_destroy_batch(tac_handle h);
 
 /* Reset every pad to rest (x = X, v = 0) with the current indenter pose set
- * to pose6_dev (device [n_pads*6]). */
+ * to pose6_dev (device [n_pads*6]): the start of an episode, x^0 and v^0 of
+ * the time stepping of Eq. (varopt). */
 int tac_reset(tac_handle h, const float* pose6_dev, void* stream);
 
 /* Set the indenter pose the next tac_step moves to, per pad (the plugin
@@ -237,12 +245,16 @@ int tac_set_frame(tac_handle h, const float* x0_dev, const float* v0_dev, const 
 int tac_markers(tac_handle h, float* out_dev, void* stream);
 
 /* Copy the vertex state out / in: x_dev, v_dev device [total_verts*3] float
- * (positions and velocities, pads concatenated in order). tac_set_state
+ * (positions and velocities, pads concatenated in order): the x^t and v^t
+ * that the next frame's x-hat = x^t + h v^t of Eq. (varopt) is built from,
+ * and the per-frame checkpoints of a multi-frame adjoint. tac_set_state
  * keeps the current pose. */
 int tac_get_state(tac_handle h, float* x_dev, float* v_dev, void* stream);
 int tac_set_state(tac_handle h, const float* x_dev, const float* v_dev, void* stream);
 
-/* Replace the material / solver parameters of all pads (host [n_pads]). */
+/* Replace the material / solver parameters of all pads (host [n_pads]):
+ * the per-environment material randomisation of Supp. C and the candidate
+ * (E, nu, rho, mu_f) of a calibration step (Sec. 4.2). */
 int tac_set_params(tac_handle h, const tac_params* per_pad, int n);
 
 /* The parameters in effect per pad (host [n]): as last set, with kappa and
@@ -284,9 +296,15 @@ int tac_broadphase(tac_handle h, int pad, const float* x_dev, const float* y_dev
  * capacity slots; a larger request fails with TAC_ERR_INVALID_ARG before any
  * device work. Each scratch entry a call reads is written earlier by the
  * same call, so the contents left by the previous call need no clearing.
+ * Preconditions the call does not check: every id in surf_verts_dev,
+ * surf_tris_dev and surf_edges_dev is below the number of vertices in x_dev,
+ * and every id in ind_tris_dev and ind_edges_dev is below n_ind_verts; an id
+ * out of range reads outside the caller's arrays.
  * The first call on a device looks up the device address of the array and
  * sets the kernel's shared-memory limit: make that first call before any
- * stream capture. All calls share the one array, so calls whose GPU work
+ * stream capture. The address is kept per device ordinal for the life of the
+ * process; after a cudaDeviceReset it is stale and the library must not be
+ * called on that device again. All calls share the one array, so calls whose GPU work
  * overlaps (different streams or threads on one device) race on it and must
  * be serialised by the caller. */
 int tac_broadphase_static(const float* x_dev, const int* surf_verts_dev, int n_surf_verts,
@@ -350,7 +368,8 @@ int tac_mesh_info(const tac_pad_desc* pad, int* n_patches, int* n_colours, int* 
 
 /* Sizes: total vertices, total markers, candidate capacity per pad, and the
  * number of CTAs of one tac_step launch (resident CTAs of the device, at most
- * one per pad). Any output pointer may be NULL. */
+ * one per pad). A service call for sizing caller buffers; the paper has no
+ * counterpart. Any output pointer may be NULL. */
 int tac_sizes(tac_handle h, int* total_verts, int* total_markers, int* pair_capacity, int* grid_ctas);
 
 /* Message of the last error on this thread (static storage, never NULL). */

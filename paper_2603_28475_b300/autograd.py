@@ -17,10 +17,25 @@ reverse sweep.
 from __future__ import annotations
 
 import copy
+import warnings
 
 import torch
 
 from . import tac as T
+
+
+class NotConvergedWarning(UserWarning):
+    """A frame's forward solve ended on a pad that did not converge, so its
+    adjoint is taken at a state that is not an equilibrium."""
+
+
+def _check_forward_status(status):
+    """Warns when the forward solve of a frame left pads unconverged: the
+    implicit-function adjoint assumes grad E = 0 at the end state."""
+    bad = int((status != 0).sum().item())
+    if bad:
+        warnings.warn(f"{bad} pad(s) of the forward frame did not converge; the adjoint at their end state "
+                      "is not the derivative of an equilibrium", NotConvergedWarning, stacklevel=3)
 
 
 def lame_to_young(lam, mu):
@@ -65,6 +80,7 @@ class TacFrameFn(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, grad_m):
+        _check_forward_status(ctx.status)
         g, st, it = ctx.batch.adjoint(grad_m.contiguous(), tol=ctx.tol)
         lame, mu_f, pose = ctx.like
         to = lambda t, ref: t.to(device=ref.device, dtype=ref.dtype).reshape(ref.shape)
@@ -131,6 +147,7 @@ class TacStepFn(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, gm, gx1, gv1):
+        _check_forward_status(ctx.status)
         b = ctx.batch
         lame, mu_f, pose_s, pose_e, x0, v0, x1 = ctx.inputs
         _set_material(b, ctx.base, lame, mu_f)

@@ -1,0 +1,188 @@
+"""Pins of two oracle functions that the GPU is compared against directly:
+the conservative step bound alpha_ccd of the per-pair CCD (its defining
+property, and exactness where the closing speed is known) and the
+candidate predicate of the set C of Eq. (ipc_energy) at its exact boundary
+(inflated-AABB gaps of r and r + one float32 ulp, decided against exact
+rational arithmetic)."""
+from fractions import Fraction
+from types import SimpleNamespace
+
+import numpy as np
+import pytest
+
+from oracle import broadphase as BP
+from oracle import energy as En
+from oracle import geometry as G
+from oracle import solver as SV
+
+from _cases import MM, small_indenter, tiny_pad
+
+DH = 0.05 * MM
+ETA = 0.9
+
+
+def _frame_near_contact(seed):
+    """Tiny jittered pad with a small icosphere 0.3 dhat above its top face:
+    candidates of all three types, indenter fixed (s = 0)."""
+    pd, pad = tiny_pad(cells=(3, 3, 1), size=(3 * MM, 3 * MM, 1 * MM), jitter=0.1, seed=seed)
+    _, ind = small_indenter(radius=0.6 * MM, subdiv=1)
+    ztop = pad.rest[:, 2].max()
+    pose = np.array([0.3, -0.2, 0.1, 1.4 * MM, 1.6 * MM, 0.0])
+    y0 = G.indenter_world(ind.verts, pose)
+    pose[5] = ztop - y0[:, 2].min() + 0.3 * DH
+    y = G.indenter_world(ind.verts, pose)
+    x = pad.rest.astype(np.float64)
+    lag = En.friction_lag(np.zeros((0, 3), np.int64), x, y, pad, ind)
+    fr = En.Frame(pad, ind, x, x.copy(), y, y, lag)
+    pairs = BP.candidates(x, y, pad, ind, 2 * DH)
+    return fr, x, y, pairs
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_ccd_bound_keeps_every_candidate_gap(seed):
+    """For every alpha in (0, alpha_ccd], every candidate keeps
+    d_k(x + alpha p) >= (1 - eta) d_k(x): the property the step bound of
+    the line search exists for. Random directions, some pushing the gel up
+    into the indenter."""
+    fr, x, y, pairs = _frame_near_contact(seed)
+    d0, _, _ = En.distances(pairs, x, y, fr.pad, fr.ind)
+    assert len(pairs) > 0 and d0.min() > 0
+    rng = np.random.default_rng(100 + seed)
+    for trial in range(6):
+        p = rng.normal(size=x.shape) * 1e-4
+        if trial % 2:
+            p[:, 2] = np.abs(p[:, 2]) * 3.0        # toward the indenter above
+        a = SV.ccd_bound(fr, x, p, 0.0, pairs, ETA)
+        assert np.isfinite(a) and a > 0
+        for al in np.linspace(0.0, a, 17)[1:]:
+            d, _, _ = En.distances(pairs, x + al * p, y, fr.pad, fr.ind)
+            assert np.all(d >= (1.0 - ETA) * d0 * (1.0 - 1e-9)), (trial, al / a)
+
+
+def test_ccd_bound_is_tight_for_a_rigid_approach():
+    """The whole gel translating straight up at speed c: every gel
+    primitive closes on the indenter at most at rate c, and the pair over a
+    face closes exactly at rate c. alpha_ccd must then be eta * d_min / c,
+    and at alpha_ccd the closest pair has exactly (1 - eta) of its gap
+    left (a bound built from the wrong side's speeds, or off by a factor,
+    fails one of the two)."""
+    pad_pd, pad = tiny_pad(cells=(3, 3, 1), size=(3 * MM, 3 * MM, 1 * MM))
+    # a flat horizontal indenter triangle above the pad centre: the closest
+    # pairs are gel vertices under its face, with a vertical normal
+    ztop = pad.rest[:, 2].max()
+    gap = 0.4 * DH
+    cx, cy = 1.5 * MM, 1.5 * MM
+    yv = np.array([[cx - 1.2 * MM, cy - 1.2 * MM, ztop + gap], [cx + 1.3 * MM, cy - 1.1 * MM, ztop + gap],
+                   [cx, cy + 1.4 * MM, ztop + gap]])
+    ind = G.build_indenter(yv.astype(np.float32), np.array([[0, 2, 1]], np.int32))
+    y = ind.verts.astype(np.float64)
+    x = pad.rest.astype(np.float64)
+    lag = En.friction_lag(np.zeros((0, 3), np.int64), x, y, pad, ind)
+    fr = En.Frame(pad, ind, x, x.copy(), y, y, lag)
+    pairs = BP.candidates(x, y, pad, ind, 2 * DH)
+    d0, _, _ = En.distances(pairs, x, y, pad, ind)
+    c = 3.0e-4
+    p = np.zeros_like(x)
+    p[:, 2] = c
+    a = SV.ccd_bound(fr, x, p, 0.0, pairs, ETA)
+    assert a == pytest.approx(ETA * d0.min() / c, rel=1e-12)
+    d1, _, _ = En.distances(pairs, x + a * p, y, pad, ind)
+    k = int(np.argmin(d0))
+    assert d1[k] == pytest.approx((1.0 - ETA) * d0[k], rel=1e-6)
+    assert np.all(d1 >= (1.0 - ETA) * d0 * (1.0 - 1e-9))
+
+
+# ---------------------------------------------------------------------------
+# the candidate predicate at its boundary
+
+
+def _f32(v):
+    return np.float32(v)
+
+
+def _boundary_value(base, r, up):
+    """float32 coordinates L next to base + r (base float32, r float64):
+    the largest L with L - base <= r (exactly) or, with ``up``, the smallest
+    L with L - base > r."""
+    B, R = Fraction(float(base)), Fraction(float(r))
+    L = _f32(float(base) + float(r))
+    while Fraction(float(L)) - B > R:
+        L = np.nextafter(L, np.float32(-np.inf))
+    while Fraction(float(np.nextafter(L, np.float32(np.inf)))) - B <= R:
+        L = np.nextafter(L, np.float32(np.inf))
+    return np.nextafter(L, np.float32(np.inf)) if up else L
+
+
+def _exact_overlap(gp, ip, r):
+    """Exact rational inflated-AABB predicate for one pair of primitives."""
+    R = Fraction(float(r))
+    for a in range(3):
+        glo = min(Fraction(float(v[a])) for v in gp)
+        ghi = max(Fraction(float(v[a])) for v in gp)
+        ilo = min(Fraction(float(v[a])) for v in ip)
+        ihi = max(Fraction(float(v[a])) for v in ip)
+        if not (glo - R <= ihi and ilo <= ghi + R):
+            return False
+    return True
+
+
+def _tiny_models(xg, yi):
+    """A gel surface of one triangle (its 3 vertices and 3 edges) and an
+    indenter of one triangle (3 vertices, 3 edges)."""
+    pad = SimpleNamespace(surf_verts=np.array([0, 1, 2]), surf_tris=np.array([[0, 1, 2]]),
+                          surf_edges=np.array([[0, 1], [0, 2], [1, 2]]))
+    ind = SimpleNamespace(tris=np.array([[0, 1, 2]]), edges=np.array([[0, 1], [0, 2], [1, 2]]),
+                          verts=yi)
+    return pad, ind
+
+
+def _exact_set(xg, yi, pad, ind, r):
+    out = []
+    for i in pad.surf_verts:
+        for j in range(ind.tris.shape[0]):
+            if _exact_overlap([xg[i]], yi[ind.tris[j]], r):
+                out.append((0, int(i), j))
+    for i in range(pad.surf_tris.shape[0]):
+        for j in range(yi.shape[0]):
+            if _exact_overlap(xg[pad.surf_tris[i]], [yi[j]], r):
+                out.append((1, i, j))
+    for i in range(pad.surf_edges.shape[0]):
+        for j in range(ind.edges.shape[0]):
+            if _exact_overlap(xg[pad.surf_edges[i]], yi[ind.edges[j]], r):
+                out.append((2, i, j))
+    return sorted(out)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("side", [1, -1])
+@pytest.mark.parametrize("r", [(DH + DH) * (1.0 + 1e-6), 2.0 ** -13])
+def test_candidate_predicate_at_exact_boundary(axis, side, r):
+    """Indenter placed so that its box's gap to the gel box along one axis
+    is r (within float32 placement: the last float32 at or below it) or one
+    float32 ulp beyond: the pairs across that gap are candidates in the
+    first case and not in the second, exactly as rational arithmetic
+    decides. With r = 2^-13 the gap is r exactly (float32 coordinates hold
+    it), so the comparison's equality case is taken too. An over-inclusive
+    predicate (inflation 2r, or r on both boxes) or a strict inequality
+    fails here."""
+    xg = np.array([[1.25e-3, 2.5e-3, 1.0e-3], [1.75e-3, 2.625e-3, 1.125e-3], [1.5e-3, 3.0e-3, 1.0625e-3]],
+                  dtype=np.float32)
+    base = (xg[:, axis].max() if side > 0 else xg[:, axis].min())
+    for up in (False, True):
+        # a triangle overlapping the gel box on the other axes, lying beyond it on this axis
+        yi = np.array([[1.3e-3, 2.55e-3, 1.05e-3], [1.7e-3, 2.6e-3, 1.1e-3], [1.5e-3, 2.9e-3, 1.06e-3]],
+                      dtype=np.float32)
+        if side > 0:
+            L = _boundary_value(base, r, up)
+            shift = [L, L + _f32(1e-5), L + _f32(2e-5)]
+        else:
+            L = -_boundary_value(-base, r, up)       # mirrored: base - L <= r
+            shift = [L, L - _f32(1e-5), L - _f32(2e-5)]
+        yi[:, axis] = np.array(shift, dtype=np.float32)
+        pad, ind = _tiny_models(xg, yi)
+        got = BP.candidates(xg.astype(np.float64), yi.astype(np.float64), pad, ind, r)
+        want = _exact_set(xg, yi, pad, ind, r)
+        assert [tuple(t) for t in got.tolist()] == want, (axis, side, up)
+        # the vertex-triangle pair whose gap is the boundary itself
+        gv = int(np.argmax(xg[:, axis])) if side > 0 else int(np.argmin(xg[:, axis]))
+        assert ((0, gv, 0) in want) == (not up)
