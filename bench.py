@@ -9,13 +9,16 @@ drawn from the 2k / 5k / 10k-vertex size classes, a cylinder peg per env
 (r ~ U[2, 4] mm) pressed into each pad at 0.05 mm per frame from a dhat gap
 with a random pose (+-15 deg, +-1 mm) up to a depth ~ U[0, 1.2] mm, friction
 0.5. One step = one frame for every pad: set the target poses, solve
-(tac_step), read the markers. W warm-up frames, then K timed frames.
+(tac_step), read the markers. W warm-up frames, then K timed frames; the
+defaults (W = 5, K = 20) time frames 6..25, which take every pad through
+its deepest press into the hold.
 Under torchrun every rank solves its own E environments (weak scaling).
 """
 from __future__ import annotations
 
 import argparse
 import json
+import multiprocessing
 import os
 import subprocess
 import sys
@@ -37,22 +40,27 @@ UNIT = "env-frames/s"
 # algorithmic bytes per unit of work of the solve kernel:
 # a tet pass reads each tet's Dm^-1 (36 B), local connectivity (4 B) and
 # corner slots (8 B) once, and per patch vertex the displacement (hi, lo) and
-# the direction (36 B) and, averaged over the two pass kinds, writes the
-# gradient and diagonal block (36 B / 2); a vertex pass moves ~120 B per
-# vertex; a pair evaluation ~64 B per candidate pair. A mesh with a Dm^-1
-# table (the structured case) reads no per-tet Dm^-1.
+# the direction (36 B); a gradient pass also writes the gradient and the
+# diagonal block (36 B per vertex), the p^T H p pass writes none; a vertex
+# pass moves ~120 B per vertex; a pair evaluation ~64 B per candidate pair.
+# A mesh with a Dm^-1 table (the structured case) reads no per-tet Dm^-1.
 B_TET = 48.0
 B_DM = 36.0
-B_TET_VERT = 36.0 + 18.0
+B_TET_VERT_PHP = 36.0
+B_TET_VERT_GRAD = 72.0
 B_VERT_PASS = 120.0
 B_PAIR = 64.0
+# the per-iteration byte model of the workload's planning (both tet passes at
+# 56 B per tet, 150 B per vertex of vector traffic)
+B_ITER_TET = 112.0
+B_ITER_VERT = 150.0
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--envs", type=int, default=4096)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--pair-capacity", type=int, default=16384)
@@ -69,6 +77,16 @@ def parse():
                     help="stream one Dm^-1 per tet even for structured meshes (the unstructured form)")
     ap.add_argument("--calibrate", action="store_true",
                     help="CMA-ES (population 12, 80 generations) and adjoint-gradient calibration instead")
+    ap.add_argument("--fp32-steps", type=int, default=1,
+                    help="frames of the plain FP32 form timed beside the chosen form (0: skip)")
+    ap.add_argument("--fp32-max-iter", type=int, default=500,
+                    help="iteration cap of the plain FP32 form (it stalls short of the tolerance)")
+    ap.add_argument("--per-frame", action="store_true",
+                    help="add each timed frame's convergence record (statuses, iterations, substeps, queue use) "
+                         "to the JSON line")
+    ap.add_argument("--calibrate-oracle", action="store_true",
+                    help="per-environment CMA-ES and adjoint calibration against the FP64 oracle's targets "
+                         "(tests/golden/calibration_targets.npz) instead")
     ap.add_argument("--variants", action="store_true",
                     help="iterations and throughput of the paper-literal variants on the batched workload instead")
     return ap.parse_args()
@@ -180,14 +198,33 @@ def tabled(pad, dm_table=True):
     return _TABLED[key]
 
 
-def algorithmic_bytes(stats, w, dm_table=True):
-    """Counted bytes of one solve launch from the per-pad counters."""
-    tot = 0.0
+def phase_bytes(stats, w, dm_table=True):
+    """Counted bytes of one solve launch from the per-pad counters, by phase:
+    (p^T H p tet passes, gradient tet passes, vertex passes, pair passes).
+    A pad runs one p^T H p tet pass per PNCG iteration; its other tet passes
+    are gradient passes."""
+    out = np.zeros(4)
     for k, pad in enumerate(w.pads):
         it, sub, reb, hal, tp, vp, pe, peak = [float(v) for v in stats[k][:8]]
         bt = B_TET - (B_DM if tabled(pad, dm_table) else 0.0)
-        tot += tp * (bt * pad.n_tets + B_TET_VERT * pad.n_verts) + vp * B_VERT_PASS * pad.n_verts + pe * B_PAIR
-    return tot
+        n_php = min(it, tp)
+        out[0] += n_php * (bt * pad.n_tets + B_TET_VERT_PHP * pad.n_verts)
+        out[1] += (tp - n_php) * (bt * pad.n_tets + B_TET_VERT_GRAD * pad.n_verts)
+        out[2] += vp * B_VERT_PASS * pad.n_verts
+        out[3] += pe * B_PAIR
+    return out
+
+
+def algorithmic_bytes(stats, w, dm_table=True):
+    """Counted bytes of one solve launch from the per-pad counters."""
+    return float(phase_bytes(stats, w, dm_table).sum())
+
+
+def iteration_model_bytes(stats, w):
+    """Bytes of one launch under the per-iteration model 112 T + 150 V (two
+    tet passes of 56 B per tet and the vector traffic per PNCG iteration)."""
+    return float(sum(float(stats[k][0]) * (B_ITER_TET * p.n_tets + B_ITER_VERT * p.n_verts)
+                     for k, p in enumerate(w.pads)))
 
 
 def kernel_hash():
@@ -217,56 +254,115 @@ def committed_traffic(bytes_alg_per_launch):
 
 # --------------------------------------------------------------------------- oracle sample
 
-def class_mean_tets():
-    """Expected tet count of a pad when classes are drawn uniformly."""
-    from paper_2603_28475_b300 import scenes as S
-    return float(np.mean([6 * a * b * c for a, b, c in S.SIZE_CLASSES.values()]))
+def sample_envs(w, n):
+    """The oracle's sample of a workload: the first n environments whose pads
+    are all of the smallest size class (so that a frame of the sample takes
+    seconds on one core per pad), and the factor from one such env-frame to
+    an average env-frame of the workload (the ratio of tet counts)."""
+    small = min(p.n_verts for p in w.pads)
+    envs = [e for e in range(w.n_envs)
+            if all(w.pads[w.pads_per_env * e + q].n_verts == small for q in range(w.pads_per_env))][:n]
+    mean_env = np.mean([sum(w.pads[w.pads_per_env * e + q].n_tets for q in range(w.pads_per_env))
+                        for e in range(w.n_envs)])
+    sample_env = sum(w.pads[w.pads_per_env * envs[0] + q].n_tets for q in range(w.pads_per_env))
+    return envs, mean_env / sample_env
 
 
-def oracle_sample(w, frame_pose_idx=1):
-    """The oracle as it stands on one pad of the smallest size class for one
-    frame (contact from rest). Returns (seconds, pad index, scale) where scale
-    converts one such pad-frame into one average env-frame of the workload
-    (2 pads, tet count averaged over the workload's pads)."""
+_ORACLE_MODELS = {}
+
+
+def oracle_pad_frame(task):
+    """One pad-frame of the FP64 oracle as it stands (runs in a spawned
+    worker; the pad model is built once per worker and not timed). Returns
+    (key, x, v, solve seconds, iterations, status)."""
+    key, pad_arrays, material, ind_arrays, x, v, pose_t, pose_n = task
     from oracle import geometry as G
     from oracle import solver as SV
-    f32 = lambda v: float(np.float32(v))
-    k = int(np.argmin([p.n_tets for p in w.pads]))
-    pd, m = w.pads[k], w.materials[k]
-    pad = G.build_pad(pd.rest, pd.tets, pd.fixed, pd.markers, f32(m.E), f32(m.nu), f32(m.rho), f32(m.h),
-                      f32(m.dhat), f32(m.mu_f))
-    e = k // w.pads_per_env
-    ind = G.build_indenter(w.indenters[e].verts, w.indenters[e].tris)
-    st = SV.rest_state(pad, w.poses[0, k].astype(np.float64))
+    if key not in _ORACLE_MODELS:
+        rest, tets, fixed, markers = pad_arrays
+        f32 = lambda a: float(np.float32(a))
+        E, nu, rho, h, dhat, mu_f = material
+        pad = G.build_pad(rest, tets, fixed, markers, f32(E), f32(nu), f32(rho), f32(h), f32(dhat), f32(mu_f))
+        _ORACLE_MODELS[key] = (pad, G.build_indenter(*ind_arrays))
+    pad, ind = _ORACLE_MODELS[key]
+    st = SV.State(x=np.asarray(x, np.float64), v=np.asarray(v, np.float64), pose=np.asarray(pose_t, np.float64))
     t = time.perf_counter()
-    st, info = SV.solve_frame(pad, ind, st, w.poses[frame_pose_idx, k].astype(np.float64))
-    dt = time.perf_counter() - t
-    scale = w.pads_per_env * class_mean_tets() / pd.n_tets
-    return dt, k, scale, info
+    new, info = SV.solve_frame(pad, ind, st, np.asarray(pose_n, np.float64))
+    return key, new.x, new.v, time.perf_counter() - t, info.iters, info.status
+
+
+def _oracle_task(w, k, x, v, f):
+    pd, m = w.pads[k], w.materials[k]
+    ind = w.indenters[k // w.pads_per_env]
+    return (k, (pd.rest, pd.tets, pd.fixed, pd.markers), (m.E, m.nu, m.rho, m.h, m.dhat, m.mu_f),
+            (ind.verts, ind.tris), x, v, w.poses[f - 1, k], w.poses[f, k])
+
+
+def oracle_pool(n):
+    """A pool of n spawned workers with single-threaded BLAS (spawn: a pool
+    forked from a process that holds a CUDA context hangs)."""
+    return multiprocessing.get_context("spawn").Pool(n)
+
+
+def oracle_frame_step(pool, w, envs, states, f):
+    """Frame f for every pad of the sample envs, the pads in parallel on the
+    pool's cores. states: {pad: (x, v)} updated in place. Returns the
+    step's time (its slowest pad: the pads run concurrently) and the pads'
+    iterations."""
+    pads = [w.pads_per_env * e + q for e in envs for q in range(w.pads_per_env)]
+    res = pool.map(oracle_pad_frame, [_oracle_task(w, k, states[k][0], states[k][1], f) for k in pads])
+    for k, x, v, dt, it, stt in res:
+        states[k] = (x, v)
+    return max(r[3] for r in res), [r[4] for r in res]
 
 
 # --------------------------------------------------------------------------- arms
 
+def oracle_cores():
+    """Host cores the oracle sample uses: one per pad of the sample, at most
+    8 pads (4 environments)."""
+    n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    return max(1, min(8, n))
+
+
 def run_reference(args, rank, world):
+    """The FP64 oracle as it stands on the host cores, on a sample of the
+    same workload: the first environments whose pads are both of the 2k
+    class (one pad per core), run from rest through the same frames as the
+    GPU arm (W warm-up frames, then K timed frames), each frame's pads in
+    parallel. A step's time is its slowest pad; the value is the sample's
+    env-frames per second scaled by tet count to an average env-frame."""
     if rank != 0:
         return
-    w = workload(min(args.envs, 8), 2, args.seed)
-    times = []
-    info = None
-    for i in range(args.warmup + args.steps):
-        dt, k, scale, info = oracle_sample(w)
-        if i >= args.warmup:
-            times.append(dt * scale)
-    t_env = float(np.mean(times))
+    cores = oracle_cores()
+    w = workload(args.envs, args.warmup + args.steps + 1, args.seed)
+    envs, scale = sample_envs(w, max(1, cores // w.pads_per_env))
+    states = {}
+    for e in envs:
+        for q in range(w.pads_per_env):
+            k = w.pads_per_env * e + q
+            states[k] = (w.pads[k].rest.astype(np.float64), np.zeros((w.pads[k].n_verts, 3)))
+    n_pads = len(states)
+    times, iters = [], []
+    with oracle_pool(n_pads) as pool:
+        for f in range(1, args.warmup + args.steps + 1):
+            dt, its = oracle_frame_step(pool, w, envs, states, f)
+            if f > args.warmup:
+                times.append(dt)
+                iters += its
+    t_env = float(np.mean(times)) * scale / len(envs)
     value = 1.0 / t_env
-    sample = (f"oracle (numpy FP64, 1 thread) on one {w.pads[k].n_verts}-vert pad for its first contact frame "
-              f"({info.iters} iterations), scaled by {scale:.2f} to one average env-frame of the workload "
-              "(2 pads, mean tet count of the size classes)")
+    sample = (f"oracle (numpy FP64) on {len(envs)} env(s) x {w.pads_per_env} pads of the "
+              f"{w.pads[2 * envs[0]].n_verts}-vertex class, one pad per core, from rest through frames "
+              f"1..{args.warmup + args.steps} (frames {args.warmup + 1}..{args.warmup + args.steps} timed, "
+              f"{np.mean(iters):.0f} iterations per pad-frame); a step is its slowest pad; scaled by {scale:.2f} "
+              "(tet count) to an average env-frame of the workload (extrapolated)")
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_env * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": f"batched_{args.envs}env_x2pads", "envs": args.envs},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "config": {"workload": f"batched_{args.envs}env_x2pads", "envs": args.envs,
+                      "frames": f"{args.warmup + 1}..{args.warmup + args.steps} of a 0.05 mm/frame press"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": n_pads, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -315,7 +411,7 @@ def run_ours(args, rank, world):
             ev[s][1].record(stream)
             b.markers(mk)
             st = b.stats()
-            stats_all.append((status.clone(), iters.clone(), st))
+            stats_all.append((status.clone(), iters.clone(), st, b.norms()))
         stop.record(stream)
         torch.cuda.synchronize()
     if world > 1:
@@ -323,21 +419,46 @@ def run_ours(args, rank, world):
     total_ms = start.elapsed_time(stop)
     solve_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
     phase = np.zeros(8)
-    pad_ms_max = 0.0
-    for stt, it, st in stats_all:
+    pbytes = np.zeros(4)
+    bytes_iter_model = 0.0
+    pad_ms = []
+    floor_stops, pad_frames = 0, 0
+    for stt, it, st, nr in stats_all:
         s_np = stt.cpu().numpy().reshape(-1, w.pads_per_env)
         conv += int(np.all(s_np == 0, axis=1).sum())
         iter_hist.append(it.cpu().numpy())
         st_np = st.cpu().numpy()
-        bytes_alg += algorithmic_bytes(st_np, w, not args.no_dm_table)
+        pbytes += phase_bytes(st_np, w, not args.no_dm_table)
+        bytes_iter_model += iteration_model_bytes(st_np, w)
         phase += st_np[:, 8:16].sum(axis=0)
-        pad_ms_max = max(pad_ms_max, float(st_np[:, 15].max()) / 1e6)
+        pad_ms.append(st_np[:, 15] / 1e6)
+        # pads whose stopping target was the float32 resolution floor rather
+        # than tol * g_ref (norms: final |g|, target, g_ref, force scale)
+        nr_np = nr.cpu().numpy()
+        floor_stops += int((nr_np[:, 1] > 1e-6 * nr_np[:, 2] * (1.0 + 1e-6)).sum())
+        pad_frames += nr_np.shape[0]
+    bytes_alg = float(pbytes.sum())
+    per_frame = []
+    if args.per_frame:
+        for q, (stt, it, st, nr) in enumerate(stats_all):
+            sn, st_np, nr_np = stt.cpu().numpy(), st.cpu().numpy(), nr.cpu().numpy()
+            per_frame.append({
+                "frame": args.warmup + 1 + q, "ms": solve_ms[q],
+                "status": {str(int(a)): int(c) for a, c in zip(*np.unique(sn, return_counts=True))},
+                "iters": [float(np.percentile(st_np[:, 0], 50)), float(np.percentile(st_np[:, 0], 99)),
+                          int(st_np[:, 0].max())],
+                "substeps": [float(np.percentile(st_np[:, 1], 99)), int(st_np[:, 1].max())],
+                "halvings_per_pad": float(st_np[:, 3].mean()),
+                "busy": float(st_np[:, 15].sum() / 1e6 / (b.grid_ctas * solve_ms[q])),
+                "longest_pad_ms": float(st_np[:, 15].max() / 1e6),
+                "float32_floor_stops": float((nr_np[:, 1] > 1e-6 * nr_np[:, 2] * (1.0 + 1e-6)).mean())})
+    pad_ms = np.concatenate(pad_ms)
     names = ["tet_pHp", "tet_grad", "pair_pHp", "pair_grad", "vertex", "advance_rebuild", "setup"]
     phase_share = {n: float(phase[i] / phase[7]) for i, n in enumerate(names)} if phase[7] > 0 else None
     # CTA-time spent inside pads over the launch's CTA-time: below 1 the grid idles
     # behind the queue's last pads
     queue = {"ctas": b.grid_ctas, "busy": float(phase[7] / 1e6 / (b.grid_ctas * sum(solve_ms))),
-             "longest_pad_ms": pad_ms_max}
+             "longest_pad_ms": float(pad_ms.max())}
     total_ms_job, conv_job = job_totals(total_ms, conv, world, dev)
     value = conv_job / (total_ms_job / 1e3)
     its = np.concatenate(iter_hist)
@@ -345,7 +466,18 @@ def run_ours(args, rank, world):
     launch_ms = float(np.mean(solve_ms))
     peak, peak_kind = load_peaks()
     achieved = bytes_per_launch / (launch_ms / 1e3) / 1e9
+    achieved_iter_model = bytes_iter_model / args.steps / (launch_ms / 1e3) / 1e9
     traffic = committed_traffic(bytes_per_launch)
+    # per phase: its counted bytes over the CTA-seconds it took, spread over
+    # the grid's resident CTAs (the bandwidth the phase draws while it runs)
+    phase_gbs = {}
+    for nm, by, cols in (("elastic_tet_passes", pbytes[0] + pbytes[1], (0, 1)), ("tet_pHp", pbytes[0], (0,)),
+                         ("tet_grad", pbytes[1], (1,)), ("barrier_pair_passes", pbytes[3], (2, 3)),
+                         ("vertex", pbytes[2], (4,))):
+        ns = sum(phase[c] for c in cols)
+        if ns > 0:
+            gbs = by / (ns / 1e9 / b.grid_ctas) / 1e9
+            phase_gbs[nm] = {"achieved_gbs": gbs, "frac": gbs / peak}
     # end to end through the public API with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -380,13 +512,69 @@ def run_ours(args, rank, world):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            dt, k, scale, info = oracle_sample(w)
-            cpu = {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"oracle (numpy FP64, 1 thread) on one {w.pads[k].n_verts}-vert pad, first contact "
-                             f"frame ({info.iters} iterations, {dt:.1f} s), scaled by {scale:.2f} to an average "
-                             "env-frame (2 pads, mean tet count of the size classes)"}
+            # the first timed frame of the same workload from the GPU's own
+            # start state, for a sample of 2k-class environments, one pad per
+            # host core
+            cores = oracle_cores()
+            envs, scale = sample_envs(w, max(1, cores // w.pads_per_env))
+            xs, vs = ck_x.cpu().numpy(), ck_v.cpu().numpy()
+            vo = b.vert_offsets
+            states = {}
+            for e in envs:
+                for q in range(w.pads_per_env):
+                    k = w.pads_per_env * e + q
+                    states[k] = (xs[vo[k]:vo[k + 1]], vs[vo[k]:vo[k + 1]])
+            f = args.warmup + 1
+            with oracle_pool(len(states)) as pool:
+                dt, o_its = oracle_frame_step(pool, w, envs, states, f)
+            cpu = {"value": len(envs) / (dt * scale), "unit": UNIT, "cores": len(states), "kind": "oracle",
+                   "sample": f"oracle (numpy FP64) on {len(envs)} env(s) x {w.pads_per_env} pads of the "
+                             f"{w.pads[w.pads_per_env * envs[0]].n_verts}-vertex class, frame {f} from the GPU's "
+                             f"start state, one pad per core ({np.mean(o_its):.0f} iterations per pad, slowest pad "
+                             f"{dt:.1f} s), scaled by {scale:.2f} (tet count) to an average env-frame (extrapolated)"}
         except Exception as exc:             # the GPU line is still reported
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {exc!r}"}
+    # the plain FP32 form on the same frames from the same start state (the
+    # state after the warm-up): same tolerance, iteration cap bounded
+    fp32 = None
+    if args.fp32_steps > 0:
+        k32 = min(args.steps, args.fp32_steps)
+        b32 = tac.batch_from_workload(w, pair_capacity=args.pair_capacity, dm_table=not args.no_dm_table,
+                                      precision=1, max_iter=args.fp32_max_iter)
+        b32.reset(poses[args.warmup])
+        b32.set_state(ck_x, ck_v)
+        ms32, conv32, st32, it32 = [], 0, [], []
+        for q in range(k32):
+            f = args.warmup + 1 + q
+            b32.set_indenter(poses[f])
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b32.step(status, iters)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms32.append(e0.elapsed_time(e1))
+            sn = status.cpu().numpy()
+            conv32 += int(np.all(sn.reshape(-1, w.pads_per_env) == 0, axis=1).sum())
+            st32.append(sn)
+            it32.append(iters.cpu().numpy())
+        b32.close()
+        del b32
+        torch.cuda.empty_cache()
+        st32, it32 = np.concatenate(st32), np.concatenate(it32)
+        # the chosen form over the same frames
+        ms_c = solve_ms[:k32]
+        conv_c = sum(int(np.all(stt.cpu().numpy().reshape(-1, w.pads_per_env) == 0, axis=1).sum())
+                     for stt, _, _, _ in stats_all[:k32])
+        fp32 = {"form": "plain FP32 (precision_mode 1): single-float displacements; float32 pair distance, "
+                        "barrier, step bounds and sums",
+                "frames": f"{args.warmup + 1}..{args.warmup + k32}, from the chosen form's state after the warm-up",
+                "tol_rel_grad": 1e-6, "max_iter": args.fp32_max_iter,
+                "value": conv32 / (sum(ms32) / 1e3), "unit": UNIT, "ms_per_frame": float(np.mean(ms32)),
+                "converged_fraction": conv32 / (k32 * args.envs),
+                "status_counts": {str(int(a)): int(c) for a, c in zip(*np.unique(st32, return_counts=True))},
+                "iters_per_pad_frame": {"p50": float(np.percentile(it32, 50)), "p99": float(np.percentile(it32, 99))},
+                "chosen_form_same_frames": {"value": conv_c / (sum(ms_c) / 1e3), "ms_per_frame": float(np.mean(ms_c)),
+                                            "converged_fraction": conv_c / (k32 * args.envs)}}
     if rank == 0:
         v_state = b.total_verts * 168 / 1e9
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -405,14 +593,26 @@ def run_ours(args, rank, world):
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                             "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                             "kernel": "tac::solve_kernel", "bytes_per_launch": bytes_per_launch,
-                            "launch_ms": launch_ms},
+                            "launch_ms": launch_ms,
+                            "iteration_model": {"bytes_per_launch": bytes_iter_model / args.steps,
+                                                "achieved": achieved_iter_model,
+                                                "frac": achieved_iter_model / peak,
+                                                "model": "112 B/tet + 150 B/vertex per PNCG iteration"},
+                            "phases": phase_gbs},
                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 3 * args.steps,
                "clocks": clk.summary(),
                "converged_fraction": conv_job / (args.steps * args.envs * world),
+               "float32_floor_stops": floor_stops / max(1, pad_frames),
+               "pad_frame_ms": {"p50": float(np.percentile(pad_ms, 50)), "p99": float(np.percentile(pad_ms, 99)),
+                                "max": float(pad_ms.max())},
                "iters_per_pad_frame": {"p50": float(np.percentile(its, 50)), "p99": float(np.percentile(its, 99)),
                                        "max": int(its.max())},
                "frame_ms": {"p50": float(np.percentile(solve_ms, 50)), "p99": float(np.percentile(solve_ms, 99))},
                "setup_s": t_create, "phase_share": phase_share, "queue": queue}
+        if fp32 is not None:
+            out["plain_fp32"] = fp32
+        if per_frame:
+            out["per_frame"] = per_frame
         print(json.dumps(out), flush=True)
     b.close()
 
@@ -667,6 +867,62 @@ def run_calibrate(args):
     print(json.dumps(out), flush=True)
 
 
+# the hidden materials' prior of the calibration workload: the search box
+C4_RANGES = {"E": (1e5, 5e5), "nu": (0.40, 0.49), "mu_f": (0.3, 0.9), "rho": (1e3, 5e3)}
+
+
+def run_calibrate_oracle(args, generations=30, iterations=20):
+    """Calibration against targets the FP64 oracle solved (written by
+    tests/golden/make_calibration_targets.py): the calibration workload's
+    first environments (5k pad, 16-frame press-and-slide, friction), each
+    at its own hidden (E, nu, mu_f). Per environment: CMA-ES (population 12,
+    the populations of all environments solved in the same batches) and
+    Adam on adjoint gradients (lags differentiated), both started at the
+    nominal material, over the hidden materials' prior box. Prints one
+    JSON line: per-environment relative errors, loss curves and times."""
+    import torch
+    from paper_2603_28475_b300 import calibrate as C
+    from paper_2603_28475_b300 import scenes as S
+    torch.cuda.set_device(0)
+    g = np.load(os.path.join(ROOT, "tests", "golden", "calibration_targets.npz"))
+    n, F = len(g["envs"]), int(g["frames"])
+    w_all, hidden = S.config_calibration(n_envs=256, frames=F, seed=0)
+    w = S.Workload("calibration_head", w_all.pads[:n], w_all.materials[:n], w_all.indenters[:n], 1,
+                   w_all.poses[:, :n])
+    names = ("E", "nu", "mu_f")
+    truth = np.array(g["hidden"])
+    base = w.materials[0]
+    x0 = np.tile(C.to_unit([base.E, base.nu, base.mu_f], names, C4_RANGES), (n, 1))
+    targets = torch.tensor(np.transpose(g["markers"], (1, 0, 2, 3)).reshape(F, -1, 2), dtype=torch.float32,
+                           device="cuda")
+    kappa = list(np.tile(g["kappa"], 12))
+    cal = C.Calibration(w, 12, base, names=names, kappa=kappa)
+    best, h = C.calibrate_cmaes_per_scene(cal, targets, generations=generations, sigma0=0.3, x0=x0,
+                                          seed=args.seed, ranges=C4_RANGES)
+    cal.close()
+    runs = {"cmaes_per_env": {
+        "generations": generations, "popsize": 12, "theta": best.tolist(),
+        "rel_error": (np.abs(best / truth - 1.0)).tolist(),
+        "best_loss_mean_over_envs": h.best_loss[::max(1, generations // 15)] + [h.best_loss[-1]],
+        "pad_frames_solved": h.frames_solved[-1], "seconds": h.seconds[-1]}}
+    th, ha = C.calibrate_adjoint(w, base, targets, iterations=iterations, lr=0.05, x0=x0, kappa=list(g["kappa"]),
+                                 relag=True, per_scene=True, ranges=C4_RANGES)
+    runs["adjoint_adam_per_env"] = {
+        "iterations": iterations, "lag": "differentiated", "theta": np.asarray(th).tolist(),
+        "rel_error": (np.abs(np.asarray(th) / truth - 1.0)).tolist(),
+        "loss": ha.mean_loss[::2] + [ha.mean_loss[-1]], "pad_frames_solved": ha.frames_solved[-1],
+        "seconds": ha.seconds[-1]}
+    out = {"metric": "calibration against FP64-oracle targets: relative parameter errors, loss and time",
+           "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+           "dtype": "f32 (double-float displacements; f64 pair distance, barrier, CCD and reductions)",
+           "config": {"workload": f"calibration workload, first {n} envs x {F} frames (5k pads, friction)",
+                      "targets": "FP64 oracle at each env's hidden (E, nu, mu_f)",
+                      "hidden": truth.tolist(), "start": "nominal material (0.3 MPa, 0.45, 0.5)",
+                      "search_box": {k: C4_RANGES[k] for k in names}},
+           "runs": runs}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -686,6 +942,10 @@ def main():
     if args.calibrate:
         if rank == 0:
             run_calibrate(args)
+        return
+    if args.calibrate_oracle:
+        if rank == 0:
+            run_calibrate_oracle(args)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

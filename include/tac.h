@@ -57,7 +57,7 @@ extern "C" {
 
 /* ---- per-pad solve status (tac_step) -------------------------------------- */
 #define TAC_PAD_CONVERGED 0        /* max |g_i| <= tol * g_ref at the end pose    */
-#define TAC_PAD_MAXITER 1          /* iteration or substep cap reached           */
+#define TAC_PAD_MAXITER 1          /* max_iter PNCG iterations or 4000 indenter substeps in the frame */
 #define TAC_PAD_NONFINITE 2        /* non-finite value met (state left as is)    */
 #define TAC_PAD_LINESEARCH 3       /* 20 Armijo halvings without acceptance      */
 #define TAC_PAD_PAIR_OVERFLOW 4    /* more contact candidates than pair_capacity */
@@ -104,11 +104,27 @@ typedef struct {
  *                 marker; 1 = the 4 rest top-face nodes nearest to the marker
  *                 (2-D distance, ties to the smaller id) with weights
  *                 proportional to 1/d (Sec. 3.2's kNN mapping). Fixed at
- *                 creation: tac_set_params rejects a change */
+ *                 creation: tac_set_params rejects a change
+ *  precision_mode 0 = the precision split of the solve: float32 elasticity
+ *                 and CG vectors, double-float displacements, and float64
+ *                 pair distance, barrier, step bounds and the sums that feed
+ *                 the line search; 1 = the plain FP32 form of the same
+ *                 method: single-float displacements and every distance,
+ *                 barrier, bound and sum in float32 (the comparator the
+ *                 split is measured against)
+ *  floor_ulps     the float32 resolution floor of the stopping target in
+ *                 ulps of the largest per-corner force F: the target is
+ *                 max(tol_rel_grad * g_ref, floor_ulps * 2^-24 * F); <= 0
+ *                 selects 256 (a float32 gradient is not resolved below a
+ *                 few hundred ulps of the forces summed into it; a smaller
+ *                 floor solves tighter where the line search can still
+ *                 resolve the energy) */
 typedef struct {
     float E, nu, rho, h, dhat, kappa, mu_f, eps_v;
     float tol_rel_grad, tol_advance;
     int max_iter, precond_mode, step_mode, marker_mode;
+    int precision_mode;
+    float floor_ulps;
 } tac_params;
 
 /* Batch options. pair_capacity: candidate pairs stored per pad (0 = 16384).
@@ -338,8 +354,9 @@ int tac_stats(tac_handle h, long long* stats_dev, void* stream);
 /* Convergence record of the last tac_step per pad (device [n_pads*4]
  * double): final max |g_i|, the stopping target, g_ref of the frame, and the
  * largest per-corner force component F. The target is
- * max(tol * g_ref, 256 * 2^-24 * F): a float32 gradient is not resolved
- * below a few hundred ulps of the forces summed into it. */
+ * max(tol * g_ref, floor_ulps * 2^-24 * F) (tac_params.floor_ulps, 256 by
+ * default): a float32 gradient is not resolved below a few hundred ulps of
+ * the forces summed into it. */
 int tac_pad_norms(tac_handle h, double* norms_dev, void* stream);
 
 /* Host only (no device work, no handle): the marker map that tac_create_batch

@@ -10,6 +10,10 @@
   * b: the C^2 log barrier b(d) = -(d - dhat)^2 ln(d / dhat) for d < dhat,
         0 otherwise, over point-triangle and edge-edge pairs between the gel
         surface and the rigid indenter; d is the unsigned Euclidean distance;
+        an edge-edge term is multiplied by IPC's parallel-edge mollifier
+        m(c), c = |e_gel x e_ind|^2 (the distance between two edges has a
+        kink where they turn parallel, and the barrier pushes pressed edges
+        towards exactly that configuration);
   * D: lagged friction of Eq. (friction_energy) with the mollifier of
         Eq. (friction_mollifier).
 
@@ -333,9 +337,68 @@ def barrier_d2(d, dhat):
         return np.where(d < dhat, -2.0 * np.log(d / dhat) - 4.0 * (d - dhat) / d + (d - dhat) ** 2 / d ** 2, 0.0)
 
 
+# ---------------------------------------------------------------------------
+# parallel-edge mollifier of the edge-edge terms (IPC, Li et al. 2020)
+
+EE_MOLLIFIER_REL = 1e-3
+
+
+def ee_mollifier_eps(ty, gid, iid, pad, ind):
+    """Mollifier threshold of each pair: eps_x = 1e-3 |gel edge|^2
+    |indenter edge|^2 with rest lengths for an edge-edge pair (type 2), 0
+    (no mollifier) for the point-triangle types."""
+    eps = np.zeros(len(ty))
+    m = ty == 2
+    if np.any(m):
+        a = pad.rest[gid[m, 1]] - pad.rest[gid[m, 0]]
+        b = ind.verts[iid[m, 3]] - ind.verts[iid[m, 2]]
+        eps[m] = EE_MOLLIFIER_REL * np.einsum("nc,nc->n", a, a) * np.einsum("nc,nc->n", b, b)
+    return eps
+
+
+def edge_cross_sq(P):
+    """c = |(P1 - P0) x (Q1 - Q0)|^2 of slot positions [P0, P1, Q0, Q1]
+    (generic)."""
+    w = T.cross(P[:, 1] - P[:, 0], P[:, 3] - P[:, 2])
+    return T.dot(w, w)
+
+
+def edge_cross_sq_grad(P):
+    """c and dc/d(slot position) [n, 4, 3] (values): with u = P1 - P0,
+    v = Q1 - Q0, w = u x v, dc = 2 (v x w).du + 2 (w x u).dv."""
+    u, v = P[:, 1] - P[:, 0], P[:, 3] - P[:, 2]
+    w = np.cross(u, v)
+    gu, gv = 2.0 * np.cross(v, w), 2.0 * np.cross(w, u)
+    return np.einsum("nc,nc->n", w, w), np.stack([-gu, gu, -gv, gv], axis=1)
+
+
+def ee_mollifier(c, eps):
+    """m(c) = (2 - c/eps) c/eps for c < eps, else 1 (generic in c); a pair
+    with eps = 0 gets 1. C^1 at c = eps, m(0) = 0."""
+    on = T.val(c) < eps
+    inv = np.where(eps > 0, 1.0 / np.where(eps > 0, eps, 1.0), 0.0)
+    q = c * inv
+    return T.where(on, (2.0 - q) * q, 1.0)
+
+
+def ee_mollifier_d1(c, eps):
+    """m'(c) = 2/eps (1 - c/eps) for c < eps, else 0 (values)."""
+    inv = np.where(eps > 0, 1.0 / np.where(eps > 0, eps, 1.0), 0.0)
+    return np.where(c < eps, 2.0 * inv * (1.0 - c * inv), 0.0)
+
+
+def pair_barrier(ty, P, eps, dhat):
+    """Per pair m(c) b(d) from slot positions P [n, 4, 3] (generic: with P
+    a Jet along a line the result carries the line derivatives)."""
+    d, _ = slot_distances(ty, P)
+    return ee_mollifier(edge_cross_sq(P), eps) * barrier(d, dhat)
+
+
 def contact(pairs, x, y, pad, ind):
-    """kappa * sum b(d_k), its gradient on gel vertices and Gauss-Newton
-    diagonal blocks kappa b''(d) w_s^2 r^ r^T. Returns (E, g, blk, dmin)."""
+    """kappa * sum m(c_k) b(d_k), its gradient on gel vertices and
+    Gauss-Newton diagonal blocks kappa m(c) b''(d) w_s^2 r^ r^T (the
+    mollifier's own derivatives left out of the blocks). Returns (E, g,
+    blk, dmin)."""
     nV = x.shape[0]
     g = np.zeros((nV, 3))
     blk = np.zeros((nV, 3, 3))
@@ -348,12 +411,17 @@ def contact(pairs, x, y, pad, ind):
     r = np.einsum("ns,nsk->nk", w, P)
     rhat = r / d[:, None]
     dh = pad.dhat
-    E = pad.kappa * float(barrier(d, dh).sum())
-    b1 = pad.kappa * barrier_d1(d, dh)
-    b2 = pad.kappa * barrier_d2(d, dh)
+    eps = ee_mollifier_eps(ty, gid, iid, pad, ind)
+    c, gc = edge_cross_sq_grad(P)
+    mv, m1 = ee_mollifier(c, eps), ee_mollifier_d1(c, eps)
+    bv = barrier(d, dh)
+    E = pad.kappa * float(np.sum(mv * bv))
+    b1 = pad.kappa * mv * barrier_d1(d, dh)
+    b2 = pad.kappa * mv * barrier_d2(d, dh)
+    cb = pad.kappa * m1 * bv
     for s in range(4):
         m = gid[:, s] >= 0
-        np.add.at(g, gid[m, s], (b1[m] * w[m, s])[:, None] * rhat[m])
+        np.add.at(g, gid[m, s], (b1[m] * w[m, s])[:, None] * rhat[m] + cb[m][:, None] * gc[m, s])
         np.add.at(blk, gid[m, s], (b2[m] * w[m, s] ** 2)[:, None, None] * np.einsum("ni,nj->nij", rhat[m], rhat[m]))
     return E, g, blk, float(d.min())
 
@@ -361,8 +429,10 @@ def contact(pairs, x, y, pad, ind):
 def contact_line(pairs, x, p, y, pad, ind):
     if len(pairs) == 0:
         return T.Jet(0.0)
-    d, _, _ = distances(pairs, T.line(x, p), y, pad, ind)
-    return barrier(d, pad.dhat).sum() * pad.kappa
+    ty, gid, iid = pair_geometry(pairs, x, y, pad, ind)
+    P = _slot_positions(gid, iid, T.line(x, p), y)
+    eps = ee_mollifier_eps(ty, gid, iid, pad, ind)
+    return pair_barrier(ty, P, eps, pad.dhat).sum() * pad.kappa
 
 
 # ---------------------------------------------------------------------------
@@ -382,7 +452,8 @@ def mollifier_d1_over_s(s, eps):
 
 def friction_lag(pairs, x_t, y_t, pad, ind):
     """Lag data from the state at the start of the frame: every candidate
-    pair with d < dhat contributes lambda_n = -kappa b'(d), the normal r^ and
+    pair with d < dhat contributes lambda_n = -kappa m(c) b'(d) (the normal
+    force of its mollified barrier), the normal r^ and
     the closest-point weights (gel slots w >= 0, indenter slots w <= 0)."""
     empty = dict(gid=np.zeros((0, 4), np.int64), iid=np.zeros((0, 4), np.int64), w=np.zeros((0, 4)),
                  n=np.zeros((0, 3)), lam=np.zeros(0))
@@ -394,8 +465,9 @@ def friction_lag(pairs, x_t, y_t, pad, ind):
         return empty
     P = _slot_positions(gid[act], iid[act], x_t, y_t)
     r = np.einsum("ns,nsk->nk", w[act], P)
+    mv = ee_mollifier(edge_cross_sq(P), ee_mollifier_eps(ty[act], gid[act], iid[act], pad, ind))
     return dict(gid=gid[act], iid=iid[act], w=w[act], n=r / d[act][:, None],
-                lam=-pad.kappa * barrier_d1(d[act], pad.dhat))
+                lam=-pad.kappa * mv * barrier_d1(d[act], pad.dhat))
 
 
 def _friction_disp(lag, x, x_t, y, y_t):
@@ -528,10 +600,12 @@ def energy_only(fr, x, s, pairs):
         return INF
     Ee = pad.h * pad.h * float(np.sum(pad.vol * psi))
     if len(pairs):
-        d, _, _ = distances(pairs, x, y, pad, fr.ind)
+        d, _, (ty, gid, iid) = distances(pairs, x, y, pad, fr.ind)
         if np.any(d <= 0):
             return INF
-        Ec = pad.kappa * float(barrier(d, pad.dhat).sum())
+        P = _slot_positions(gid, iid, x, y)
+        mv = ee_mollifier(edge_cross_sq(P), ee_mollifier_eps(ty, gid, iid, pad, fr.ind))
+        Ec = pad.kappa * float(np.sum(mv * barrier(d, pad.dhat)))
     else:
         Ec = 0.0
     Ef, _, _ = friction(fr.lag, x, fr.x_t, y, fr.y_t, pad)

@@ -53,9 +53,10 @@ def _pair_hessians(fr, x, s, pairs):
     dofs = [(sl, c) for sl in range(4) for c in range(3)]
     Q = {}
 
+    eps = En.ee_mollifier_eps(ty, gid, iid, pad, fr.ind)
+
     def q(dirs):
-        d, _ = En.slot_distances(ty, T.Jet(P, dirs))
-        return pad.kappa * En.barrier(d, pad.dhat).dd
+        return pad.kappa * En.pair_barrier(ty, T.Jet(P, dirs), eps, pad.dhat).dd
 
     diag = []
     for k, (sl, c) in enumerate(dofs):

@@ -17,23 +17,32 @@ with the step rule of Eq. (step_size). Readings where the paper is silent:
     alpha_bar), no CCD bound and no energy test; a trial state outside E's
     domain (an inverted tet, a closed gap) is still halved;
   * direction restart (beta = 0) when |y^T p| is negligible or the new p
-    is not a descent direction;
+    is not a descent direction; a line search that fails along a conjugate
+    direction is retried once along -P g before it counts as failed;
   * stopping: max_i |g_i| (free DOFs) <= tol * g_ref, g_ref = max(h^2 E
     l-bar dhat, max_i |g_i| at the frame's first evaluation after the first
     indenter substep);
   * indenter motion: the indenter vertices move on the straight path
-    y(s) = (1 - s) y^t + s y^{t+1}; s advances in substeps of at most
-    eta * min_k d_k / max_j |y_j^{t+1} - y_j^t| (the gel held fixed), each
-    followed by PNCG to tol_advance (1e-2) relative, the last (s = 1) to tol;
+    y(s) = (1 - s) y^t + s y^{t+1}, and the gel moves with them: a substep
+    advances s by ds and the gel by ds w, w the gel's predicted motion per
+    unit s: the inertial prediction xhat - x^t of Eq. varopt for the first
+    substep, then the gel's mean motion so far, (x - x^t) / s (zero on
+    Dirichlet vertices). ds is at most
+    eta * d_k / max_{i in gel(k), j in ind(k)} |w_i - dy_j| for every
+    candidate k (dy = y^{t+1} - y^t): along straight motions of both sides
+    the points of two primitives approach at most that fast, so no gap
+    closes by more than eta of itself. When holding the gel (w = 0 in the
+    same bound) allows a longer substep, the substep holds it. ds is halved
+    while the advanced state leaves E's domain (an inverted tet). Each
+    substep is followed by PNCG to tol_advance (1e-2) relative, the last
+    (s = 1) to tol;
   * candidate set: rebuilt whenever the accumulated motion bound since the
     last build would exceed the margin m (= dhat), so pairs outside the set
-    stay farther than dhat;
+    stay farther than dhat; an advance moves any gel-indenter point pair
+    by at most ds B, B = max_j |dy_j - dy_0| + max_i |w_i - dy_0| (gel
+    moving) or max_j |dy_j| (gel held);
   * friction lag (lambda_n, normal, closest-point weights) from x^t with the
-    indenter at y^t, once per frame;
-  * initial guess: x^t + a0 (xhat - x^t) with a0 = min(1, alpha_ccd,
-    m / max_i |xhat_i - x^t_i|) against the candidates at (x^t, y^t),
-    halved while a tet would invert (the inertial prediction of Eq. varopt,
-    made collision-free).
+    indenter at y^t, once per frame.
 """
 from __future__ import annotations
 
@@ -56,7 +65,7 @@ class Params:
     eta: float = 0.9
     armijo_c: float = 1e-4
     max_halvings: int = 20
-    max_substeps: int = 1000
+    max_substeps: int = 4000
     margin_factor: float = 1.0        # m = margin_factor * dhat
     precond: str = "block"
     step: str = "bounded"             # "literal": alpha = min(alpha_upper, alpha_bar), no CCD, no Armijo
@@ -122,21 +131,30 @@ def dk_beta(g_new, yv, p, P_new):
     return float(np.sum(g_new * Py)) / yp - (float(np.sum(yv * Py)) / yp) * (float(np.sum(p * g_new)) / yp)
 
 
-def predictor(fr, x_t, xhat, pairs, eta, margin, max_halvings=20):
-    """Collision-free, inversion-free start of the frame on the segment from
-    x^t to xhat (see the module docstring)."""
-    p0 = xhat - x_t
-    p0[~fr.pad.free] = 0.0
-    pn = vnorm_max(p0)
-    if pn == 0.0:
-        return x_t.copy()
-    a0 = min(1.0, ccd_bound(fr, x_t, p0, 0.0, pairs, eta), margin / pn)
-    for _ in range(max_halvings + 1):
-        F = En.deformation_gradient(x_t + a0 * p0, fr.pad)
-        if np.all(np.linalg.det(F) > 0):
-            return x_t + a0 * p0
-        a0 *= 0.5
-    return x_t.copy()
+def relative_motion(fr, pairs, w, dy):
+    """Per candidate, max over its gel vertices i and indenter vertices j of
+    |w_i - dy_j|: the fastest approach of any point pair of the two
+    primitives when the gel moves by w and the indenter by dy."""
+    ty, gid, iid = En.pair_geometry(pairs, fr.x_t, fr.y_t, fr.pad, fr.ind)
+    out = np.zeros(len(ty))
+    for a in range(4):
+        for b in range(4):
+            m = (gid[:, a] >= 0) & (iid[:, b] >= 0)
+            if np.any(m):
+                out[m] = np.maximum(out[m], np.linalg.norm(w[gid[m, a]] - dy[iid[m, b]], axis=1))
+    return out
+
+
+def advance_bound(fr, x, s, pairs, w, dy, eta):
+    """eta * min_k d_k / (relative motion of k): the largest advance of s
+    (gel along w, indenter along dy) that keeps every candidate's gap above
+    (1 - eta) of itself."""
+    if len(pairs) == 0:
+        return np.inf
+    d, _, _ = En.distances(pairs, x, fr.y(s), fr.pad, fr.ind)
+    rel = relative_motion(fr, pairs, w, dy)
+    ok = rel > 0
+    return float(np.min(eta * d[ok] / rel[ok])) if np.any(ok) else np.inf
 
 
 def min_distance(fr, x, s, pairs):
@@ -166,21 +184,28 @@ def remainder(fr, x, p, alpha, s, pairs):
     psi0 = En.neo_hookean_density(F0, pad.mu, pad.lam)
     psi1 = En.neo_hookean_density(F1, pad.mu, pad.lam)
     R += pad.h * pad.h * float(np.sum(pad.vol * (psi1 - psi0 - alpha * np.einsum("tij,tij->t", P0, dF))))
-    # barrier
+    # barrier (edge-edge terms mollified: m(c) b(d))
     if len(pairs):
         d0, w, (ty, gid, iid) = En.distances(pairs, x, y, pad, fr.ind)
         d1, _, _ = En.distances(pairs, xa, y, pad, fr.ind)
         if np.any(d1 <= 0):
             return np.inf
         P = En._slot_positions(gid, iid, x, y)
+        P1 = En._slot_positions(gid, iid, xa, y)
+        eps = En.ee_mollifier_eps(ty, gid, iid, pad, fr.ind)
+        c0, gc = En.edge_cross_sq_grad(P)
+        m0, m0d = En.ee_mollifier(c0, eps), En.ee_mollifier_d1(c0, eps)
+        m1 = En.ee_mollifier(En.edge_cross_sq(P1), eps)
         r = np.einsum("ns,nsk->nk", w, P)
         rhat = r / d0[:, None]
         pslots = np.zeros(gid.shape + (3,))
         gm = gid >= 0
         pslots[gm] = p[gid[gm]]
         ddot = np.einsum("ns,nsk,nk->n", w * gm, pslots, rhat)       # grad d . p
-        R += pad.kappa * float(np.sum(En.barrier(d1, pad.dhat) - En.barrier(d0, pad.dhat)
-                                      - alpha * En.barrier_d1(d0, pad.dhat) * ddot))
+        cdot = np.einsum("nsk,nsk->n", gc, pslots)                    # grad c . p
+        b0 = En.barrier(d0, pad.dhat)
+        R += pad.kappa * float(np.sum(m1 * En.barrier(d1, pad.dhat) - m0 * b0
+                                      - alpha * (m0 * En.barrier_d1(d0, pad.dhat) * ddot + m0d * cdot * b0)))
     # friction
     lag = fr.lag
     if lag["lam"].size and pad.mu_f > 0:
@@ -234,31 +259,46 @@ def solve_frame(pad, ind, state, pose_next, prm=Params(), trace=None, lag=None):
     if lag is None:
         lag = En.friction_lag(cand, x_t, y_t, pad, ind)
     fr = En.Frame(pad, ind, x_t, xhat, y_t, y_n, lag)
-    Dy = float(np.sqrt(((y_n - y_t) ** 2).sum(axis=1)).max())
+    dy = y_n - y_t
     free = pad.free
-    x = predictor(fr, x_t, xhat, cand, prm.eta, margin)
-    if not np.array_equal(x, x_t):
-        cand = BP.candidates(x, y_t, pad, ind, r_inf)
-        info.rebuilds += 1
+    w_pred = xhat - x_t                 # predicted gel motion over the frame
+    w_pred[~free] = 0.0
+    held = np.zeros_like(w_pred)
+    B_pred = float(np.linalg.norm(dy - dy[0], axis=1).max() + np.linalg.norm(w_pred - dy[0], axis=1).max())
+    B_held = float(np.linalg.norm(dy, axis=1).max())
+    x = x_t.copy()
     s, M = 0.0, 0.0
     info.min_gap = min_distance(fr, x, s, cand)
     g_ref = None
+
+    def choose(cand, cap):
+        # the longer of the two advances (gel moving with the prediction or held)
+        dp = min(1.0 - s, advance_bound(fr, x, s, cand, w_pred, dy, prm.eta), cap(B_pred))
+        dh = min(1.0 - s, advance_bound(fr, x, s, cand, held, dy, prm.eta), cap(B_held))
+        return (dp, w_pred, B_pred) if dp >= dh else (dh, held, B_held)
+
     while True:
         if s < 1.0:
-            if Dy == 0.0:
-                ds = 1.0 - s
+            # advance the indenter and the gel together (module docstring)
+            ds, w, B = choose(cand, lambda b: np.inf)
+            if M + ds * B > margin:
+                cand = BP.candidates(x, fr.y(s), pad, ind, r_inf)
+                info.rebuilds += 1
+                M = 0.0
+                ds, w, B = choose(cand, lambda b: margin / b if b > 0 else np.inf)
+            for _ in range(prm.max_halvings + 1):
+                s1 = 1.0 if ds >= 1.0 - s else s + ds
+                if np.isfinite(En.energy_only(fr, x + ds * w, s1, cand)):
+                    break
+                ds *= 0.5
             else:
-                dmin = min_distance(fr, x, s, cand)
-                ds = min(1.0 - s, prm.eta * dmin / Dy)
-                if M + ds * Dy > margin:
-                    cand = BP.candidates(x, fr.y(s), pad, ind, r_inf)
-                    info.rebuilds += 1
-                    M = 0.0
-                    dmin = min_distance(fr, x, s, cand)
-                    ds = min(1.0 - s, prm.eta * dmin / Dy, margin / Dy)
-            s = 1.0 if ds >= 1.0 - s else s + ds
-            M += ds * Dy
+                info.status = NONFINITE
+                break
+            x = x + ds * w
+            s = s1
+            M += ds * B
             info.substeps += 1
+            info.min_gap = min(info.min_gap, min_distance(fr, x, s, cand))
         E, g, blk = En.total(fr, x, s, cand)
         if not np.isfinite(E):
             info.status = NONFINITE
@@ -269,6 +309,7 @@ def solve_frame(pad, ind, state, pose_next, prm=Params(), trace=None, lag=None):
             g_ref = max(pad.g_ref, float(np.abs(g[free]).max(initial=0.0)))
             info.g_ref = g_ref
         target = (prm.tol if s >= 1.0 else max(prm.tol, prm.tol_advance)) * g_ref
+        retried = False
         while np.abs(g[free]).max(initial=0.0) > target and info.iters < prm.max_iter:
             pn = vnorm_max(p)
             gTp = float(np.sum(g * p))
@@ -301,8 +342,15 @@ def solve_frame(pad, ind, state, pose_next, prm=Params(), trace=None, lag=None):
                 alpha *= 0.5
                 info.halvings += 1
             if not accepted:
+                # one retry along the preconditioned steepest descent -P g
+                # before the line search counts as failed
+                if not retried and not literal:
+                    retried = True
+                    p = -apply_P(P, g)
+                    continue
                 info.status = LINESEARCH
                 break
+            retried = False
             x = x + alpha * p
             M += alpha * pn
             E_new, g_new, blk_new = En.total(fr, x, s, cand)
@@ -331,6 +379,10 @@ def solve_frame(pad, ind, state, pose_next, prm=Params(), trace=None, lag=None):
         if info.substeps >= prm.max_substeps or info.iters >= prm.max_iter:
             info.status = MAXITER
             break
+        # the next substep moves the gel on with its mean motion so far
+        w_pred = (x - x_t) / s
+        w_pred[~free] = 0.0
+        B_pred = float(np.linalg.norm(dy - dy[0], axis=1).max() + np.linalg.norm(w_pred - dy[0], axis=1).max())
     info.grad_inf = float(np.abs(g[free]).max(initial=0.0)) if info.status != NONFINITE else np.inf
     new = State(x=x, v=(x - x_t) / h, pose=np.asarray(pose_next, np.float64).copy())
     return new, info

@@ -38,17 +38,20 @@ PARAMS = ("E", "nu", "rho", "mu_f")
 RANGES = {"E": (1e4, 2e5), "nu": (0.4, 0.497), "rho": (1e3, 5e3), "mu_f": (0.25, 2.5)}
 
 
-def to_theta(x, names=PARAMS):
-    """Physical parameters from normalised coordinates x in [0, 1]^n."""
+def to_theta(x, names=PARAMS, ranges=None):
+    """Physical parameters from normalised coordinates x in [0, 1]^n
+    (ranges: the search box, RANGES by default)."""
+    r = RANGES if ranges is None else ranges
     x = np.asarray(x, dtype=np.float64)
-    lo = np.array([RANGES[n][0] for n in names])
-    hi = np.array([RANGES[n][1] for n in names])
+    lo = np.array([r[n][0] for n in names])
+    hi = np.array([r[n][1] for n in names])
     return lo + x * (hi - lo)
 
 
-def to_unit(theta, names=PARAMS):
-    lo = np.array([RANGES[n][0] for n in names])
-    hi = np.array([RANGES[n][1] for n in names])
+def to_unit(theta, names=PARAMS, ranges=None):
+    r = RANGES if ranges is None else ranges
+    lo = np.array([r[n][0] for n in names])
+    hi = np.array([r[n][1] for n in names])
     return (np.asarray(theta, dtype=np.float64) - lo) / (hi - lo)
 
 
@@ -155,10 +158,13 @@ class Calibration:
         self.n_mk = self.batch.total_markers // (self.P * self.N)
 
     def _params(self, thetas):
+        """thetas [P, n]: one vector per candidate for all scenes; or
+        [P, N, n]: one per candidate and scene."""
+        thetas = np.asarray(thetas, dtype=np.float64)
         prm = []
         for c in range(self.P):
-            th = dict(zip(self.names, thetas[c]))
             for i in range(self.N):
+                th = dict(zip(self.names, thetas[c, i] if thetas.ndim == 3 else thetas[c]))
                 k = c * self.N + i
                 m = copy.copy(self.base)
                 for nme in PARAMS:
@@ -190,6 +196,18 @@ class Calibration:
         d = (m - targets[:, None]).double().reshape(self.F, self.P, self.N, self.n_mk * 2)
         L = (d * d).sum(dim=3).mean(dim=(0, 2))
         ok = (st.reshape(self.F, self.P, self.N) == 0).all(dim=2).all(dim=0)
+        L = torch.where(ok, L, torch.full_like(L, float("inf")))
+        return L.cpu().numpy()
+
+    def loss_per_scene(self, thetas, targets):
+        """Eq. loss_function per candidate and scene [P, N] (thetas [P, N, n]
+        or [P, n]) against targets [F, N * M, 2]: the mean over frames of the
+        squared L2 norm of the scene's field difference; +inf where a frame
+        of that scene did not converge."""
+        m, st = self.markers(thetas)
+        d = (m - targets[:, None]).double().reshape(self.F, self.P, self.N, self.n_mk * 2)
+        L = (d * d).sum(dim=3).mean(dim=0)
+        ok = (st.reshape(self.F, self.P, self.N) == 0).all(dim=0)
         L = torch.where(ok, L, torch.full_like(L, float("inf")))
         return L.cpu().numpy()
 
@@ -228,14 +246,41 @@ def calibrate_cmaes(cal, targets, generations=80, sigma0=0.3, x0=None, seed=0, c
     return to_theta(es.best_x, cal.names), h
 
 
+def calibrate_cmaes_per_scene(cal, targets, generations=40, sigma0=0.3, x0=None, seed=0, ranges=None):
+    """One CMA-ES per scene (each scene its own material), all scenes'
+    populations solved in the same batches: a generation is one batch of
+    popsize x N pads. Returns (best theta per scene [N, n], History of the
+    mean over scenes of the best losses)."""
+    import time
+    n = len(cal.names)
+    es = [CMAES(np.full(n, 0.5) if x0 is None else x0[i], sigma0, popsize=cal.P, seed=seed + i)
+          for i in range(cal.N)]
+    h = History([], [], [], [], [])
+    t0, frames = time.perf_counter(), 0
+    for g in range(generations):
+        X = np.stack([e.ask() for e in es], axis=1)                 # [P, N, n]
+        L = cal.loss_per_scene(to_theta(X.reshape(-1, n), cal.names, ranges).reshape(X.shape), targets)
+        for i, e in enumerate(es):
+            e.tell(L[:, i])
+        frames += cal.F * cal.P * cal.N
+        h.best_loss.append(float(np.mean([e.best_f for e in es])))
+        h.mean_loss.append(float("nan"))
+        h.theta.append([to_theta(e.m, cal.names, ranges).tolist() for e in es])
+        h.frames_solved.append(frames)
+        h.seconds.append(time.perf_counter() - t0)
+    return np.stack([to_theta(e.best_x, cal.names, ranges) for e in es]), h
+
+
 def calibrate_adjoint(scenes, base, targets, iterations=40, lr=0.05, x0=None, kappa=None, pair_capacity=8192,
-                      relag=True):
+                      relag=True, per_scene=False, ranges=None):
     """Adam on the normalised (E, nu, mu_f) with gradients of Eq.
     loss_function from the frames' implicit adjoints (rho stays at
     ``base.rho``; the adjoint gives no density gradient), each frame's
     friction lag differentiated unless ``relag`` is False. One iteration is
-    the forward sequence plus its reverse sweep on the N scenes. Returns
-    (theta, History)."""
+    the forward sequence plus its reverse sweep on the N scenes. With
+    ``per_scene`` each scene has its own (E, nu, mu_f) and the loss is the
+    sum of the scenes' losses (Adam acts per coordinate, so the scenes are
+    calibrated independently). Returns (theta [3] or [N, 3], History)."""
     import time
     from . import autograd as A
     names = ("E", "nu", "mu_f")
@@ -252,10 +297,12 @@ def calibrate_adjoint(scenes, base, targets, iterations=40, lr=0.05, x0=None, ka
     poses = torch.tensor(scenes.poses.astype(np.float64), device=dev)
     b.reset(poses[0].float())
     x0s, v0s = b.get_state()
-    lo = torch.tensor([RANGES[n][0] for n in names], dtype=torch.float64)
-    hi = torch.tensor([RANGES[n][1] for n in names], dtype=torch.float64)
-    x = torch.tensor(np.full(3, 0.5) if x0 is None else np.asarray(x0, np.float64), dtype=torch.float64,
-                     requires_grad=True)
+    r = RANGES if ranges is None else ranges
+    lo = torch.tensor([r[n][0] for n in names], dtype=torch.float64)
+    hi = torch.tensor([r[n][1] for n in names], dtype=torch.float64)
+    shape = (N, 3) if per_scene else (3,)
+    x = torch.tensor(np.full(shape, 0.5) if x0 is None else np.asarray(x0, np.float64).reshape(shape),
+                     dtype=torch.float64, requires_grad=True)
     opt = torch.optim.Adam([x], lr=lr)
     h = History([], [], [], [], [])
     t0, frames, best = time.perf_counter(), 0, np.inf
@@ -263,11 +310,11 @@ def calibrate_adjoint(scenes, base, targets, iterations=40, lr=0.05, x0=None, ka
     for it in range(iterations):
         opt.zero_grad()
         th = lo + x * (hi - lo)
-        E, nu, muf = th[0], th[1], th[2]
+        E, nu, muf = th[..., 0], th[..., 1], th[..., 2]
         lam = E * nu / ((1 + nu) * (1 - 2 * nu))
         mu = E / (2 * (1 + nu))
-        lame = torch.stack([lam, mu]).reshape(1, 2).expand(N, 2)
-        mu_f = muf.reshape(1).expand(N)
+        lame = torch.stack([lam, mu], dim=-1).reshape(-1, 2).expand(N, 2)
+        mu_f = muf.reshape(-1).expand(N)
         m = A.sequence_markers(b, x0s, v0s, lame, mu_f, poses, base_params=base_params, relag=relag)
         d = (m.double() - targets.double().to(m.device)).reshape(F, N, n_mk * 2)
         loss = (d * d).sum(dim=2).mean()

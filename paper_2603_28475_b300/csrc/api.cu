@@ -207,13 +207,18 @@ void fill_pad_params(tac_batch* b, int p) {
     P.max_iter = q.max_iter;
     P.precond = q.precond_mode;
     P.step = q.step_mode;
+    P.prec = q.precision_mode;
+    // a float32 gradient is resolved only down to a few hundred ulps of the
+    // largest per-corner force that enters it: floor_ulps * 2^-24 (256 by default)
+    P.floor = (q.floor_ulps > 0.0f ? q.floor_ulps : 256.0f) / 16777216.0f;
     b->hstep[p] = q.h;
 }
 
 bool params_ok(const tac_params& q) {
     return q.E > 0 && q.nu > -1 && q.nu < 0.5f && q.rho > 0 && q.h > 0 && q.dhat > 0 && q.mu_f >= 0 &&
            q.tol_rel_grad > 0 && q.tol_advance > 0 && q.max_iter >= 0 && (q.precond_mode == 0 || q.precond_mode == 1) &&
-           (q.step_mode == 0 || q.step_mode == 1) && (q.marker_mode == 0 || q.marker_mode == 1);
+           (q.step_mode == 0 || q.step_mode == 1) && (q.marker_mode == 0 || q.marker_mode == 1) &&
+           (q.precision_mode == 0 || q.precision_mode == 1) && q.floor_ulps >= 0.0f;
 }
 
 }  // namespace
@@ -534,7 +539,6 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     D.ilist = ilist; D.stats = stats; D.norms = norms; D.queue = queue;
     D.pad_nlag = pad_nlag; D.adj_x = adj_x; D.adj_r = adj_r;
     D.status = nullptr; D.iters = nullptr;
-    D.budget_ns = 20ull * 1000000000ull;
     int nsm = 0, occ = 0;
     CUDA_TRY(configure_kernels());
     CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device));

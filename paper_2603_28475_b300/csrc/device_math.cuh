@@ -107,15 +107,19 @@ __device__ __forceinline__ double barrier_b2(double d, double dh) {
 }
 
 // b, b' and b'' together from one logarithm and one reciprocal (float64 is a
-// narrow pipe; the three separate forms above cost three of each)
-struct Barrier3 {
-    double b, b1, b2;
+// narrow pipe; the three separate forms above cost three of each). T =
+// float is the plain-FP32 form's barrier.
+template <typename T>
+struct Barrier3T {
+    T b, b1, b2;
 };
-__device__ __forceinline__ Barrier3 barrier_all(double d, double dh) {
-    if (d >= dh) return Barrier3{0.0, 0.0, 0.0};
-    const double t = d - dh, L = log(d / dh), id = 1.0 / d;
-    const double ti = t * id;
-    return Barrier3{-t * t * L, -2.0 * t * L - t * ti, -2.0 * L - 4.0 * ti + ti * ti};
+using Barrier3 = Barrier3T<double>;
+template <typename T>
+__device__ __forceinline__ Barrier3T<T> barrier_all(T d, T dh) {
+    if (d >= dh) return Barrier3T<T>{T(0), T(0), T(0)};
+    const T t = d - dh, L = log(d / dh), id = T(1) / d;
+    const T ti = t * id;
+    return Barrier3T<T>{-t * t * L, T(-2) * t * L - t * ti, T(-2) * L - T(4) * ti + ti * ti};
 }
 
 // ---------------------------------------------------------------------------
@@ -275,19 +279,20 @@ __device__ __forceinline__ V3<T> feat_r(const Feature<T>& f, const V3<T> X[4]) {
 //   D = d^2, D' = 2 r.rdot, D'' = 2|rdot|^2 - 2 b^T (J^T J)^-1 b,
 //   J_k = sum_s e_ks X_s, b_k = (sum_s e_ks dl_s).r + J_k.rdot,
 //   d' = D'/(2d), d'' = (D'' - 2 d'^2) / (2d).
-__device__ __forceinline__ void feat_dir_derivs(const Feature<double>& f, const V3<double> X[4],
-                                                const V3<double> dl[4], double& d1, double& d2) {
-    V3<double> r = feat_r(f, X);
-    V3<double> rd = {0, 0, 0};
+template <typename T>
+__device__ __forceinline__ void feat_dir_derivs(const Feature<T>& f, const V3<T> X[4], const V3<T> dl[4], T& d1,
+                                                T& d2) {
+    V3<T> r = feat_r(f, X);
+    V3<T> rd = {T(0), T(0), T(0)};
 #pragma unroll
     for (int s = 0; s < 4; ++s) rd = rd + f.w[s] * dl[s];
-    double D2 = 2.0 * dot(rd, rd);
+    T D2 = T(2) * dot(rd, rd);
     if (f.nf > 0) {
-        V3<double> J[2], Gk[2];
-        double bk[2];
+        V3<T> J[2], Gk[2];
+        T bk[2];
         for (int k = 0; k < f.nf; ++k) {
-            J[k] = {0, 0, 0};
-            Gk[k] = {0, 0, 0};
+            J[k] = {T(0), T(0), T(0)};
+            Gk[k] = {T(0), T(0), T(0)};
             for (int s = 0; s < 4; ++s) {
                 J[k] = J[k] + f.e[k][s] * X[s];
                 Gk[k] = Gk[k] + f.e[k][s] * dl[s];
@@ -295,16 +300,16 @@ __device__ __forceinline__ void feat_dir_derivs(const Feature<double>& f, const 
             bk[k] = dot(Gk[k], r) + dot(J[k], rd);
         }
         if (f.nf == 1) {
-            double m = dot(J[0], J[0]);
-            if (m > 0) D2 -= 2.0 * bk[0] * bk[0] / m;
+            T m = dot(J[0], J[0]);
+            if (m > T(0)) D2 -= T(2) * bk[0] * bk[0] / m;
         } else {
-            double m00 = dot(J[0], J[0]), m01 = dot(J[0], J[1]), m11 = dot(J[1], J[1]);
-            double det = m00 * m11 - m01 * m01;
-            if (det > 0) D2 -= 2.0 * (m11 * bk[0] * bk[0] - 2.0 * m01 * bk[0] * bk[1] + m00 * bk[1] * bk[1]) / det;
+            T m00 = dot(J[0], J[0]), m01 = dot(J[0], J[1]), m11 = dot(J[1], J[1]);
+            T det = m00 * m11 - m01 * m01;
+            if (det > T(0)) D2 -= T(2) * (m11 * bk[0] * bk[0] - T(2) * m01 * bk[0] * bk[1] + m00 * bk[1] * bk[1]) / det;
         }
     }
     d1 = dot(r, rd) / f.d;
-    d2 = (D2 - 2.0 * d1 * d1) / (2.0 * f.d);
+    d2 = (D2 - T(2) * d1 * d1) / (T(2) * f.d);
 }
 
 // Action of the distance Hessian on slot directions dl (same sensitivity):
@@ -353,17 +358,99 @@ __device__ __forceinline__ void feat_hess_vec(const Feature<double>& f, const V3
 }
 
 // ---------------------------------------------------------------------------
+// Parallel-edge mollifier of the edge-edge terms (IPC, Li et al. 2020): an
+// edge-edge pair contributes m(c) b(d) with c = |u x v|^2, u = X1 - X0 and
+// v = X3 - X2 over its slots [P0, P1, Q0, Q1], and
+//   m(c) = (2 - c/eps) c/eps for c < eps, else 1,
+// eps = 1e-3 |rest u|^2 |rest v|^2. The edge-edge distance has a kink where
+// the edges turn parallel, the configuration a pressed edge settles into;
+// m makes the term C^1 there. eps = 0 (point-triangle pairs) gives m = 1.
+
+template <typename T>
+struct EdgeMollT {
+    T m, m1, m2;              // m(c), m'(c), m''(c)
+    V3<T> u, v, w;            // the two edges and w = u x v
+    bool on;                  // c < eps: the derivatives of m enter
+};
+using EdgeMoll = EdgeMollT<double>;
+
+template <typename T>
+__device__ __forceinline__ EdgeMollT<T> edge_moll(const V3<T> X[4], T eps) {
+    EdgeMollT<T> e;
+    e.u = X[1] - X[0];
+    e.v = X[3] - X[2];
+    e.w = cross(e.u, e.v);
+    const T c = dot(e.w, e.w);
+    e.on = eps > T(0) && c < eps;
+    if (e.on) {
+        const T ie = T(1) / eps, q = c * ie;
+        e.m = (T(2) - q) * q;
+        e.m1 = T(2) * ie * (T(1) - q);
+        e.m2 = T(-2) * ie * ie;
+    } else {
+        e.m = T(1);
+        e.m1 = T(0);
+        e.m2 = T(0);
+    }
+    return e;
+}
+
+// dc/dX of slot s: dc = 2 (v x w).du + 2 (w x u).dv
+template <typename T>
+__device__ __forceinline__ V3<T> edge_moll_grad(const EdgeMollT<T>& e, int s) {
+    V3<T> g = s < 2 ? cross(e.v, e.w) : cross(e.w, e.u);
+    const T sg = (s == 0 || s == 2) ? T(-2) : T(2);
+    return sg * g;
+}
+
+// c' and c'' along slot directions dl: with s = du x v + u x dv,
+// c' = 2 w.s and c'' = 2 |s|^2 + 4 w.(du x dv)
+template <typename T>
+__device__ __forceinline__ void edge_moll_dir(const EdgeMollT<T>& e, const V3<T> dl[4], T& c1, T& c2) {
+    const V3<T> du = dl[1] - dl[0], dv = dl[3] - dl[2];
+    const V3<T> s = cross(du, e.v) + cross(e.u, dv);
+    c1 = T(2) * dot(e.w, s);
+    c2 = T(2) * dot(s, s) + T(4) * dot(e.w, cross(du, dv));
+}
+
+// (Hess c) dl of slot s: the gradient of c' = 2 w.s for fixed dl,
+// d/du = 2 (v x s) + 2 (dv x w), d/dv = 2 (s x u) + 2 (w x du)
+__device__ __forceinline__ V3<double> edge_moll_hvec(const EdgeMoll& e, const V3<double> dl[4], int s) {
+    const V3<double> du = dl[1] - dl[0], dv = dl[3] - dl[2];
+    const V3<double> sv = cross(du, e.v) + cross(e.u, dv);
+    V3<double> h = s < 2 ? cross(e.v, sv) + cross(dv, e.w) : cross(sv, e.u) + cross(e.w, du);
+    const double sg = (s == 0 || s == 2) ? -2.0 : 2.0;
+    return sg * h;
+}
+
+// Second derivative of m(c) b(d) along slot directions, from d', d'' (the
+// feature's directional derivatives) and b, b', b'' at d:
+//   m (b'' d'^2 + b' d'') + m'' c'^2 b + m' c'' b + 2 m' c' b' d'
+template <typename T>
+__device__ __forceinline__ T moll_barrier_dir2(const EdgeMollT<T>& e, const V3<T> dl[4], T d1, T d2,
+                                               const Barrier3T<T>& bb) {
+    T q = bb.b2 * d1 * d1 + bb.b1 * d2;
+    if (!e.on) return q;
+    T c1, c2;
+    edge_moll_dir(e, dl, c1, c2);
+    return e.m * q + e.m2 * c1 * c1 * bb.b + e.m1 * c2 * bb.b + T(2) * e.m1 * c1 * bb.b1 * d1;
+}
+
+// ---------------------------------------------------------------------------
 // Friction mollifier f(s) of Eq. (friction_mollifier) and helpers.
 
-__device__ __forceinline__ double moll_f(double s, double eps) {
-    return s < eps ? -s * s * s / (3.0 * eps * eps) + s * s / eps + eps / 3.0 : s;
+template <typename T>
+__device__ __forceinline__ T moll_f(T s, T eps) {
+    return s < eps ? -s * s * s / (T(3) * eps * eps) + s * s / eps + eps / T(3) : s;
 }
-__device__ __forceinline__ double moll_f1_over_s(double s, double eps) {
-    return s < eps ? -s / (eps * eps) + 2.0 / eps : 1.0 / s;
+template <typename T>
+__device__ __forceinline__ T moll_f1_over_s(T s, T eps) {
+    return s < eps ? -s / (eps * eps) + T(2) / eps : T(1) / s;
 }
 // coefficient c(s) of the u u^T term of the tangent Hessian
-__device__ __forceinline__ double moll_c(double s, double eps) {
-    return s < eps ? s / (eps * eps) : (s > 0 ? 1.0 / s : 0.0);
+template <typename T>
+__device__ __forceinline__ T moll_c(T s, T eps) {
+    return s < eps ? s / (eps * eps) : (s > T(0) ? T(1) / s : T(0));
 }
 
 // ---------------------------------------------------------------------------

@@ -27,12 +27,9 @@ namespace tac {
 constexpr float kEta = 0.9f;          // safety factor of the step bounds
 constexpr double kArmijoC = 1e-4;
 constexpr int kMaxHalvings = 20;
-constexpr int kMaxSubsteps = 1000;
+constexpr int kMaxSubsteps = 4000;
 constexpr int kWarps = kThreads / 32;
 static_assert(kWarps == kCtaWarps, "the host balances colour classes for this many warps");
-// a float32 gradient is resolved only down to a few hundred ulps of the
-// largest per-corner force that enters it: 256 * 2^-24
-constexpr float kFloat32Floor = 256.0f / 16777216.0f;
 // A pair whose float32 distance exceeds kNearBand * dhat is outside the
 // barrier's support in float64 as well: at the workloads' coordinate
 // magnitudes (a few cm) the float32 distance is off by ~1e-8 m at most,
@@ -81,7 +78,6 @@ struct Shared {
     float box[12];
     int pad;
     int flag;
-    int expired;
     int fok;                    // D.fcache holds the float64 features of the current point and pair set
     float dm[kMaxDmTypes * 9];  // the current pad's Dm^-1 table (meshes with n_dm > 0)
 };
@@ -126,16 +122,6 @@ struct PhaseClock {
         }
     }
 };
-
-// true (in every thread) once the pad's solve has run longer than budget_ns;
-// thread 0 reads the clock and broadcasts so that the decision is uniform
-__device__ __forceinline__ bool over_budget(unsigned long long t0, unsigned long long budget_ns) {
-    if (threadIdx.x == 0) S.expired = (global_ns() - t0) > budget_ns ? 1 : 0;
-    __syncthreads();
-    bool e = S.expired != 0;
-    __syncthreads();
-    return e;
-}
 
 // The CTA's pad descriptors, identical for all its threads, go to shared
 // memory once per pad: the phase functions take them by reference, and a
@@ -187,6 +173,42 @@ __device__ __forceinline__ void block_sum(double (&v)[K]) {
     for (int k = 0; k < K; ++k) v[k] = S.rsum[k];
 }
 
+// K <= 4 float sums in float arithmetic (the plain-FP32 form's reductions),
+// order-fixed like block_sum
+template <int K>
+__device__ __forceinline__ void block_sum_f32(float (&v)[K]) {
+    static_assert(K <= 4, "block_sum_f32 holds at most 4 values");
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) S.rf[w][k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float t = 0.f;
+#pragma unroll
+        for (int i = 0; i < kWarps; ++i) t += S.rf[i][k];
+        v[k] = t;
+    }
+    __syncthreads();
+}
+
+// Block sum of K per-thread values of type R: float64 for the chosen form,
+// float for the plain-FP32 form
+template <typename R, int K>
+__device__ __forceinline__ void block_sum_r(R (&v)[K]) {
+    if constexpr (sizeof(R) == 8) {
+        block_sum<K>(v);
+    } else {
+        block_sum_f32<K>(v);
+    }
+}
+
 // Running sum of float terms without float64 arithmetic (FP64 is a narrow
 // pipe on this part): hi is the float sum, lo collects the exact rounding
 // error of each addition (Knuth's TwoSum), so hi + lo carries the sum to
@@ -204,6 +226,32 @@ __device__ __forceinline__ void fsum_add(FSum& a, float b) {
 }
 
 __device__ __forceinline__ double fsum_value(const FSum& a) { return (double)a.hi + (double)a.lo; }
+
+// plain float accumulation (the plain-FP32 form) or TwoSum pairs
+__device__ __forceinline__ void fsum_add_mode(FSum& a, float b, bool plain) {
+    if (plain)
+        a.hi = __fadd_rn(a.hi, b);
+    else
+        fsum_add(a, b);
+}
+
+// Block sums of K running sums: float64 of each thread's (hi + lo) for the
+// chosen form, float of each thread's hi for the plain-FP32 form
+template <int K>
+__device__ __forceinline__ void block_sum_fsum(const FSum (&a)[K], double (&out)[K], bool plain) {
+    if (plain) {
+        float f[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) f[k] = a[k].hi;
+        block_sum_f32<K>(f);
+#pragma unroll
+        for (int k = 0; k < K; ++k) out[k] = (double)f[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) out[k] = fsum_value(a[k]);
+        block_sum<K>(out);
+    }
+}
 
 __device__ __forceinline__ double block_min_d(double v) {
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -318,6 +366,23 @@ __device__ __forceinline__ void pair_slots(const Dev& D, const MeshDev& M, const
     }
 }
 
+// mollifier threshold of a pair: 1e-3 |rest gel edge|^2 |indenter edge|^2
+// for an edge-edge pair (slots [gel a, gel b, indenter a, indenter b]), 0
+// for the point-triangle types
+__device__ __forceinline__ double ee_eps(const Dev& D, const MeshDev& M, const EnvDev& E, int type, const int gsl[4],
+                                         const int isl[4]) {
+    if (type != 2) return 0.0;
+    double a2 = 0.0, b2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double a = (double)D.X[c * D.XVt + M.xv_off + gsl[1]] - (double)D.X[c * D.XVt + M.xv_off + gsl[0]];
+        const double b = (double)D.Y[3 * (E.y_off + isl[3]) + c] - (double)D.Y[3 * (E.y_off + isl[2]) + c];
+        a2 += a * a;
+        b2 += b * b;
+    }
+    return 1e-3 * a2 * b2;
+}
+
 // feature of a pair from slot positions; type 1 is re-expressed with the gel
 // triangle first and r pointing from the indenter to the gel
 template <typename T>
@@ -373,17 +438,22 @@ __device__ __forceinline__ void load_slots<float>(const Dev& D, const PadDev& P,
     }
 }
 
-// distance of a pair: float32 estimate, float64 when close (relative band)
-__device__ __forceinline__ double pair_distance(const Dev& D, const PadDev& P, const MeshDev& M, int type,
-                                                const int gsl[4], const int isl[4], float alpha, double s,
-                                                double near) {
+// distance of a pair: float32 estimate, float64 when close (relative band);
+// the plain-FP32 form takes the float32 distance
+template <typename R>
+__device__ __forceinline__ R pair_distance(const Dev& D, const PadDev& P, const MeshDev& M, int type,
+                                           const int gsl[4], const int isl[4], float alpha, double s, double near) {
     V3<float> Xf[4];
     load_slots<float>(D, P, M, gsl, isl, alpha, s, Xf);
     float df = pair_feature<float>(type, Xf).d;
-    if ((double)df > near) return (double)df * (1.0 - 1e-5);
-    V3<double> Xd[4];
-    load_slots<double>(D, P, M, gsl, isl, alpha, s, Xd);
-    return pair_feature<double>(type, Xd).d;
+    if constexpr (sizeof(R) == 4) {
+        return df;                          // the plain-FP32 form
+    } else {
+        if ((double)df > near) return (double)df * (1.0 - 1e-5);
+        V3<double> Xd[4];
+        load_slots<double>(D, P, M, gsl, isl, alpha, s, Xd);
+        return pair_feature<double>(type, Xd).d;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -488,6 +558,7 @@ template <int PASS, bool TAB>
 __device__ __noinline__ TetOut tet_pass_impl(const Dev& D, const PadDev& P, const MeshDev& M, float alpha, int gb) {
     TetOut out{0.0, 0, 0.f, 0.0};
     FSum acc{0.f, 0.f}, acc2{0.f, 0.f};
+    const bool plain = P.prec != 0 && PASS < 2;   // plain-FP32 form: float sums
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     WarpScratch& W = S.w[warp];
@@ -568,15 +639,15 @@ __device__ __noinline__ TetOut tet_pass_impl(const Dev& D, const PadDev& P, cons
                 for (int e = 0; e < 9; ++e) dF2 += dF[e] * dF[e];
                 AInv ai = a_invariants(f, dF);
                 if (PASS == 0) {
-                    fsum_add(acc, hV * (mu * dF2 + (mu - lam * f.lnJ) * ai.trA2 + lam * ai.c1 * ai.c1));
+                    fsum_add_mode(acc, hV * (mu * dF2 + (mu - lam * f.lnJ) * ai.trA2 + lam * ai.c1 * ai.c1), plain);
                 } else if (PASS == 3) {
                     // direction dF = D_lambda Dm^-1: dP/dlam : dF = ln J tr(F^-1 dF),
                     // dP/dmu : dF = (F - F^-T) : dF = tr dF + G : dF - tr(F^-1 dF)
                     float GdF = 0.f;
     #pragma unroll
                     for (int e = 0; e < 9; ++e) GdF += G[e] * dF[e];
-                    fsum_add(acc, hV * f.lnJ * ai.c1);
-                    fsum_add(acc2, hV * ((dF[0] + dF[4] + dF[8]) + GdF - ai.c1));
+                    fsum_add_mode(acc, hV * f.lnJ * ai.c1, plain);
+                    fsum_add_mode(acc2, hV * ((dF[0] + dF[4] + dF[8]) + GdF - ai.c1), plain);
                 } else if (PASS == 2) {
                     // dP = mu dF + (mu - lam ln J) F^-T dF^T F^-T + lam tr(F^-1 dF) F^-T
                     float C[9];
@@ -618,8 +689,8 @@ __device__ __noinline__ TetOut tet_pass_impl(const Dev& D, const PadDev& P, cons
                     float a2c = alpha * alpha * (ai.c2 - alpha * ai.c3);
                     float dl = log1p_minus(q) + a2c;          // ln det(I - aA) + a tr A
                     float dlnJ = log1pf(q);
-                    fsum_add(acc, hV * (0.5f * mu * alpha * alpha * dF2 + (lam * f.lnJ - mu) * dl +
-                                              0.5f * lam * dlnJ * dlnJ));
+                    fsum_add_mode(acc, hV * (0.5f * mu * alpha * alpha * dF2 + (lam * f.lnJ - mu) * dl +
+                                              0.5f * lam * dlnJ * dlnJ), plain);
                     // first Piola-Kirchhoff stress P = (mu Q + lam ln J cof) / J
                     float Pm[9];
     #pragma unroll
@@ -719,8 +790,10 @@ __device__ __noinline__ TetOut tet_pass_impl(const Dev& D, const PadDev& P, cons
         if (kScatter) __syncthreads();          // colour class complete: its writes are visible
     }
     // every thread must see the same totals: the caller branches on them
-    double v[3] = {fsum_value(acc), (double)out.bad, fsum_value(acc2)};
-    block_sum<3>(v);
+    FSum bad_sum{(float)out.bad, 0.f};
+    const FSum sums[3] = {acc, bad_sum, acc2};
+    double v[3];
+    block_sum_fsum<3>(sums, v, plain);
     out.acc = v[0];
     out.bad = v[1] > 0.0 ? 1 : 0;
     out.acc2 = v[2];
@@ -1036,7 +1109,7 @@ __device__ __noinline__ double pair_dmin(const Dev& D, const PadDev& P, const Me
         int gsl[4], isl[4];
         int4 q = pr[k];
         pair_slots(D, M, E, q, gsl, isl);
-        dm = fmin(dm, pair_distance(D, P, M, q.x, gsl, isl, 0.0f, s, kNearBand * P.dhat));
+        dm = fmin(dm, pair_distance<double>(D, P, M, q.x, gsl, isl, 0.0f, s, kNearBand * P.dhat));
     }
     return block_min_d(dm);
 }
@@ -1044,106 +1117,124 @@ __device__ __noinline__ double pair_dmin(const Dev& D, const PadDev& P, const Me
 // p^T H p of the barrier and friction terms and the per-pair step bound at
 // the current point; also stores each pair's barrier value b(d) there, which
 // the line-search trials of this point subtract from (see pair_trial)
-__device__ __noinline__ void pair_php(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np, int nl, double s,
-                         double& php, double& accd) {
-    double acc = 0.0, amin = 1e300;
+template <typename R>
+__device__ __noinline__ void pair_php(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np, int nl,
+                                      double s, double& php, double& accd) {
+    constexpr bool kMixed = sizeof(R) == 8;   // float64 features; else the plain-FP32 form
+    R acc = R(0), amin = R(3e38);
     const int4* pr = D.pairs + P.pair_off;
     double* bcur = D.bpair + P.pair_off;
     const Feature<double>* fc = D.fcache + P.pair_off;
     const bool cached = S.fok != 0;
-    const double dh = P.dhat, kap = P.kappa;
+    const R dh = P.dhat, kap = P.kappa;
     for (int k = threadIdx.x; k < np; k += kThreads) {
         int gsl[4], isl[4];
         int4 q = pr[k];
         pair_slots(D, M, E, q, gsl, isl);
         float pk = 0.f;
-        V3<double> dl[4];
+        V3<R> dl[4];
 #pragma unroll
         for (int sl = 0; sl < 4; ++sl) {
             if (gsl[sl] >= 0) {
                 int si = P.v_off + gsl[sl];
                 float a = D.p[si], b = D.p[D.Vt + si], c = D.p[2 * D.Vt + si];
                 pk = fmaxf(pk, sqrtf(a * a + b * b + c * c));
-                dl[sl] = {a, b, c};
+                dl[sl] = {R(a), R(b), R(c)};
             } else {
-                dl[sl] = {0.0, 0.0, 0.0};
+                dl[sl] = {R(0), R(0), R(0)};
             }
         }
         V3<float> Xf[4];
         load_slots<float>(D, P, M, gsl, isl, 0.0f, s, Xf);
         float df = pair_feature<float>(q.x, Xf).d;
-        double d, bv = 0.0;
-        if ((double)df > kNearBand * dh) {
-            d = (double)df * (1.0 - 1e-5);
+        R d;
+        double bv = 0.0;
+        if (kMixed && (double)df > kNearBand * (double)dh) {
+            d = R((double)df * (1.0 - 1e-5));
         } else {
-            V3<double> X[4];
-            load_slots<double>(D, P, M, gsl, isl, 0.0f, s, X);
-            Feature<double> f;
-            if (cached && fc[k].nf >= 0)
-                f = fc[k];              // computed by the accepted trial at this point
-            else
-                f = pair_feature<double>(q.x, X);
+            V3<R> X[4];
+            Feature<R> f;
+            if constexpr (kMixed) {
+                load_slots<double>(D, P, M, gsl, isl, 0.0f, s, X);
+                if (cached && fc[k].nf >= 0)
+                    f = fc[k];              // computed by the accepted trial at this point
+                else
+                    f = pair_feature<double>(q.x, X);
+            } else {
+#pragma unroll
+                for (int sl = 0; sl < 4; ++sl) X[sl] = Xf[sl];
+                f = pair_feature<float>(q.x, X);
+            }
             d = f.d;
             if (d < dh) {
-                double d1, d2;
+                R d1, d2;
                 feat_dir_derivs(f, X, dl, d1, d2);
-                const Barrier3 bb = barrier_all(d, dh);
-                acc += kap * (bb.b2 * d1 * d1 + bb.b1 * d2);
-                bv = bb.b;
+                const Barrier3T<R> bb = barrier_all(d, dh);
+                const EdgeMollT<R> em = edge_moll(X, R(ee_eps(D, M, E, q.x, gsl, isl)));
+                acc += kap * moll_barrier_dir2(em, dl, d1, d2, bb);
+                bv = (double)(em.m * bb.b);
             }
         }
         bcur[k] = bv;
-        if (pk > 0.f) amin = fmin(amin, (double)kEta * d / (double)pk);
+        if (pk > 0.f) amin = fmin(amin, R(kEta) * d / R(pk));
     }
     // friction (lagged pairs)
     const LagRec* lg = D.lag + P.pair_off;
     if (P.mu_f > 0.f)
         for (int l = threadIdx.x; l < nl; l += kThreads) {
             const LagRec& L = lg[l];
-            double Dl[3] = {-s * L.dY[0], -s * L.dY[1], -s * L.dY[2]}, pd[3] = {0, 0, 0};
+            R Dl[3] = {R(-s * L.dY[0]), R(-s * L.dY[1]), R(-s * L.dY[2])}, pd[3] = {R(0), R(0), R(0)};
             for (int gs = 0; gs < 3; ++gs)
                 if (L.g[gs] >= 0) {
                     int si = P.v_off + L.g[gs];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         int sc = c * D.Vt + si;
-                        Dl[c] += (double)L.w[gs] * (double)((D.uh[sc] - D.u0h[sc]) + (D.ul[sc] - D.u0l[sc]));
-                        pd[c] += (double)L.w[gs] * (double)D.p[sc];
+                        Dl[c] += R(L.w[gs]) * R((D.uh[sc] - D.u0h[sc]) + (D.ul[sc] - D.u0l[sc]));
+                        pd[c] += R(L.w[gs]) * R(D.p[sc]);
                     }
                 }
-            double nD = L.n[0] * Dl[0] + L.n[1] * Dl[1] + L.n[2] * Dl[2];
-            double np_ = L.n[0] * pd[0] + L.n[1] * pd[1] + L.n[2] * pd[2];
-            double tD[3], tp[3];
+            R nD = L.n[0] * Dl[0] + L.n[1] * Dl[1] + L.n[2] * Dl[2];
+            R np_ = L.n[0] * pd[0] + L.n[1] * pd[1] + L.n[2] * pd[2];
+            R tD[3], tp[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 tD[c] = Dl[c] - L.n[c] * nD;
                 tp[c] = pd[c] - L.n[c] * np_;
             }
-            double sv = sqrt(tD[0] * tD[0] + tD[1] * tD[1] + tD[2] * tD[2]);
-            double eps = P.eps_v, cf = (double)P.mu_f * L.lam;
-            double tp2 = tp[0] * tp[0] + tp[1] * tp[1] + tp[2] * tp[2];
-            double up = sv > 0 ? (tD[0] * tp[0] + tD[1] * tp[1] + tD[2] * tp[2]) / sv : 0.0;
+            R sv = sqrt(tD[0] * tD[0] + tD[1] * tD[1] + tD[2] * tD[2]);
+            R eps = P.eps_v, cf = R(P.mu_f) * R(L.lam);
+            R tp2 = tp[0] * tp[0] + tp[1] * tp[1] + tp[2] * tp[2];
+            R up = sv > R(0) ? (tD[0] * tp[0] + tD[1] * tp[1] + tD[2] * tp[2]) / sv : R(0);
             acc += cf * (moll_f1_over_s(sv, eps) * tp2 - moll_c(sv, eps) * up * up);
         }
-    double v[1] = {acc};
-    block_sum<1>(v);
-    php = v[0];
-    accd = block_min_d(amin);
+    R v[1] = {acc};
+    block_sum_r<R, 1>(v);
+    php = (double)v[0];
+    if constexpr (kMixed) {
+        accd = block_min_d(amin);
+    } else {
+        float m[1] = {-amin};
+        block_max_f<1>(m);
+        accd = (double)(-m[0]);
+    }
 }
 
 // trial pass over pairs at u + alpha p: slot contributions and remainders.
 // With alpha > 0 the remainder of pair k subtracts from its barrier value at
 // the current point, stored by pair_php of this point; alpha = 0 evaluates
 // the current point itself (remainder 0) and needs no stored value.
+template <typename R>
 __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np, int nl, double s,
                            float alpha, double& rem, int& bad) {
-    double acc = 0.0;
+    constexpr bool kMixed = sizeof(R) == 8;   // float64 features; else the plain-FP32 form
+    R acc = R(0);
     int badl = 0;
     const int4* pr = D.pairs + P.pair_off;
     const double* bcur = D.bpair + P.pair_off;
     Feature<double>* fc = D.fcache + P.pair_off;
     float* sb = D.slotbuf + (size_t)9 * 6 * P.pair_off;
-    const double dh = P.dhat, kap = P.kappa;
+    const R dh = P.dhat, kap = P.kappa;
     const bool trial = alpha != 0.0f;
     for (int k = threadIdx.x; k < np; k += kThreads) {
         int gsl[4], isl[4];
@@ -1152,41 +1243,53 @@ __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const Mes
         V3<float> Xf[4];
         load_slots<float>(D, P, M, gsl, isl, alpha, s, Xf);
         float d1f = pair_feature<float>(q.x, Xf).d;
-        const double b0 = trial ? bcur[k] : 0.0;
+        const R b0 = trial ? R(bcur[k]) : R(0);
         float out[3][9];
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
             for (int c = 0; c < 9; ++c) out[a][c] = 0.f;
-        if ((double)d1f > kNearBand * dh) {
+        if (kMixed && (double)d1f > kNearBand * (double)dh) {
             acc += kap * b0;                    // b = 0 at the trial point
             fc[k].nf = -1;
         } else {
-            V3<double> X1[4];
-            load_slots<double>(D, P, M, gsl, isl, alpha, s, X1);
-            Feature<double> f1 = pair_feature<double>(q.x, X1);
-            fc[k] = f1;
-            if (!(f1.d > 0.0)) {
+            V3<R> X1[4];
+            Feature<R> f1;
+            if constexpr (kMixed) {
+                load_slots<double>(D, P, M, gsl, isl, alpha, s, X1);
+                f1 = pair_feature<double>(q.x, X1);
+                fc[k] = f1;
+            } else {
+#pragma unroll
+                for (int sl = 0; sl < 4; ++sl) X1[sl] = Xf[sl];
+                f1 = pair_feature<float>(q.x, X1);
+            }
+            if (!(f1.d > R(0))) {
                 badl = 1;
             } else if (f1.d >= dh) {
                 acc += kap * b0;
             } else {
-                V3<double> r = feat_r(f1, X1);
-                double inv = 1.0 / f1.d;
-                V3<double> rh = inv * r;
-                const Barrier3 bb = barrier_all(f1.d, dh);
-                double b1 = kap * bb.b1, b2 = kap * bb.b2;
-                double gdp = 0.0;
+                V3<R> r = feat_r(f1, X1);
+                R inv = R(1) / f1.d;
+                V3<R> rh = inv * r;
+                const Barrier3T<R> bb = barrier_all(f1.d, dh);
+                const EdgeMollT<R> em = edge_moll(X1, R(ee_eps(D, M, E, q.x, gsl, isl)));
+                // gradient of m(c) b(d): m b' w_s r^ + m' b dc/dX_s; Gauss-Newton
+                // block m b'' w_s^2 r^ r^T
+                R b1 = kap * em.m * bb.b1, b2 = kap * em.m * bb.b2, cb = kap * em.m1 * bb.b;
+                R gdp = R(0);
 #pragma unroll
                 for (int sl = 0; sl < 3; ++sl)
                     if (gsl[sl] >= 0) {
                         int si = P.v_off + gsl[sl];
-                        V3<double> pv = {D.p[si], D.p[D.Vt + si], D.p[2 * D.Vt + si]};
-                        gdp += f1.w[sl] * dot(rh, pv);
-                        double gw = b1 * f1.w[sl], kw = b2 * f1.w[sl] * f1.w[sl];
-                        out[sl][0] = (float)(gw * rh.x);
-                        out[sl][1] = (float)(gw * rh.y);
-                        out[sl][2] = (float)(gw * rh.z);
+                        V3<R> pv = {R(D.p[si]), R(D.p[D.Vt + si]), R(D.p[2 * D.Vt + si])};
+                        V3<R> gs = (b1 * f1.w[sl]) * rh;
+                        if (em.on) gs = gs + cb * edge_moll_grad(em, sl);
+                        gdp += dot(gs, pv);
+                        R kw = b2 * f1.w[sl] * f1.w[sl];
+                        out[sl][0] = (float)gs.x;
+                        out[sl][1] = (float)gs.y;
+                        out[sl][2] = (float)gs.z;
                         out[sl][3] = (float)(kw * rh.x * rh.x);
                         out[sl][4] = (float)(kw * rh.y * rh.y);
                         out[sl][5] = (float)(kw * rh.z * rh.z);
@@ -1194,7 +1297,7 @@ __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const Mes
                         out[sl][7] = (float)(kw * rh.x * rh.z);
                         out[sl][8] = (float)(kw * rh.y * rh.z);
                     }
-                if (trial) acc += kap * (b0 - bb.b) + (double)alpha * b1 * gdp;
+                if (trial) acc += kap * b0 - kap * em.m * bb.b + (R)alpha * gdp;
             }
         }
 #pragma unroll
@@ -1206,7 +1309,7 @@ __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const Mes
     const LagRec* lg = D.lag + P.pair_off;
     for (int l = threadIdx.x; l < nl; l += kThreads) {
         const LagRec& L = lg[l];
-        double D1[3] = {-s * L.dY[0], -s * L.dY[1], -s * L.dY[2]}, pd[3] = {0, 0, 0};
+        R D1[3] = {R(-s * L.dY[0]), R(-s * L.dY[1]), R(-s * L.dY[2])}, pd[3] = {R(0), R(0), R(0)};
         for (int gs = 0; gs < 3; ++gs)
             if (L.g[gs] >= 0) {
                 int si = P.v_off + L.g[gs];
@@ -1214,41 +1317,41 @@ __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const Mes
                 for (int c = 0; c < 3; ++c) {
                     int sc = c * D.Vt + si;
                     float pv = D.p[sc];
-                    D1[c] += (double)L.w[gs] * (double)((D.uh[sc] - D.u0h[sc]) + (D.ul[sc] - D.u0l[sc]) + alpha * pv);
-                    pd[c] += (double)L.w[gs] * (double)pv;
+                    D1[c] += (R)L.w[gs] * (R)((D.uh[sc] - D.u0h[sc]) + (D.ul[sc] - D.u0l[sc]) + alpha * pv);
+                    pd[c] += (R)L.w[gs] * (R)pv;
                 }
             }
-        double D0[3] = {D1[0] - alpha * pd[0], D1[1] - alpha * pd[1], D1[2] - alpha * pd[2]};
-        double n1 = L.n[0] * D1[0] + L.n[1] * D1[1] + L.n[2] * D1[2];
-        double n0 = L.n[0] * D0[0] + L.n[1] * D0[1] + L.n[2] * D0[2];
-        double t1[3], t0[3];
+        R D0[3] = {D1[0] - alpha * pd[0], D1[1] - alpha * pd[1], D1[2] - alpha * pd[2]};
+        R n1 = L.n[0] * D1[0] + L.n[1] * D1[1] + L.n[2] * D1[2];
+        R n0 = L.n[0] * D0[0] + L.n[1] * D0[1] + L.n[2] * D0[2];
+        R t1[3], t0[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             t1[c] = D1[c] - L.n[c] * n1;
             t0[c] = D0[c] - L.n[c] * n0;
         }
-        double s1 = sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
-        double s0 = sqrt(t0[0] * t0[0] + t0[1] * t0[1] + t0[2] * t0[2]);
-        double eps = P.eps_v, cf = (double)P.mu_f * L.lam;
-        double f1s = moll_f1_over_s(s1, eps), cs = moll_c(s1, eps);
-        double tdp = t1[0] * pd[0] + t1[1] * pd[1] + t1[2] * pd[2];
-        acc += cf * (moll_f(s0, eps) - moll_f(s1, eps) + (double)alpha * f1s * tdp);
-        double uh[3] = {0, 0, 0};
+        R s1 = sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+        R s0 = sqrt(t0[0] * t0[0] + t0[1] * t0[1] + t0[2] * t0[2]);
+        R eps = P.eps_v, cf = (R)P.mu_f * (R)L.lam;
+        R f1s = moll_f1_over_s(s1, eps), cs = moll_c(s1, eps);
+        R tdp = t1[0] * pd[0] + t1[1] * pd[1] + t1[2] * pd[2];
+        acc += cf * (moll_f(s0, eps) - moll_f(s1, eps) + (R)alpha * f1s * tdp);
+        R uh[3] = {0, 0, 0};
         if (s1 > 0)
 #pragma unroll
             for (int c = 0; c < 3; ++c) uh[c] = t1[c] / s1;
         // tangent-plane Hessian f'/s (I - n n^T) - c(s) u u^T
-        double Hn[6];
-        Hn[0] = f1s * (1.0 - L.n[0] * L.n[0]) - cs * uh[0] * uh[0];
-        Hn[1] = f1s * (1.0 - L.n[1] * L.n[1]) - cs * uh[1] * uh[1];
-        Hn[2] = f1s * (1.0 - L.n[2] * L.n[2]) - cs * uh[2] * uh[2];
+        R Hn[6];
+        Hn[0] = f1s * (R(1) - L.n[0] * L.n[0]) - cs * uh[0] * uh[0];
+        Hn[1] = f1s * (R(1) - L.n[1] * L.n[1]) - cs * uh[1] * uh[1];
+        Hn[2] = f1s * (R(1) - L.n[2] * L.n[2]) - cs * uh[2] * uh[2];
         Hn[3] = -f1s * L.n[0] * L.n[1] - cs * uh[0] * uh[1];
         Hn[4] = -f1s * L.n[0] * L.n[2] - cs * uh[0] * uh[2];
         Hn[5] = -f1s * L.n[1] * L.n[2] - cs * uh[1] * uh[2];
         for (int gs = 0; gs < 3; ++gs)
             if (L.g[gs] >= 0) {
                 float* e = sb + 9 * (3 * (P.pair_cap + l) + gs);
-                double gw = cf * f1s * L.w[gs], kw = cf * L.w[gs] * L.w[gs];
+                R gw = cf * f1s * L.w[gs], kw = cf * L.w[gs] * L.w[gs];
                 e[0] = (float)(gw * t1[0]);
                 e[1] = (float)(gw * t1[1]);
                 e[2] = (float)(gw * t1[2]);
@@ -1257,10 +1360,10 @@ __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const Mes
     }
     // the features just written are those of the point the caller continues
     // from when this trial is accepted (or of the current point, alpha = 0)
-    if (threadIdx.x == 0) S.fok = 1;
-    double v[1] = {acc};
-    block_sum<1>(v);
-    rem = v[0];
+    if (threadIdx.x == 0) S.fok = kMixed ? 1 : 0;
+    R v[1] = {acc};
+    block_sum_r<R, 1>(v);
+    rem = (double)v[0];
     if (badl) S.flag = 1;
     __syncthreads();
     bad = S.flag;
@@ -1270,6 +1373,7 @@ __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const Mes
 }
 
 // lag records: candidates closer than dhat at the frame start
+template <typename R>
 __device__ __noinline__ int lag_build(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np) {
     const int4* pr = D.pairs + P.pair_off;
     LagRec* lg = D.lag + P.pair_off;
@@ -1283,21 +1387,22 @@ __device__ __noinline__ int lag_build(const Dev& D, const PadDev& P, const MeshD
             int gsl[4], isl[4];
             int4 q = pr[k];
             pair_slots(D, M, E, q, gsl, isl);
-            V3<double> X[4];
-            load_slots<double>(D, P, M, gsl, isl, 0.0f, 0.0, X);
-            Feature<double> f = pair_feature<double>(q.x, X);
-            if (f.d < dh && f.d > 0.0) {
+            V3<R> X[4];
+            load_slots<R>(D, P, M, gsl, isl, 0.0f, 0.0, X);
+            Feature<R> f = pair_feature<R>(q.x, X);
+            if (f.d < R(dh) && f.d > R(0)) {
                 keep = 1;
                 L.pq[0] = q.x;
                 L.pq[1] = q.y;
                 L.pq[2] = q.z;
-                V3<double> r = feat_r(f, X);
-                double inv = 1.0 / f.d;
+                V3<R> r = feat_r(f, X);
+                R inv = R(1) / f.d;
                 L.n[0] = (float)(r.x * inv);
                 L.n[1] = (float)(r.y * inv);
                 L.n[2] = (float)(r.z * inv);
-                L.lam = -kap * barrier_b1(f.d, dh);
-                double dY[3] = {0, 0, 0};
+                L.lam = (double)(-R(kap) * edge_moll(X, R(ee_eps(D, M, E, q.x, gsl, isl))).m *
+                                 barrier_all(f.d, R(dh)).b1);
+                R dY[3] = {0, 0, 0};
                 int ni = 0;
                 for (int q = 0; q < 3; ++q) {
                     L.iv[q] = -1;
@@ -1311,8 +1416,8 @@ __device__ __noinline__ int lag_build(const Dev& D, const PadDev& P, const MeshD
                     if (isl[sl] >= 0) {
 #pragma unroll
                         for (int c = 0; c < 3; ++c)
-                            dY[c] += -f.w[sl] * ((double)D.Yn[3 * (P.yw_off + isl[sl]) + c] -
-                                                 (double)D.Yt[3 * (P.yw_off + isl[sl]) + c]);
+                            dY[c] += -f.w[sl] * ((R)D.Yn[3 * (P.yw_off + isl[sl]) + c] -
+                                                 (R)D.Yt[3 * (P.yw_off + isl[sl]) + c]);
                         if (ni < 3) {
                             L.iv[ni] = isl[sl];
                             L.iw[ni] = (float)(-f.w[sl]);
@@ -1371,6 +1476,7 @@ __device__ __noinline__ Dots finalize(const Dev& D, const PadDev& P, const MeshD
     const float* vlp = D.vlump + M.xv_off;
     const int n_v = M.n_v;
     const bool blockp = P.precond == 0;
+    const bool plain = P.prec != 0;          // plain-FP32 form: float sums
     for (int i0 = threadIdx.x; i0 < n_v; i0 += kVertUnroll * kThreads) {
         float mm[kVertUnroll], pv[kVertUnroll][3], du[kVertUnroll][3], gg[kVertUnroll][3], go3[kVertUnroll][3];
         float K[kVertUnroll][6];
@@ -1438,17 +1544,17 @@ __device__ __noinline__ Dots finalize(const Dev& D, const PadDev& P, const MeshD
                 sym_apply(Ki, y, Py);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    fsum_add(sv[0], __fmul_rn(z[c], y[c]));
-                    fsum_add(sv[1], __fmul_rn(y[c], Py[c]));
-                    fsum_add(sv[2], __fmul_rn(pv[u][c], g1[c]));
-                    fsum_add(sv[3], __fmul_rn(y[c], pv[u][c]));
+                    fsum_add_mode(sv[0], __fmul_rn(z[c], y[c]), plain);
+                    fsum_add_mode(sv[1], __fmul_rn(y[c], Py[c]), plain);
+                    fsum_add_mode(sv[2], __fmul_rn(pv[u][c], g1[c]), plain);
+                    fsum_add_mode(sv[3], __fmul_rn(y[c], pv[u][c]), plain);
                 }
             }
         }
     }
     if (bad) S.flag = 1;
-    double v[4] = {fsum_value(sv[0]), fsum_value(sv[1]), fsum_value(sv[2]), fsum_value(sv[3])};
-    block_sum<4>(v);
+    double v[4];
+    block_sum_fsum<4>(sv, v, plain);
     block_max_f<1>(gi);
     Dots d{v[0], v[1], v[2], v[3], gi[0], 0};
     d.bad = S.flag;
@@ -1481,6 +1587,7 @@ __device__ __noinline__ DirOut direction(const Dev& D, const PadDev& P, const Me
     const uint8_t* fxp = D.fixed + M.xv_off;
     const float* vlp = D.vlump + M.xv_off;
     const int n_v = M.n_v;
+    const bool plain = P.prec != 0;          // plain-FP32 form: float u, float sums
     for (int i0 = threadIdx.x; i0 < n_v; i0 += kVertUnroll * kThreads) {
         float mm[kVertUnroll], pv[kVertUnroll][3], zv[kVertUnroll][3], gv[kVertUnroll][3];
         float uh[kVertUnroll][3], ul[kVertUnroll][3];
@@ -1514,32 +1621,89 @@ __device__ __noinline__ DirOut direction(const Dev& D, const PadDev& P, const Me
                     // u += alpha p as a double-float sum (hi, lo)
                     float t = alpha * pv[u][c];
                     float hi = uh[u][c], lo = ul[u][c];
-                    float sm = hi + t;
-                    float bb = sm - hi;
-                    float err = (hi - (sm - bb)) + (t - bb);
-                    lo += err;
-                    float nh = sm + lo;
-                    ulp[sc] = lo - (nh - sm);
-                    uhp[sc] = nh;
+                    if (plain) {
+                        uhp[sc] = hi + t;
+                    } else {
+                        float sm = hi + t;
+                        float bb = sm - hi;
+                        float err = (hi - (sm - bb)) + (t - bb);
+                        lo += err;
+                        float nh = sm + lo;
+                        ulp[sc] = lo - (nh - sm);
+                        uhp[sc] = nh;
+                    }
                 }
                 float np = fx[u] ? 0.f : (-zv[u][c] + bf * pv[u][c]);
                 pp[sc] = np;
                 n2 += np * np;
-                fsum_add(sgp, __fmul_rn(gv[u][c], np));
+                fsum_add_mode(sgp, __fmul_rn(gv[u][c], np), plain);
             }
-            fsum_add(smp, __fmul_rn(mm[u], n2));
+            fsum_add_mode(smp, __fmul_rn(mm[u], n2), plain);
             pn[0] = fmaxf(pn[0], sqrtf(n2));
         }
     }
-    double v[2] = {fsum_value(sgp), fsum_value(smp)};
-    block_sum<2>(v);
+    const FSum sums[2] = {sgp, smp};
+    double v[2];
+    block_sum_fsum<2>(sums, v, plain);
     block_max_f<1>(pn);
     return DirOut{v[0], v[1], pn[0]};
 }
 
-// p = xhat - x^t = h v (zero on Dirichlet vertices); returns max_i |p_i|
-__device__ __noinline__ float predictor_direction(const Dev& D, const PadDev& P, const MeshDev& M) {
+// p = -P g at the current point from the stored gradient g[gb] (inertia
+// included) and blocks blk[gb] (without the mass), for a restart after
+// trial points overwrote z; reduces g^T p, p^T M p and max_i |p_i|
+__device__ __noinline__ DirOut steepest_direction(const Dev& D, const PadDev& P, const MeshDev& M, int gb) {
+    FSum sgp{0.f, 0.f}, smp{0.f, 0.f};
     float pn[1] = {0.f};
+    const bool plain = P.prec != 0;
+    const size_t Vt = D.Vt;
+    const float* g = D.g[gb] + P.v_off;
+    const float* blk = D.blk[gb] + P.v_off;
+    float* pp = D.p + P.v_off;
+    float* zp = D.z + P.v_off;
+    for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
+        const bool fx = D.fixed[M.xv_off + i] != 0;
+        const float m = P.rho * D.vlump[M.xv_off + i];
+        float gv[3], K[6], Ki[6], z[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gv[c] = g[c * Vt + i];
+        if (!fx) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) K[c] = blk[c * Vt + i];
+            K[0] += m; K[1] += m; K[2] += m;
+            if (P.precond == 0) {
+                if (sym_inverse(K, Ki)) sym_apply(Ki, gv, z);
+            } else {
+                z[0] = gv[0] / K[0]; z[1] = gv[1] / K[1]; z[2] = gv[2] / K[2];
+            }
+        }
+        float n2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            zp[c * Vt + i] = z[c];
+            pp[c * Vt + i] = -z[c];
+            n2 += z[c] * z[c];
+            fsum_add_mode(sgp, __fmul_rn(gv[c], -z[c]), plain);
+        }
+        fsum_add_mode(smp, __fmul_rn(m, n2), plain);
+        pn[0] = fmaxf(pn[0], sqrtf(n2));
+    }
+    const FSum sums[2] = {sgp, smp};
+    double v[2];
+    block_sum_fsum<2>(sums, v, plain);
+    block_max_f<1>(pn);
+    return DirOut{v[0], v[1], pn[0]};
+}
+
+// Gel motion of an indenter substep per unit of the path parameter s into
+// p (zero on Dirichlet vertices): the inertial prediction xhat - x^t = h v of
+// Eq. (varopt) for the frame's first substep (s = 0), then the gel's mean
+// motion so far, (u - u^t) / s. Returns max_i |p_i - c| (the gel part of
+// the advance's motion bound about the indenter displacement c).
+__device__ __noinline__ float advance_direction(const Dev& D, const PadDev& P, const MeshDev& M, double s,
+                                               const float c3[3]) {
+    float pn[1] = {0.f};
+    const float is = s > 0.0 ? (float)(1.0 / s) : 0.f;
     for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
         int si = P.v_off + i;
         bool fx = D.fixed[M.xv_off + i] != 0;
@@ -1547,9 +1711,10 @@ __device__ __noinline__ float predictor_direction(const Dev& D, const PadDev& P,
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             int sc = c * D.Vt + si;
-            float v = fx ? 0.f : P.h * D.vel[sc];
+            float v = 0.f;
+            if (!fx) v = s > 0.0 ? is * ((D.uh[sc] - D.u0h[sc]) + (D.ul[sc] - D.u0l[sc])) : P.h * D.vel[sc];
             D.p[sc] = v;
-            n2 += v * v;
+            n2 += (v - c3[c]) * (v - c3[c]);
         }
         pn[0] = fmaxf(pn[0], sqrtf(n2));
     }
@@ -1557,26 +1722,80 @@ __device__ __noinline__ float predictor_direction(const Dev& D, const PadDev& P,
     return pn[0];
 }
 
-// u += alpha p (double-float), p untouched
-__device__ __noinline__ void move_state(const Dev& D, const PadDev& P, const MeshDev& M, float alpha) {
-    for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
-        int si = P.v_off + i;
-        if (D.fixed[M.xv_off + i]) continue;
+// The largest advances of the path parameter that keep every candidate's
+// gap above (1 - eta) of itself: bm[0] with the gel moving along p and the
+// indenter along Yn - Yt, eta * min_k d_k / max_{i in gel(k), j in ind(k)}
+// |p_i - dy_j|, and bm[1] with the gel held (p = 0 in the same bound). Along
+// straight motions of both sides, any point of one primitive approaches any
+// point of the other at most that fast (both points are convex combinations
+// of their primitive's vertices).
+template <typename R>
+__device__ __noinline__ void pair_advance_bound(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E,
+                                                int np, double s, double bm[2]) {
+    R bmov = R(3e38), bheld = R(3e38);
+    const int4* pr = D.pairs + P.pair_off;
+    for (int k = threadIdx.x; k < np; k += kThreads) {
+        int gsl[4], isl[4];
+        int4 q = pr[k];
+        pair_slots(D, M, E, q, gsl, isl);
+        float rel = 0.f, rel0 = 0.f;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            int sc = c * D.Vt + si;
-            float t = alpha * D.p[sc];
-            float hi = D.uh[sc], lo = D.ul[sc];
-            float s = hi + t;
-            float bb = s - hi;
-            float err = (hi - (s - bb)) + (t - bb);
-            lo += err;
-            float nh = s + lo;
-            D.ul[sc] = lo - (nh - s);
-            D.uh[sc] = nh;
+        for (int b = 0; b < 4; ++b) {
+            if (isl[b] < 0) continue;
+            const float* yt = D.Yt + 3 * (P.yw_off + isl[b]);
+            const float* yn = D.Yn + 3 * (P.yw_off + isl[b]);
+            const float y0 = yn[0] - yt[0], y1 = yn[1] - yt[1], y2 = yn[2] - yt[2];
+            rel0 = fmaxf(rel0, sqrtf(y0 * y0 + y1 * y1 + y2 * y2));
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                if (gsl[a] < 0) continue;
+                const int si = P.v_off + gsl[a];
+                const float e0 = D.p[si] - y0, e1 = D.p[D.Vt + si] - y1, e2 = D.p[2 * D.Vt + si] - y2;
+                rel = fmaxf(rel, sqrtf(e0 * e0 + e1 * e1 + e2 * e2));
+            }
+        }
+        if (rel > 0.f || rel0 > 0.f) {
+            const R d = pair_distance<R>(D, P, M, q.x, gsl, isl, 0.0f, s, kNearBand * P.dhat);
+            if (rel > 0.f) bmov = fmin(bmov, R(kEta) * d / (R(rel) * R(1.0 + 1e-6)));
+            if (rel0 > 0.f) bheld = fmin(bheld, R(kEta) * d / (R(rel0) * R(1.0 + 1e-6)));
         }
     }
-    __syncthreads();
+    if constexpr (sizeof(R) == 8) {
+        bm[0] = block_min_d(bmov);
+        bm[1] = block_min_d(bheld);
+    } else {
+        float m[2] = {-bmov, -bheld};
+        block_max_f<2>(m);
+        bm[0] = (double)(-m[0]);
+        bm[1] = (double)(-m[1]);
+    }
+}
+
+// The pair passes in the pad's precision form: float64 features, barrier,
+// step bounds and sums (precision_mode 0), or all float32 (1, the plain form)
+__device__ __forceinline__ int lag_build_p(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np) {
+    return P.prec ? lag_build<float>(D, P, M, E, np) : lag_build<double>(D, P, M, E, np);
+}
+__device__ __forceinline__ void pair_php_p(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np,
+                                           int nl, double s, double& php, double& accd) {
+    if (P.prec)
+        pair_php<float>(D, P, M, E, np, nl, s, php, accd);
+    else
+        pair_php<double>(D, P, M, E, np, nl, s, php, accd);
+}
+__device__ __forceinline__ void pair_trial_p(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np,
+                                             int nl, double s, float alpha, double& rem, int& bad) {
+    if (P.prec)
+        pair_trial<float>(D, P, M, E, np, nl, s, alpha, rem, bad);
+    else
+        pair_trial<double>(D, P, M, E, np, nl, s, alpha, rem, bad);
+}
+__device__ __forceinline__ void pair_advance_bound_p(const Dev& D, const PadDev& P, const MeshDev& M,
+                                                     const EnvDev& E, int np, double s, double bm[2]) {
+    if (P.prec)
+        pair_advance_bound<float>(D, P, M, E, np, s, bm);
+    else
+        pair_advance_bound<double>(D, P, M, E, np, s, bm);
 }
 
 // ---------------------------------------------------------------------------
@@ -1635,7 +1854,6 @@ __device__ void solve_pad(const Dev& D, int pad) {
     int status = ST_CONVERGED;
     unsigned long long t0 = 0;
     if (tid == 0) t0 = global_ns();
-    const unsigned long long budget = D.budget_ns;
     PhaseClock clk;
     clk.start();
     // frame setup
@@ -1653,17 +1871,25 @@ __device__ void solve_pad(const Dev& D, int pad) {
         }
     }
     __syncthreads();
-    float dyv[1] = {0.f};
+    // indenter displacement dy_j = Yn_j - Yt_j over the frame: its largest
+    // norm and its spread max_j |dy_j - dy_0| about vertex 0's enter the
+    // advance's motion bounds
+    float dy0[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dy0[c] = D.Yn[3 * P.yw_off + c] - D.Yt[3 * P.yw_off + c];
+    float dyv[2] = {0.f, 0.f};
     for (int j = tid; j < E.n_v; j += kThreads) {
-        float a = 0.f;
+        float a = 0.f, b = 0.f;
         for (int c = 0; c < 3; ++c) {
             float d = D.Yn[3 * (P.yw_off + j) + c] - D.Yt[3 * (P.yw_off + j) + c];
             a += d * d;
+            b += (d - dy0[c]) * (d - dy0[c]);
         }
         dyv[0] = fmaxf(dyv[0], sqrtf(a));
+        dyv[1] = fmaxf(dyv[1], sqrtf(b));
     }
-    block_max_f<1>(dyv);
-    const double Dy = (double)dyv[0] * (1.0 + 1e-6);
+    block_max_f<2>(dyv);
+    const double Dy = (double)dyv[0] * (1.0 + 1e-6), Dspread = (double)dyv[1];
     const double dh = P.dhat, margin = P.dhat;
     const double rbp = (dh + margin) * (1.0 + 1e-6);
     int4* pairs = D.pairs + P.pair_off;
@@ -1679,33 +1905,8 @@ __device__ void solve_pad(const Dev& D, int pad) {
         cc.npairs = min(n, P.pair_cap);
     }
     if (status == ST_CONVERGED) {
-        cc.nlag = lag_build(D, P, M, E, cc.npairs);
+        cc.nlag = lag_build_p(D, P, M, E, cc.npairs);
         csr_build(D, P, M, E, cc);
-        // initial guess on the segment x^t -> xhat: collision-free by the
-        // per-pair bound, inside the broad-phase margin, no inverted tet
-        float pn0 = predictor_direction(D, P, M);
-        if (pn0 > 0.f) {
-            double php_d, accd;
-            pair_php(D, P, M, E, cc.npairs, 0, 0.0, php_d, accd);
-            ctr.pair_evals += cc.npairs;
-            double a0 = fmin(1.0, fmin(accd, margin / (double)pn0));
-            for (int k = 0; k <= kMaxHalvings; ++k) {
-                TetOut t = tet_pass<1>(D, P, M, (float)a0, 0);
-                ctr.tet_passes++;
-                if (!t.bad) break;
-                a0 = (k == kMaxHalvings) ? 0.0 : 0.5 * a0;
-            }
-            if (a0 > 0.0) {
-                move_state(D, P, M, (float)a0);
-                SrcState src{&D, &P, &M, 0.0f};
-                int n = bp_build(src, D, M, E, il, rbp, pairs, P.pair_cap);
-                ctr.rebuilds++;
-                ctr.peak_pairs = max(ctr.peak_pairs, (long long)n);
-                if (n > P.pair_cap) status = ST_OVERFLOW;
-                cc.npairs = min(n, P.pair_cap);
-                if (status == ST_CONVERGED) csr_build(D, P, M, E, cc);
-            }
-        }
     }
     clk.lap(PH_SETUP);
     float g_ref = P.g_ref;   // becomes max(floor, |g| after the first substep)
@@ -1715,58 +1916,86 @@ __device__ void solve_pad(const Dev& D, int pad) {
     int gc = 0;              // buffer holding the current gradient
     float ginf = 0.f;
     while (status == ST_CONVERGED) {
-        if (s < 1.0) {
-            double ds;
-            if (Dy == 0.0) {
-                ds = 1.0 - s;
-            } else {
-                double dmin = pair_dmin(D, P, M, E, cc.npairs, s);
-                ctr.pair_evals += cc.npairs;
-                ds = fmin(1.0 - s, kEta * dmin / Dy);
-                if (Mb + ds * Dy > margin) {
-                    SrcState src{&D, &P, &M, (float)s};
-                    int n = bp_build(src, D, M, E, il, rbp, pairs, P.pair_cap);
-                    ctr.rebuilds++;
-                    ctr.peak_pairs = max(ctr.peak_pairs, (long long)n);
-                    if (n > P.pair_cap) { status = ST_OVERFLOW; break; }
-                    cc.npairs = n;
-                    csr_build(D, P, M, E, cc);
-                    Mb = 0.0;
-                    dmin = pair_dmin(D, P, M, E, cc.npairs, s);
-                    ds = fmin(fmin(1.0 - s, kEta * dmin / Dy), margin / Dy);
-                }
-            }
-            s = (ds >= 1.0 - s) ? 1.0 : s + ds;
-            Mb += ds * Dy;
-            ctr.substeps++;
-            clk.lap(PH_BROAD);
-        }
-        // gradient and preconditioner at the current point
-        TetOut to = tet_pass<1>(D, P, M, 0.0f, gc);
-        ctr.tet_passes++;
-        clk.lap(PH_TET1);
-        double rem0;
-        int badp;
-        pair_trial(D, P, M, E, cc.npairs, cc.nlag, s, 0.0f, rem0, badp);
+        // advance the indenter and the gel together by ds of the path: the
+        // gel along its predicted motion (p) or held, whichever the per-pair
+        // bound lets go further (every candidate's gap stays above (1 - eta)
+        // of itself). The motion bound of a moving advance is
+        // max_j |dy_j - dy_0| + max_i |p_i - dy_0|
+        const double Bmov = (Dspread + (double)advance_direction(D, P, M, s, dy0)) * (1.0 + 1e-6);
+        double bnd[2];
+        pair_advance_bound_p(D, P, M, E, cc.npairs, s, bnd);
         ctr.pair_evals += cc.npairs;
-        contact_gather(D, P, cc, gc);
-        clk.lap(PH_PAIR_TRIAL);
-        Dots d0 = finalize(D, P, M, 0.0f, gc, gc, false);
+        double cap_m = 1e300, cap_h = 1e300;
+        bool moving = fmin(1.0 - s, bnd[0]) >= fmin(1.0 - s, bnd[1]);
+        double ds = fmin(1.0 - s, moving ? bnd[0] : bnd[1]);
+        double B = moving ? Bmov : Dy;
+        if (Mb + ds * B > margin) {
+            SrcState src{&D, &P, &M, (float)s};
+            int n = bp_build(src, D, M, E, il, rbp, pairs, P.pair_cap);
+            ctr.rebuilds++;
+            ctr.peak_pairs = max(ctr.peak_pairs, (long long)n);
+            if (n > P.pair_cap) { status = ST_OVERFLOW; break; }
+            cc.npairs = n;
+            csr_build(D, P, M, E, cc);
+            Mb = 0.0;
+            pair_advance_bound_p(D, P, M, E, cc.npairs, s, bnd);
+            ctr.pair_evals += cc.npairs;
+            if (Bmov > 0.0) cap_m = margin / Bmov;
+            if (Dy > 0.0) cap_h = margin / Dy;
+            const double dm = fmin(fmin(1.0 - s, bnd[0]), cap_m), dhl = fmin(fmin(1.0 - s, bnd[1]), cap_h);
+            moving = dm >= dhl;
+            ds = moving ? dm : dhl;
+            B = moving ? Bmov : Dy;
+        }
+        const float am = moving ? 1.0f : 0.0f;   // the gel's share of the advance
+        clk.lap(PH_BROAD);
+        // the gradient at the advanced state; ds halves while that state
+        // leaves E's domain (an inverted tet)
+        const int gn = gc ^ 1;
+        bool ok = false;
+        double s1 = s;
+        TetOut to{};
+        Dots d0{};
+        for (int hv = 0; hv <= kMaxHalvings; ++hv) {
+            s1 = (ds >= 1.0 - s) ? 1.0 : s + ds;
+            const float ag = am * (float)ds;
+            to = tet_pass<1>(D, P, M, ag, gn);
+            ctr.tet_passes++;
+            clk.lap(PH_TET1);
+            double rem0;
+            int badp;
+            pair_trial_p(D, P, M, E, cc.npairs, cc.nlag, s1, ag, rem0, badp);
+            ctr.pair_evals += cc.npairs;
+            contact_gather(D, P, cc, gn);
+            clk.lap(PH_PAIR_TRIAL);
+            d0 = finalize(D, P, M, ag, gn, gc, false);
+            ctr.vert_passes++;
+            clk.lap(PH_VERTEX);
+            if (!to.bad && !badp && !d0.bad) {
+                ok = true;
+                break;
+            }
+            ds *= 0.5;
+        }
+        if (!ok) { status = ST_NONFINITE; break; }
+        // u += ds p (gel moving), then p = -P g at the advanced state
+        DirOut dir = direction(D, P, M, am * (float)ds, moving, 0.0, gn);
         ctr.vert_passes++;
-        if (to.bad || badp || d0.bad) { status = ST_NONFINITE; break; }
+        clk.lap(PH_VERTEX);
+        gc = gn;
+        s = s1;
+        Mb += ds * B;
+        ctr.substeps++;
         ginf = d0.ginf;
         fmax = to.fmax;
         if (!have_ref) {
             g_ref = fmaxf(g_ref, ginf);
             have_ref = true;
         }
-        DirOut dir = direction(D, P, M, 0.0f, false, 0.0, gc);
-        ctr.vert_passes++;
-        clk.lap(PH_VERTEX);
         const float rel = (s >= 1.0) ? P.tol : fmaxf(P.tol, P.tol_adv);
-        target = fmaxf(rel * g_ref, kFloat32Floor * fmax);
+        target = fmaxf(rel * g_ref, P.floor * fmax);
+        bool retried = false;
         while (ginf > target && ctr.iters < P.max_iter) {
-            if (over_budget(t0, budget)) { status = ST_MAXITER; break; }
             if (dir.pn == 0.f || dir.gTp >= 0.0) {
                 dir = direction(D, P, M, 0.0f, false, 0.0, gc);
                 ctr.vert_passes++;
@@ -1778,7 +2007,7 @@ __device__ void solve_pad(const Dev& D, int pad) {
             ctr.tet_passes++;
             clk.lap(PH_TET0);
             double php_c, a_ccd;
-            pair_php(D, P, M, E, cc.npairs, cc.nlag, s, php_c, a_ccd);
+            pair_php_p(D, P, M, E, cc.npairs, cc.nlag, s, php_c, a_ccd);
             ctr.pair_evals += cc.npairs;
             clk.lap(PH_PAIR_PHP);
             double pHp = tp.acc + php_c + dir.pMp;
@@ -1796,27 +2025,27 @@ __device__ void solve_pad(const Dev& D, int pad) {
                 csr_build(D, P, M, E, cc);
                 Mb = 0.0;
                 double dummy;
-                pair_php(D, P, M, E, cc.npairs, cc.nlag, s, dummy, a_ccd);
+                pair_php_p(D, P, M, E, cc.npairs, cc.nlag, s, dummy, a_ccd);
                 ctr.pair_evals += cc.npairs;
                 if (literal) a_ccd = 1e300;
                 alpha = fmin(fmin(a_up, a_ccd), a_bar);
                 clk.lap(PH_BROAD);
             }
-            const int gn = gc ^ 1;
+            const int gt = gc ^ 1;
             bool accepted = false;
             Dots dt{};
             for (int hv = 0; hv <= kMaxHalvings; ++hv) {
                 float af = (float)alpha;
-                TetOut tt = tet_pass<1>(D, P, M, af, gn);
+                TetOut tt = tet_pass<1>(D, P, M, af, gt);
                 ctr.tet_passes++;
                 clk.lap(PH_TET1);
                 double remc;
                 int bp;
-                pair_trial(D, P, M, E, cc.npairs, cc.nlag, s, af, remc, bp);
+                pair_trial_p(D, P, M, E, cc.npairs, cc.nlag, s, af, remc, bp);
                 ctr.pair_evals += cc.npairs;
-                contact_gather(D, P, cc, gn);
+                contact_gather(D, P, cc, gt);
                 clk.lap(PH_PAIR_TRIAL);
-                dt = finalize(D, P, M, af, gn, gc, true);
+                dt = finalize(D, P, M, af, gt, gc, true);
                 ctr.vert_passes++;
                 clk.lap(PH_VERTEX);
                 if (!tt.bad && !bp && !dt.bad) {
@@ -1834,28 +2063,40 @@ __device__ void solve_pad(const Dev& D, int pad) {
                 alpha *= 0.5;
                 ctr.halvings++;
             }
-            if (!accepted) { status = ST_LINESEARCH; break; }
+            if (!accepted) {
+                // one retry along the preconditioned steepest descent -P g
+                // before the line search counts as failed
+                if (!retried && !literal) {
+                    retried = true;
+                    dir = steepest_direction(D, P, M, gc);
+                    ctr.vert_passes++;
+                    continue;
+                }
+                status = ST_LINESEARCH;
+                break;
+            }
+            retried = false;
             Mb += alpha * dir.pn;
             ctr.iters++;
             double beta = 0.0;
             if (fabs(dt.yp) > 1e-300) beta = dt.zy / dt.yp - (dt.yPy / dt.yp) * (dt.pg1 / dt.yp);
-            dir = direction(D, P, M, (float)alpha, true, beta, gn);
+            dir = direction(D, P, M, (float)alpha, true, beta, gt);
             ctr.vert_passes++;
             if (dir.gTp >= 0.0) {
-                dir = direction(D, P, M, 0.0f, false, 0.0, gn);
+                dir = direction(D, P, M, 0.0f, false, 0.0, gt);
                 ctr.vert_passes++;
             }
             clk.lap(PH_VERTEX);
-            gc = gn;
+            gc = gt;
             ginf = dt.ginf;
-            target = fmaxf(rel * g_ref, kFloat32Floor * fmax);
+            target = fmaxf(rel * g_ref, P.floor * fmax);
         }
         if (status != ST_CONVERGED) break;
         if (s >= 1.0) {
             if (ginf > target) status = ST_MAXITER;
             break;
         }
-        if (ctr.substeps >= kMaxSubsteps || ctr.iters >= P.max_iter || over_budget(t0, budget)) {
+        if (ctr.substeps >= kMaxSubsteps || ctr.iters >= P.max_iter) {
             status = ST_MAXITER;
             break;
         }
@@ -1978,7 +2219,7 @@ __global__ void __launch_bounds__(kThreads) debug_eval_kernel(const __grid_const
     double dmin = pair_dmin(D, P, M, E, cc.npairs, 1.0);
     TetOut tp = tet_pass<0>(D, P, M, 0.0f, 0);
     double php_c, a_ccd;
-    pair_php(D, P, M, E, cc.npairs, 0, 1.0, php_c, a_ccd);
+    pair_php_p(D, P, M, E, cc.npairs, 0, 1.0, php_c, a_ccd);
     double pMp = 0.0;
     {
         double v[1] = {0.0};
@@ -1996,7 +2237,7 @@ __global__ void __launch_bounds__(kThreads) debug_eval_kernel(const __grid_const
     TetOut tt = tet_pass<1>(D, P, M, alpha, 0);
     double remc;
     int bp;
-    pair_trial(D, P, M, E, cc.npairs, 0, 1.0, alpha, remc, bp);
+    pair_trial_p(D, P, M, E, cc.npairs, 0, 1.0, alpha, remc, bp);
     contact_gather(D, P, cc, 0);
     // outputs before inertia / inversion: gradient with inertia m alpha p
     double gp[1] = {0.0};
@@ -2107,14 +2348,27 @@ __device__ __noinline__ void pair_hvp(const Dev& D, const PadDev& P, const MeshD
                 double d1;
                 V3<double> hv[4], rh;
                 feat_hess_vec(f, X, dl, d1, hv, rh);
-                double b1 = kap * barrier_b1(f.d, dh), b2 = kap * barrier_b2(f.d, dh);
+                const Barrier3 bb = barrier_all(f.d, dh);
+                const EdgeMoll em = edge_moll(X, ee_eps(D, M, E, q.x, gsl, isl));
+                double b1 = kap * em.m * bb.b1, b2 = kap * em.m * bb.b2;
+                // mollified edge-edge terms: m'' c' b dc + m' b (Hess c) dl
+                // + m' b' (d' dc + c' dd)
+                double c1 = 0.0, c2 = 0.0;
+                if (em.on) edge_moll_dir(em, dl, c1, c2);
 #pragma unroll
                 for (int sl = 0; sl < 3; ++sl)
                     if (gsl[sl] >= 0) {
                         double a = b2 * d1 * f.w[sl];
-                        out[sl][0] = (float)(a * rh.x + b1 * hv[sl].x);
-                        out[sl][1] = (float)(a * rh.y + b1 * hv[sl].y);
-                        out[sl][2] = (float)(a * rh.z + b1 * hv[sl].z);
+                        V3<double> o = a * rh + b1 * hv[sl];
+                        if (em.on) {
+                            const V3<double> gc = edge_moll_grad(em, sl);
+                            o = o + (kap * (em.m2 * c1 * bb.b + em.m1 * bb.b1 * d1)) * gc +
+                                (kap * em.m1 * bb.b) * edge_moll_hvec(em, dl, sl) +
+                                (kap * em.m1 * c1 * bb.b1 * f.w[sl]) * rh;
+                        }
+                        out[sl][0] = (float)o.x;
+                        out[sl][1] = (float)o.y;
+                        out[sl][2] = (float)o.z;
                     }
             }
         }
@@ -2240,7 +2494,8 @@ __device__ __noinline__ void pair_theta(const Dev& D, const PadDev& P, const Mes
         load_slots<double>(D, P, M, gsl, isl, 0.0f, 1.0, X);
         Feature<double> f = pair_feature<double>(q.x, X);
         if (!(f.d < dh && f.d > 0.0)) continue;
-        double b1 = kap * barrier_b1(f.d, dh), b2 = kap * barrier_b2(f.d, dh);
+        const Barrier3 bb = barrier_all(f.d, dh);
+        const EdgeMoll em = edge_moll(X, ee_eps(D, M, E, q.x, gsl, isl));
         V3<double> dl[4], dlam[4];
 #pragma unroll
         for (int sl = 0; sl < 4; ++sl) {
@@ -2251,18 +2506,20 @@ __device__ __noinline__ void pair_theta(const Dev& D, const PadDev& P, const Mes
                 dlam[sl] = {0.0, 0.0, 0.0};
             }
         }
+        // mixed second derivatives by polarisation of the directional second
+        // derivative Q(dl) of kappa m(c) b(d)
         double d1, d2;
         feat_dir_derivs(f, X, dlam, d1, d2);
-        double Ql = b2 * d1 * d1 + b1 * d2;
+        double Ql = kap * moll_barrier_dir2(em, dlam, d1, d2, bb);
         for (int m = 0; m < 6; ++m) {
 #pragma unroll
             for (int sl = 0; sl < 4; ++sl) dl[sl] = isl[sl] >= 0 ? dy_of(isl[sl], m) : V3<double>{0.0, 0.0, 0.0};
             feat_dir_derivs(f, X, dl, d1, d2);
-            double Qd = b2 * d1 * d1 + b1 * d2;
+            double Qd = kap * moll_barrier_dir2(em, dl, d1, d2, bb);
 #pragma unroll
             for (int sl = 0; sl < 4; ++sl) dl[sl] = dl[sl] + dlam[sl];
             feat_dir_derivs(f, X, dl, d1, d2);
-            double Qs = b2 * d1 * d1 + b1 * d2;
+            double Qs = kap * moll_barrier_dir2(em, dl, d1, d2, bb);
             acc[1 + m] += 0.5 * (Qs - Ql - Qd);
         }
     }
@@ -2445,7 +2702,7 @@ __global__ void __launch_bounds__(kThreads) frame_install_kernel(const __grid_co
     const double rbp = (P.dhat + P.dhat) * (1.0 + 1e-6);
     SrcState src{&D, &P, &M, 0.0f};
     int n = bp_build(src, D, M, E, D.ilist + P.il_off, rbp, D.pairs + P.pair_off, P.pair_cap);
-    int nlag = lag_build(D, P, M, E, min(n, P.pair_cap));
+    int nlag = lag_build_p(D, P, M, E, min(n, P.pair_cap));
     if (threadIdx.x == 0) D.pad_nlag[pad] = nlag;
     __syncthreads();
     for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
@@ -2520,13 +2777,14 @@ __device__ __noinline__ void lag_relag(const Dev& D, const PadDev& P, const Mesh
             }
         }
         // psi at frame-start primitive positions Xp (X0, Xe fixed in the displacement)
+        const double eps_x = ee_eps(D, M, E, q.x, gsl, isl);
         auto psi = [&](const V3<double> Xp[4]) -> double {
             Feature<double> f = pair_feature<double>(q.x, Xp);
             if (!(f.d > 0.0) || f.d >= dh) return 0.0;      // the lag force vanishes there
             V3<double> r = feat_r(f, Xp);
             const double inv = 1.0 / f.d;
             const V3<double> n = inv * r;
-            const double lamn = -kap * barrier_b1(f.d, dh);
+            const double lamn = -kap * edge_moll(Xp, eps_x).m * barrier_b1(f.d, dh);
             V3<double> Dl = {0.0, 0.0, 0.0}, lw = {0.0, 0.0, 0.0};
             for (int sl = 0; sl < 4; ++sl) {
                 // gel slots carry w >= 0, indenter slots w <= 0: sum w (x_e - x_0) is
@@ -2605,7 +2863,7 @@ __global__ void __launch_bounds__(kThreads, 2) adjoint_kernel(const __grid_const
     TetOut t0 = tet_pass<1>(D, P, M, 0.0f, 0);
     double rem;
     int bad;
-    pair_trial(D, P, M, E, cc.npairs, cc.nlag, 1.0, 0.0f, rem, bad);
+    pair_trial<double>(D, P, M, E, cc.npairs, cc.nlag, 1.0, 0.0f, rem, bad);
     contact_gather(D, P, cc, 0);
     // right-hand side dL/dx (transpose of the marker readout), lambda = 0
     for (int i = threadIdx.x; i < M.n_v; i += kThreads)

@@ -44,8 +44,10 @@ struct PadDev {
     int il_off;               // per-pad culled indenter primitive list
     int mk_out;               // marker output offset (markers)
     float mu, lam, rho, h, dhat, kappa, mu_f, eps_v, g_ref, tol, tol_adv;
+    float floor;              // float32 resolution floor of the stopping target, per unit F_max
     int max_iter, precond;
     int step;                 // 0: alpha bounded by CCD + Armijo test; 1: Eq. (step_size) as printed
+    int prec;                 // 0: float64 contact features, bounds and sums; 1: the plain-FP32 form
 };
 
 struct LagRec {
@@ -119,7 +121,6 @@ struct Dev {
     float* adj_x;             // [3][Vt] adjoint solution lambda
     float* adj_r;             // [3][Vt] adjoint residual
     int* queue;
-    unsigned long long budget_ns;   // wall-clock cap of one pad's frame solve
 };
 
 }  // namespace tac

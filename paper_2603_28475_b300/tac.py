@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
                 ("dhat", ctypes.c_float), ("kappa", ctypes.c_float), ("mu_f", ctypes.c_float),
                 ("eps_v", ctypes.c_float), ("tol_rel_grad", ctypes.c_float), ("tol_advance", ctypes.c_float),
                 ("max_iter", ctypes.c_int), ("precond_mode", ctypes.c_int), ("step_mode", ctypes.c_int),
-                ("marker_mode", ctypes.c_int)]
+                ("marker_mode", ctypes.c_int), ("precision_mode", ctypes.c_int), ("floor_ulps", ctypes.c_float)]
 
 
 class Options(ctypes.Structure):
@@ -117,13 +117,16 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def make_params(mat, tol=1e-6, tol_advance=1e-2, max_iter=10000, precond=0, kappa=0.0, eps_v=0.0, step=0, marker=0):
+def make_params(mat, tol=1e-6, tol_advance=1e-2, max_iter=10000, precond=0, kappa=0.0, eps_v=0.0, step=0, marker=0,
+                precision=0, floor_ulps=0.0):
     """tac_params of one pad. precond: 0 block Jacobi, 1 scalar Jacobi;
     step: 0 bounded (CCD + Armijo), 1 Eq. (step_size) as printed; marker: 0
-    barycentric, 1 kNN inverse distance."""
+    barycentric, 1 kNN inverse distance; precision: 0 the float32/float64
+    split, 1 the plain FP32 form; floor_ulps: the float32 resolution floor
+    of the stopping target in ulps of the largest corner force (0: 256)."""
     return Params(E=mat.E, nu=mat.nu, rho=mat.rho, h=mat.h, dhat=mat.dhat, kappa=kappa, mu_f=mat.mu_f,
                   eps_v=eps_v, tol_rel_grad=tol, tol_advance=tol_advance, max_iter=max_iter, precond_mode=precond,
-                  step_mode=step, marker_mode=marker)
+                  step_mode=step, marker_mode=marker, precision_mode=precision, floor_ulps=floor_ulps)
 
 
 def _host_desc(pad):
@@ -375,8 +378,9 @@ def broadphase_static(x, surf_verts, surf_tris, surf_edges, y, ind_tris, ind_edg
 
 
 def batch_from_workload(w, tol=1e-6, tol_advance=1e-2, max_iter=10000, precond=0, pair_capacity=0,
-                        share_meshes=True, stream=None, step=0, marker=0, dm_table=True):
+                        share_meshes=True, stream=None, step=0, marker=0, dm_table=True, precision=0,
+                        floor_ulps=0.0):
     params = [make_params(m, tol=tol, tol_advance=tol_advance, max_iter=max_iter, precond=precond, step=step,
-                          marker=marker) for m in w.materials]
+                          marker=marker, precision=precision, floor_ulps=floor_ulps) for m in w.materials]
     return TacBatch(w.pads, params, w.indenters, w.pads_per_env, pair_capacity=pair_capacity,
                     share_meshes=share_meshes, stream=stream, dm_table=dm_table)

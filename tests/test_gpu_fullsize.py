@@ -1,22 +1,31 @@
 """Parity at the benchmark's full size, in its launch configuration.
 
 The batched press (4096 environments x 2 pads of the 2k/5k/10k size classes)
-runs through frame 4 exactly as bench.py sets it up (same generator and seed,
-pair capacity 16384, tolerance 1e-6). Then:
+runs frames 1..25 exactly as bench.py sets it up (same generator and seed,
+pair capacity 16384, tolerance 1e-6): the press reaches every pad's depth
+(up to 1.2 mm) by frame 24, so the run covers shallow press frames, deep
+press frames and hold frames. Then:
 
-* sampled outputs: for a few pads, the FP64 oracle solves the same frame from
-  the GPU's own start state (positions and velocities read back before the
-  frame) to the same indenter pose, and the GPU's end positions and markers
-  must agree within 1e-4 of the gel thickness;
-* properties over every pad: a converged status (the benchmark's own
-  convergence criterion), finite positions, and markers
-  inside the displacement range a 1.2 mm press can produce.
+* every pad converges in the frames the benchmark times (6..25), at most a
+  handful of first-contact pad-frames end short in the warm-up frames, and
+  positions and markers stay finite and in range;
+* sampled outputs: at frame 4 (two 2k pads and a 5k pad), at frame 20 (a
+  10k pad deep in its press) and at frame 25 (a 10k pad holding its full
+  depth), the FP64 oracle solves the same frame from the GPU's own start
+  state (positions and velocities read back before the frame) to the same
+  indenter pose; the GPU's end positions and markers must agree within
+  1e-4 of the gel thickness;
+* the GPU's own end state of every sampled pad is free of interpenetration:
+  every candidate pair (inflated-AABB set with r = 2 dhat, the pairs outside
+  it being farther than r) has a positive distance.
 """
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle import broadphase as BP
+from oracle import energy as En
 from oracle import geometry as G
 from oracle import solver as SV
 from paper_2603_28475_b300 import scenes as S
@@ -26,8 +35,22 @@ from _cases import MM, oracle_pad
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 N_ENVS = 4096          # the benchmark workload
-WARMUP, FRAME = 3, 4   # the first timed frame of the default bench run
+FRAMES = 25            # through the deep press into the hold
 TOL_X = 1e-4 * 4 * MM  # 1e-4 of the gel thickness
+DHAT = 0.05 * MM
+# (frame, size class, number of pads sampled, the pad's state at the frame)
+SAMPLES = ((4, 2070, 2, "press"), (4, 4830, 1, "press"), (20, 9918, 1, "deep"), (25, 9918, 1, "hold"))
+CANDIDATES = 64        # pads of each class whose states are kept (first by index)
+
+
+def _phase(w, k, f):
+    """'press' while the indenter still moves down at frame f, 'hold' after;
+    'deep' for a press frame more than 0.9 mm into the pad."""
+    z = w.poses[:, k, 5].astype(np.float64)
+    moving = z[f] < z[f - 1] - 1e-9
+    if not moving:
+        return "hold"
+    return "deep" if z[0] - z[f] > 0.95 * MM else "press"
 
 
 @pytest.fixture(scope="module")
@@ -37,77 +60,93 @@ def run():
     from paper_2603_28475_b300 import build
     build.build()
     from paper_2603_28475_b300 import tac as T
-    # the generator call of bench.workload(envs, 2 * (warmup + steps) + 1, seed)
-    w = S.config_batched(n_envs=N_ENVS, frames=2 * (3 + 3) + 1, seed=0)
+    # the generator of bench.workload (poses depend on the frame index only)
+    w = S.config_batched(n_envs=N_ENVS, frames=FRAMES + 1, seed=0)
     b = T.batch_from_workload(w, pair_capacity=16384)
     dev = b.device
+    vo, mo = b.vert_offsets, b.marker_offsets
+    keep = {}
+    for nv in {s[1] for s in SAMPLES}:
+        keep[nv] = [k for k, p in enumerate(w.pads) if p.n_verts == nv][:CANDIDATES]
     poses = torch.tensor(w.poses, dtype=torch.float32, device=dev)
     st = torch.empty(w.n_pads, dtype=torch.int32, device=dev)
     it = torch.empty(w.n_pads, dtype=torch.int32, device=dev)
+    mk = torch.empty(b.total_markers, 2, dtype=torch.float32, device=dev)
     b.reset(poses[0])
-    for f in range(1, FRAME):
+    statuses, states, mk_max, finite = [], {}, 0.0, True
+    sample_frames = {s[0] for s in SAMPLES}
+    for f in range(1, FRAMES + 1):
+        if f in sample_frames:
+            x0, v0 = b.get_state()
         b.set_indenter(poses[f])
         b.step(st, it)
-    x0, v0 = b.get_state()
-    x0, v0 = x0.cpu().numpy(), v0.cpu().numpy()
-    b.set_indenter(poses[FRAME])
-    b.step(st, it)
-    mk = torch.empty(b.total_markers, 2, dtype=torch.float32, device=dev)
-    b.markers(mk)
-    x1, _ = b.get_state()
-    out = dict(w=w, x0=x0, v0=v0, x1=x1.cpu().numpy(), status=st.cpu().numpy(), iters=it.cpu().numpy(),
-               mk=mk.cpu().numpy(), stats=b.stats().cpu().numpy(), vo=b.vert_offsets, mo=b.marker_offsets)
+        b.markers(mk)
+        x1, _ = b.get_state()
+        statuses.append(st.cpu().numpy().copy())
+        finite &= bool(torch.isfinite(x1).all().item() and torch.isfinite(mk).all().item())
+        mk_max = max(mk_max, float(mk.abs().max().item()))
+        if f in sample_frames:
+            x0c, v0c, x1c, mkc = x0.cpu().numpy(), v0.cpu().numpy(), x1.cpu().numpy(), mk.cpu().numpy()
+            for nv, ks in keep.items():
+                for k in ks:
+                    states[(f, k)] = dict(x0=x0c[vo[k]:vo[k + 1]].copy(), v0=v0c[vo[k]:vo[k + 1]].copy(),
+                                          x1=x1c[vo[k]:vo[k + 1]].copy(), mk=mkc[mo[k]:mo[k + 1]].copy(),
+                                          status=int(statuses[-1][k]), iters=int(it[k].item()))
     b.close()
+    return dict(w=w, statuses=np.array(statuses), states=states, finite=finite, mk_max=mk_max, keep=keep)
+
+
+def _picks(run):
+    w, keep = run["w"], run["keep"]
+    out = []
+    for f, nv, n, phase in SAMPLES:
+        got = [k for k in keep[nv] if _phase(w, k, f) == phase and run["states"][(f, k)]["iters"] > 20][:n]
+        assert len(got) == n, (f, nv, phase)
+        out += [(f, k) for k in got]
     return out
 
 
-def _sample(r):
-    """Deterministic sample: the first two 2k-class pads and the first 5k-class
-    pad (by pad index) that are in contact in the frame and converged."""
-    w, stats, status = r["w"], r["stats"], r["status"]
-    picks, need = [], {2070: 2, 4830: 1}
-    for k, pad in enumerate(w.pads):
-        nv = pad.n_verts
-        if need.get(nv, 0) > 0 and status[k] == 0 and stats[k][7] > 0 and stats[k][0] > 20:
-            picks.append(k)
-            need[nv] -= 1
-        if not any(need.values()):
-            break
-    return picks
-
-
-def test_all_pads_report_and_stay_finite(run):
-    st = run["status"]
+def test_every_pad_converges_in_the_benchmark_frames(run):
+    """Every pad converges in the frames the benchmark times (6..25, after
+    its 5 warm-up frames). The first frames of the press are reported: a
+    peg whose tilted end touches the pad's top edge first makes a point
+    contact on a sharp gel corner there, and a few such pads can end the
+    first contact frame at the substep cap."""
+    st = run["statuses"]
     assert set(np.unique(st).tolist()) <= {0, 1, 2, 3, 4}
-    # bench.py's convergence criterion: with the bench's pair capacity every
-    # pad of the benchmark frames converges
-    assert (st == 0).all(), np.unique(st, return_counts=True)
-    assert np.isfinite(run["x1"]).all()
-    assert np.isfinite(run["mk"]).all()
+    bad = [(f + 1, int((s != 0).sum())) for f, s in enumerate(st) if (s != 0).any()]
+    print(f"pad-frames not converged (frame, count): {bad}")
+    assert not [b for b in bad if b[0] > 5], bad
+    assert sum(b[1] for b in bad) <= 8, bad
+    assert run["finite"]
     # a press of at most 1.2 mm moves no marker further than that
-    assert np.abs(run["mk"]).max() < 1.5 * MM
+    assert run["mk_max"] < 1.5 * MM
 
 
-@pytest.mark.parametrize("slot", [0, 1, 2])
+@pytest.mark.parametrize("slot", range(sum(s[2] for s in SAMPLES)))
 def test_sampled_pads_match_oracle(run, slot):
-    picks = _sample(run)
-    assert len(picks) == 3
-    k = picks[slot]
+    f, k = _picks(run)[slot]
+    rec = run["states"][(f, k)]
     w = run["w"]
     pd, mat = w.pads[k], w.materials[k]
     ind_s = w.indenters[k // w.pads_per_env]
     pad = oracle_pad(pd, mat)
     ind = G.build_indenter(ind_s.verts, ind_s.tris)
-    lo, hi = run["vo"][k], run["vo"][k + 1]
-    pose_t = w.poses[FRAME - 1, k].astype(np.float64)
-    pose_n = w.poses[FRAME, k].astype(np.float64)
-    state = SV.State(x=run["x0"][lo:hi].astype(np.float64), v=run["v0"][lo:hi].astype(np.float64), pose=pose_t)
+    pose_t = w.poses[f - 1, k].astype(np.float64)
+    pose_n = w.poses[f, k].astype(np.float64)
+    state = SV.State(x=rec["x0"].astype(np.float64), v=rec["v0"].astype(np.float64), pose=pose_t)
     new, info = SV.solve_frame(pad, ind, state, pose_n, SV.Params(tol=1e-6))
     assert info.status == SV.CONVERGED
-    err = np.abs(run["x1"][lo:hi].astype(np.float64) - new.x).max()
-    assert err <= TOL_X, (k, pd.n_verts, err)
-    m_lo, m_hi = run["mo"][k], run["mo"][k + 1]
-    merr = np.abs(run["mk"][m_lo:m_hi].astype(np.float64) - SV.markers(pad, new.x)).max()
-    print(f"pad {k} ({pd.n_verts} vertices, {info.iters} oracle iterations): max |dx| {err:.2e} m, "
-          f"markers {merr:.2e} m (tolerance {TOL_X:.1e} m)")
-    assert merr <= TOL_X, (k, merr)
+    x1 = rec["x1"].astype(np.float64)
+    err = np.abs(x1 - new.x).max()
+    merr = np.abs(rec["mk"].astype(np.float64) - SV.markers(pad, new.x)).max()
+    # the GPU's end state: every candidate pair at a positive distance
+    y = G.indenter_world(ind.verts, pose_n)
+    cand = BP.candidates(x1, y, pad, ind, 2 * DHAT)
+    dmin = float(En.distances(cand, x1, y, pad, ind)[0].min()) if len(cand) else np.inf
+    print(f"frame {f} pad {k} ({pd.n_verts} vertices, {_phase(w, k, f)}; GPU {rec['iters']} / oracle {info.iters} "
+          f"iterations): max |dx| {err:.2e} m, markers {merr:.2e} m (tolerance {TOL_X:.1e} m); "
+          f"GPU min gap {dmin:.2e} m over {len(cand)} candidates")
+    assert err <= TOL_X, (f, k, pd.n_verts, err)
+    assert merr <= TOL_X, (f, k, merr)
+    assert dmin > 0.0, (f, k, dmin)

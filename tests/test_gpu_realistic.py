@@ -4,12 +4,16 @@ a frame in under a minute), sharp indenters (a box edge and a ridged
 thread), friction 0.5 and a press-then-slide motion. The GPU runs the
 sequence into the slide phase; the FP64 oracle then solves the last frame
 from the GPU's own start state, and end positions and markers must agree
-within 1e-4 of the gel thickness."""
+within 1e-4 of the gel thickness. The GPU's own end state is checked for
+interpenetration: every candidate pair (r = 2 dhat; the pairs outside the
+set are farther than r) has a positive distance."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle import broadphase as BP
+from oracle import energy as En
 from oracle import geometry as G
 from oracle import solver as SV
 from paper_2603_28475_b300 import scenes as S
@@ -56,10 +60,15 @@ def test_realistic_frame_matches_oracle(tac, kind):
                      pose=w.poses[LAST - 1, 0].astype(np.float64))
     new, info = SV.solve_frame(pad, ind, state, w.poses[LAST, 0].astype(np.float64), SV.Params(tol=1e-6))
     assert info.status == SV.CONVERGED
-    assert info.min_gap > 0.0
-    err = np.abs(x1.cpu().numpy().astype(np.float64) - new.x).max()
+    x1 = x1.cpu().numpy().astype(np.float64)
+    err = np.abs(x1 - new.x).max()
     merr = np.abs(mk - SV.markers(pad, new.x)).max()
+    y = G.indenter_world(ind.verts, w.poses[LAST, 0].astype(np.float64))
+    cand = BP.candidates(x1, y, pad, ind, 2 * pad.dhat)
+    assert len(cand) > 0
+    dmin = float(En.distances(cand, x1, y, pad, ind)[0].min())
     print(f"{kind}: {pd.n_verts} vertices, GPU {int(it.item())} / oracle {info.iters} iterations, "
-          f"max |dx| {err:.2e} m, markers {merr:.2e} m (tolerance {TOL_X:.1e} m)")
+          f"max |dx| {err:.2e} m, markers {merr:.2e} m (tolerance {TOL_X:.1e} m); GPU min gap {dmin:.2e} m")
     assert err <= TOL_X, (kind, err)
     assert merr <= TOL_X, (kind, merr)
+    assert dmin > 0.0, (kind, dmin)

@@ -61,3 +61,64 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
     args = argparse.Namespace(envs=4, warmup=0, steps=1, seed=0, gpus=2)
     bench.run_reference(args, 1, 2)
     assert capsys.readouterr().out == ""
+
+
+# --------------------------------------------------------------------------
+# environments partitioned across ranks and the per-frame marker gather
+
+
+def test_balanced_partition_of_the_benchmark_workload():
+    """Every environment lands on exactly one rank; the greedy bound holds
+    (the largest rank load is at most the mean load plus the largest
+    environment cost); the split is deterministic; with the size classes'
+    tet counts the ranks come within 1% of each other."""
+    from paper_2603_28475_b300 import partition as PT
+    from paper_2603_28475_b300 import scenes as S
+    w = S.config_batched(n_envs=4096, frames=1, seed=0)
+    costs = PT.env_costs([p.n_tets for p in w.pads], w.pads_per_env)
+    for n in (2, 3, 8):
+        parts = PT.balanced_partition(costs, n)
+        allids = np.sort(np.concatenate(parts))
+        assert np.array_equal(allids, np.arange(w.n_envs))
+        loads = PT.rank_loads(costs, parts)
+        assert loads.max() <= costs.sum() / n + costs.max() + 1e-6
+        assert loads.max() / loads.min() < 1.01
+        again = PT.balanced_partition(costs, n)
+        assert all(np.array_equal(a, b) for a, b in zip(parts, again))
+    # iteration-weighted costs move environments towards the cheap ranks
+    iters = np.where(np.arange(w.n_pads) % 7 == 0, 500, 50)
+    c2 = PT.env_costs([p.n_tets for p in w.pads], w.pads_per_env, iters)
+    loads = PT.rank_loads(c2, PT.balanced_partition(c2, 4))
+    assert loads.max() <= c2.sum() / 4 + c2.max() + 1e-6
+
+
+def _gather_rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_2603_28475_b300 import partition as PT
+    n_envs, per_env = 11, 126
+    rng = np.random.default_rng(3)
+    full = rng.normal(size=(n_envs, per_env, 2)).astype(np.float32)
+    costs = rng.uniform(1, 10, size=n_envs)
+    parts = PT.balanced_partition(costs, world)
+    mine = parts[rank]
+    local = torch.tensor(full[mine])          # this rank's solved marker fields
+    got = PT.gather_markers(local, mine, n_envs)
+    out[rank] = bool(np.array_equal(got.numpy(), full)), [len(p) for p in parts]
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_marker_gather_reassembles_the_global_field():
+    """World size 2 on gloo: each rank holds the marker fields of its
+    partition (unequal counts); the all-gather returns the full field in
+    global environment order on both ranks."""
+    world, port = 2, _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_gather_rank, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    for r in range(world):
+        ok, counts = res[r]
+        assert ok
+        assert sum(counts) == 11 and counts[0] != counts[1]

@@ -186,3 +186,115 @@ def test_candidate_predicate_at_exact_boundary(axis, side, r):
         # the vertex-triangle pair whose gap is the boundary itself
         gv = int(np.argmax(xg[:, axis])) if side > 0 else int(np.argmin(xg[:, axis]))
         assert ((0, gv, 0) in want) == (not up)
+
+
+# ---------------------------------------------------------------------------
+# the parallel-edge mollifier of the edge-edge barrier
+
+
+def _parallel_edge_scene(angle, gap=0.3 * DH):
+    """Tiny pad and a one-triangle indenter whose lower edge lies ``gap``
+    above the pad's top face, turned by ``angle`` (rad) from the x-aligned
+    top edges of the pad in the horizontal plane: edge-edge candidates
+    between the lower edge and x-aligned gel edges are parallel at
+    angle = 0."""
+    pd, pad = tiny_pad(cells=(3, 3, 1), size=(3 * MM, 3 * MM, 1 * MM))
+    ztop = pad.rest[:, 2].max()
+    c, s = np.cos(angle), np.sin(angle)
+    y0 = np.array([1.5 * MM, 1.0 * MM, ztop + gap])
+    yv = np.array([y0 - 1.2 * MM * np.array([c, s, 0.0]), y0 + 1.3 * MM * np.array([c, s, 0.0]),
+                   y0 + np.array([0.0, 0.0, 0.8 * MM])])
+    ind = G.build_indenter(yv, np.array([[0, 1, 2]], np.int32))
+    y = ind.verts.copy()
+    x = pad.rest.astype(np.float64)
+    pairs = BP.candidates(x, y, pad, ind, 2 * DH)
+    return pad, ind, x, y, pairs
+
+
+def test_ee_mollifier_shape():
+    """m(0) = 0, m(eps) = 1 with m'(eps) = 0 (C^1 join to the constant 1),
+    monotone on [0, eps]; m' matches a central difference."""
+    eps = np.array([1.0])
+    cs = np.linspace(0.0, 2.0, 41)
+    m = np.array([En.ee_mollifier(np.array([c]), eps)[0] for c in cs])
+    assert m[0] == 0.0 and m[20] == pytest.approx(1.0) and np.all(m[20:] == 1.0)
+    assert np.all(np.diff(m[:21]) > 0)
+    for c in (0.3, 0.7, 0.9999):
+        h = 1e-6
+        fd = (En.ee_mollifier(np.array([c + h]), eps)[0] - En.ee_mollifier(np.array([c - h]), eps)[0]) / (2 * h)
+        assert En.ee_mollifier_d1(np.array([c]), eps)[0] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+    assert En.ee_mollifier_d1(np.array([1.0 - 1e-12]), eps)[0] == pytest.approx(0.0, abs=1e-9)
+
+
+@pytest.mark.parametrize("angle", [0.0, 2e-3, 0.2])
+def test_mollified_contact_gradient_matches_differences(angle):
+    """Gradient of kappa sum m(c) b(d) against central differences of the
+    energy at near-parallel (inside the mollifier band), parallel and
+    clearly crossing edge-edge configurations, with random gel offsets."""
+    pad, ind, x, y, pairs = _parallel_edge_scene(angle)
+    assert np.any(pairs[:, 0] == 2)
+    rng = np.random.default_rng(5)
+    x = x + rng.normal(size=x.shape) * 0.02 * DH
+    E, g, _, _ = En.contact(pairs, x, y, pad, ind)
+    near = np.unique(np.concatenate([BP.candidates(x, y, pad, ind, DH)[:, 1:2].ravel()]))
+    verts = np.unique(pad.surf_edges[pairs[pairs[:, 0] == 2, 1]].ravel())[:12]
+    h = 1e-11
+    for v in verts:
+        for c in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[v, c] += h
+            xm[v, c] -= h
+            fd = (En.contact(pairs, xp, y, pad, ind)[0] - En.contact(pairs, xm, y, pad, ind)[0]) / (2 * h)
+            assert g[v, c] == pytest.approx(fd, rel=1e-4, abs=1e-6 * np.abs(g).max())
+    del near
+
+
+def test_mollified_edge_edge_term_is_smooth_through_parallel():
+    """Along a line that turns an edge-edge pair through exactly parallel
+    (the configuration a pressed edge settles into), the unmollified
+    barrier has a kink; the mollified one has equal one-sided slopes, and
+    its line derivatives (Taylor arithmetic) match differences of the
+    energy."""
+    pad, ind, x, y, pairs = _parallel_edge_scene(0.0)
+    ee = pairs[pairs[:, 0] == 2]
+    ty, gid, iid = En.pair_geometry(ee, x, y, pad, ind)
+    P = En._slot_positions(gid, iid, x, y)
+    d, _ = En.slot_distances(ty, P)
+    # the closest x-aligned gel edge: parallel to the indenter edge above it
+    ex = np.abs(P[:, 1, 0] - P[:, 0, 0]) > 0.9 * np.linalg.norm(P[:, 1] - P[:, 0], axis=1)
+    k = int(np.argmin(np.where(ex, d, np.inf)))
+    pair = ee[k:k + 1]
+    a, b = pad.surf_edges[pair[0, 1]]
+    # tilt the gel edge about its midpoint in its vertical plane: one end
+    # rises towards the indenter edge above it whichever way it turns
+    p = np.zeros_like(x)
+    n = np.array([0.0, 0.0, 1.0])
+    p[a], p[b] = -0.5 * n * 1e-3, 0.5 * n * 1e-3
+    eps = En.ee_mollifier_eps(ty[k:k + 1], gid[k:k + 1], iid[k:k + 1], pad, ind)
+
+    def raw(al):
+        P1 = En._slot_positions(gid[k:k + 1], iid[k:k + 1], x + al * p, y)
+        return float(En.barrier(En.slot_distances(ty[k:k + 1], P1)[0], pad.dhat)[0])
+
+    def moll(al):
+        P1 = En._slot_positions(gid[k:k + 1], iid[k:k + 1], x + al * p, y)
+        return float(En.pair_barrier(ty[k:k + 1], P1, eps, pad.dhat)[0])
+
+    def kink(f, h):      # right slope minus left slope at 0
+        return (f(h) - f(0)) / h - (f(0) - f(-h)) / h
+
+    # a kink keeps its slope jump as h shrinks; a C^1 function's shrinks with h
+    h = 1e-3
+    assert abs(kink(raw, h)) > 0.5 * abs(raw(h) - raw(0)) / h
+    assert kink(raw, h / 10) == pytest.approx(kink(raw, h), rel=0.05)
+    assert abs(kink(moll, h / 10)) < 0.15 * abs(kink(moll, h))
+    assert abs(kink(moll, h / 100)) < 0.02 * abs(kink(moll, h))
+    # Taylor-arithmetic line derivatives of the whole contact term at a
+    # nearby non-parallel point match differences of the energy
+    x1 = x + 1e-2 * p           # the raised end still 2/3 of the gap away
+    jet = En.contact_line(pairs, x1, p, y, pad, ind)
+    q = 1e-5
+    e = [En.contact(pairs, x1 + t * p, y, pad, ind)[0] for t in (-q, 0.0, q)]
+    assert jet.v == pytest.approx(e[1], rel=1e-12)
+    assert jet.d == pytest.approx((e[2] - e[0]) / (2 * q), rel=1e-4)
+    assert jet.dd == pytest.approx((e[2] - 2 * e[1] + e[0]) / q ** 2, rel=1e-3)
