@@ -24,10 +24,9 @@ with the step rule of Eq. (step_size). Readings where the paper is silent:
     indenter substep);
   * indenter motion: the indenter vertices move on the straight path
     y(s) = (1 - s) y^t + s y^{t+1}, and the gel moves with them: a substep
-    advances s by ds and the gel by ds w, w the gel's predicted motion per
-    unit s: the inertial prediction xhat - x^t of Eq. varopt for the first
-    substep, then the gel's mean motion so far, (x - x^t) / s (zero on
-    Dirichlet vertices). ds is at most
+    advances s by ds and the gel by ds w, w = xhat - x^t the inertial
+    prediction of Eq. varopt (zero on Dirichlet vertices), the same for
+    every substep of the frame. ds is at most
     eta * d_k / max_{i in gel(k), j in ind(k)} |w_i - dy_j| for every
     candidate k (dy = y^{t+1} - y^t): along straight motions of both sides
     the points of two primitives approach at most that fast, so no gap
@@ -379,10 +378,6 @@ def solve_frame(pad, ind, state, pose_next, prm=Params(), trace=None, lag=None):
         if info.substeps >= prm.max_substeps or info.iters >= prm.max_iter:
             info.status = MAXITER
             break
-        # the next substep moves the gel on with its mean motion so far
-        w_pred = (x - x_t) / s
-        w_pred[~free] = 0.0
-        B_pred = float(np.linalg.norm(dy - dy[0], axis=1).max() + np.linalg.norm(w_pred - dy[0], axis=1).max())
     info.grad_inf = float(np.abs(g[free]).max(initial=0.0)) if info.status != NONFINITE else np.inf
     new = State(x=x, v=(x - x_t) / h, pose=np.asarray(pose_next, np.float64).copy())
     return new, info

@@ -1696,14 +1696,12 @@ __device__ __noinline__ DirOut steepest_direction(const Dev& D, const PadDev& P,
 }
 
 // Gel motion of an indenter substep per unit of the path parameter s into
-// p (zero on Dirichlet vertices): the inertial prediction xhat - x^t = h v of
-// Eq. (varopt) for the frame's first substep (s = 0), then the gel's mean
-// motion so far, (u - u^t) / s. Returns max_i |p_i - c| (the gel part of
-// the advance's motion bound about the indenter displacement c).
-__device__ __noinline__ float advance_direction(const Dev& D, const PadDev& P, const MeshDev& M, double s,
-                                               const float c3[3]) {
+// p: the inertial prediction xhat - x^t = h v of Eq. (varopt), zero on
+// Dirichlet vertices (the same for every substep of the frame). Returns
+// max_i |p_i - c| (the gel part of the advance's motion bound about the
+// indenter displacement c).
+__device__ __noinline__ float advance_direction(const Dev& D, const PadDev& P, const MeshDev& M, const float c3[3]) {
     float pn[1] = {0.f};
-    const float is = s > 0.0 ? (float)(1.0 / s) : 0.f;
     for (int i = threadIdx.x; i < M.n_v; i += kThreads) {
         int si = P.v_off + i;
         bool fx = D.fixed[M.xv_off + i] != 0;
@@ -1711,8 +1709,7 @@ __device__ __noinline__ float advance_direction(const Dev& D, const PadDev& P, c
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             int sc = c * D.Vt + si;
-            float v = 0.f;
-            if (!fx) v = s > 0.0 ? is * ((D.uh[sc] - D.u0h[sc]) + (D.ul[sc] - D.u0l[sc])) : P.h * D.vel[sc];
+            float v = fx ? 0.f : P.h * D.vel[sc];
             D.p[sc] = v;
             n2 += (v - c3[c]) * (v - c3[c]);
         }
@@ -1921,7 +1918,7 @@ __device__ void solve_pad(const Dev& D, int pad) {
         // bound lets go further (every candidate's gap stays above (1 - eta)
         // of itself). The motion bound of a moving advance is
         // max_j |dy_j - dy_0| + max_i |p_i - dy_0|
-        const double Bmov = (Dspread + (double)advance_direction(D, P, M, s, dy0)) * (1.0 + 1e-6);
+        const double Bmov = (Dspread + (double)advance_direction(D, P, M, dy0)) * (1.0 + 1e-6);
         double bnd[2];
         pair_advance_bound_p(D, P, M, E, cc.npairs, s, bnd);
         ctr.pair_evals += cc.npairs;
