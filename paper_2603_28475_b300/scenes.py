@@ -296,6 +296,53 @@ def ridged_thread(radius=3 * MM, length=20 * MM, pitch=1.5 * MM, depth=0.4 * MM,
     return Indenter(verts=V.astype(np.float32), tris=ind.tris)
 
 
+def chamfered_peg(radius=2.5 * MM, length=12 * MM, chamfer=0.6 * MM, n_around=96, n_along=40, n_cap=12):
+    """Closed peg with its axis along local z, centred at the origin, whose
+    lower end is chamfered at 45 degrees by ``chamfer``: a surface of
+    revolution (side rings down the straight part and the chamfer, then
+    concentric rings across the lower face, a fan at each end). Convex, so
+    each face is oriented away from the centroid."""
+    zb, zt = -length / 2, length / 2
+    # profile (r, z) from the top rim down the side and chamfer, then in to the axis
+    n_ch = max(2, n_along // 8)
+    zs = np.linspace(zt, zb + chamfer, n_along - n_ch + 1)
+    prof = [(radius, z) for z in zs]
+    prof += [(radius - chamfer * k / n_ch, zb + chamfer * (1 - k / n_ch)) for k in range(1, n_ch + 1)]
+    r_end = radius - chamfer
+    prof += [(r_end * (1 - k / n_cap), zb) for k in range(1, n_cap)]
+    th = 2 * np.pi * np.arange(n_around) / n_around
+    verts = [(r * np.cos(t), r * np.sin(t), z) for r, z in prof for t in th]
+    tris = []
+    for i in range(len(prof) - 1):
+        for j in range(n_around):
+            a = i * n_around + j
+            b = i * n_around + (j + 1) % n_around
+            c = (i + 1) * n_around + j
+            d = (i + 1) * n_around + (j + 1) % n_around
+            tris += [(a, b, d), (a, d, c)]
+    top = len(verts)
+    verts.append((0.0, 0.0, zt))
+    bot = len(verts)
+    verts.append((0.0, 0.0, zb))
+    last = (len(prof) - 1) * n_around
+    for j in range(n_around):
+        tris.append((top, j, (j + 1) % n_around))
+        tris.append((bot, last + j, last + (j + 1) % n_around))
+    V = np.array(verts)
+    F = np.array(tris, dtype=np.int64)
+    cen = V[F].mean(axis=1) - V.mean(axis=0)
+    nrm = np.cross(V[F[:, 1]] - V[F[:, 0]], V[F[:, 2]] - V[F[:, 0]])
+    flip = np.einsum("ij,ij->i", nrm, cen) < 0
+    F[flip, 1], F[flip, 2] = F[flip, 2].copy(), F[flip, 1].copy()
+    return Indenter(verts=V.astype(np.float32), tris=F.astype(np.int32))
+
+
+def nut_flank(radius=3 * MM, length=16 * MM, pitch=1.0 * MM, depth=0.35 * MM):
+    """A threaded flank of about 10k triangles: the ridged thread profile
+    on a cylinder along local x (64 around x 80 along)."""
+    return ridged_thread(radius=radius, length=length, pitch=pitch, depth=depth, n_around=64, n_along=80)
+
+
 def lowest_z(verts, rotvec):
     """Lowest local-frame-rotated z of an indenter (pose helper for placing
     the indenter above the gel; plain rotation, no solver arithmetic)."""
@@ -544,6 +591,46 @@ def config_calibration(n_envs=256, frames=16, seed=0, step=0.05 * MM, mu_f=0.5, 
         poses[:, e, 5] = z0 - press
     w = Workload(f"calibration_{n_envs}env", pads, mats, inds, 1, poses.astype(np.float32))
     return w, hidden
+
+
+def config_trajectory(n_envs=64, n_verts=50000, frames=60, seed=0, step=0.05 * MM, slide_step=0.02 * MM,
+                      mu_f=0.5):
+    """Long trajectories on fine pads (the large-scale sweep's configuration):
+    ``n_envs`` environments of one hex-split pad of about ``n_verts``
+    vertices and an indenter of about 10k triangles, alternately a
+    chamfered peg pressing its end (axis near vertical) and a threaded nut
+    flank pressing its thread (axis near horizontal). Per env: rotation
+    vector components ~ U(+-15 deg) about the indenter's nominal
+    orientation, xy offset ~ U(+-1 mm); the indenter presses ``step`` per
+    frame from a d-hat gap to a depth ~ U[0.2, 1.0] mm and holds until half
+    the frames, then slides ``slide_step`` per frame along a random
+    in-plane direction at that depth; friction ``mu_f``."""
+    rng = np.random.default_rng(np.random.PCG64(20260 + 6000 + seed))
+    pad = size_class_pad(n_verts)
+    peg, flank = chamfered_peg(), nut_flank()
+    pads, mats, inds = [], [], []
+    poses = np.zeros((frames + 1, n_envs, 6))
+    half = frames // 2
+    for e in range(n_envs):
+        ind = peg if e % 2 == 0 else flank
+        pads.append(pad)
+        mats.append(Material(mu_f=mu_f))
+        inds.append(ind)
+        rot = np.deg2rad(rng.uniform(-15, 15, size=3))
+        off = rng.uniform(-1 * MM, 1 * MM, size=2)
+        depth = float(rng.uniform(0.2 * MM, 1.0 * MM))
+        ang = float(rng.uniform(0, 2 * np.pi))
+        lx, ly, lz = pad.size
+        cx, cy = lx / 2 + off[0], ly / 2 + off[1]
+        z0 = place_above_box(ind.verts, rot, (cx, cy), pad.size, DHAT, ind.tris)
+        k = np.arange(frames + 1)
+        press = np.minimum(step * np.minimum(k, half), depth + DHAT)
+        slide = slide_step * np.maximum(k - half, 0)
+        poses[:, e, :3] = rot
+        poses[:, e, 3] = cx + np.cos(ang) * slide
+        poses[:, e, 4] = cy + np.sin(ang) * slide
+        poses[:, e, 5] = z0 - press
+    return Workload(f"trajectory_{n_envs}env_{pad.n_verts}v", pads, mats, inds, 1, poses.astype(np.float32))
 
 
 def config_sweep(n_envs, n_verts, frames=8, seed=0, step=0.05 * MM, mu_f=0.5):
