@@ -93,10 +93,26 @@ def parse():
                          "(tests/golden/calibration_targets.npz) instead")
     ap.add_argument("--variants", action="store_true",
                     help="iterations and throughput of the paper-literal variants on the batched workload instead")
+    ap.add_argument("--block-shape", default="auto", choices=["auto", "256", "512"],
+                    help="threads per pad's CTA in the solve launch: the library's autotuner on the first timed "
+                         "frame (auto, before the timed region) or a fixed shape")
     return ap.parse_args()
 
 
 # --------------------------------------------------------------------------- helpers
+
+
+def choose_block_shape(b, poses_next, mode):
+    """Block shape of the batch's solve launch: 'auto' runs the library's
+    autotuner (tac_autotune_block_shape: the next frame solved in each shape
+    from the same state, the state put back) on poses_next; otherwise the
+    given thread count. Returns the bench line's record of the choice."""
+    if mode == "auto":
+        th, ms = b.autotune_block_shape(poses_next, reps=1)
+        return {"threads": th, "chosen_by": "tac_autotune_block_shape on the first timed frame",
+                "tuning_ms": {"256": ms[0], "512": ms[1]}}
+    b.set_block_shape(int(mode))
+    return {"threads": int(mode), "chosen_by": "--block-shape"}
 
 def load_peaks():
     try:
@@ -393,6 +409,7 @@ def run_ours(args, rank, world):
         b.step(status, iters)
         b.markers(mk)
     torch.cuda.synchronize()
+    shape = choose_block_shape(b, poses[args.warmup + 1], args.block_shape)
     # the state after the warm-up: the end-to-end leg re-runs the same frames from it
     ck_x, ck_v = b.get_state()
     ck_x, ck_v = ck_x.clone(), ck_v.clone()
@@ -545,6 +562,7 @@ def run_ours(args, rank, world):
         k32 = min(args.steps, args.fp32_steps)
         b32 = tac.batch_from_workload(w, pair_capacity=args.pair_capacity, dm_table=not args.no_dm_table,
                                       precision=1, max_iter=args.fp32_max_iter)
+        b32.set_block_shape(shape["threads"])
         b32.reset(poses[args.warmup])
         b32.set_state(ck_x, ck_v)
         ms32, conv32, st32, it32 = [], 0, [], []
@@ -612,7 +630,7 @@ def run_ours(args, rank, world):
                "iters_per_pad_frame": {"p50": float(np.percentile(its, 50)), "p99": float(np.percentile(its, 99)),
                                        "max": int(its.max())},
                "frame_ms": {"p50": float(np.percentile(solve_ms, 50)), "p99": float(np.percentile(solve_ms, 99))},
-               "setup_s": t_create, "phase_share": phase_share, "queue": queue}
+               "setup_s": t_create, "phase_share": phase_share, "queue": queue, "block_shape": shape}
         if fp32 is not None:
             out["plain_fp32"] = fp32
         if per_frame:
@@ -723,6 +741,7 @@ def run_sweep(args):
             b.set_indenter(poses[f])
             b.step(st, it)
         torch.cuda.synchronize()
+        shape = choose_block_shape(b, poses[W + 1], args.block_shape)
         stream = torch.cuda.current_stream()
         ms, conv, nbytes, iters = 0.0, 0, 0.0, []
         for f in range(W + 1, W + K + 1):
@@ -741,7 +760,7 @@ def run_sweep(args):
         pts.append({"envs": envs, "pad_verts": w.pads[0].n_verts, "pad_tets": w.pads[0].n_tets,
                     "pair_capacity": cap, "env_frames_per_s": conv / (ms / 1e3), "ms_per_frame": ms / K,
                     "converged_fraction": conv / (K * envs), "iters_p50": float(np.percentile(its, 50)),
-                    "counted_gbs": gbs, "frac_of_peak": gbs / peak})
+                    "counted_gbs": gbs, "frac_of_peak": gbs / peak, "block_shape": shape})
         b.close()
         del b
         torch.cuda.empty_cache()
@@ -891,6 +910,18 @@ def run_trajectory(args, frames=60, n_verts=50000):
     poses = torch.tensor(w.poses, dtype=torch.float32, device=dev)
     st = torch.empty(w.n_pads, dtype=torch.int32, device=dev)
     it = torch.empty(w.n_pads, dtype=torch.int32, device=dev)
+    # the block shape: tuned on frame 6 of an untimed first pass (the
+    # press in contact), then the trajectory runs from rest in that shape
+    tune_frame = 6
+    b.reset(poses[0])
+    if args.block_shape == "auto":
+        for f in range(1, tune_frame):
+            b.set_indenter(poses[f])
+            b.step(st, it)
+        torch.cuda.synchronize()
+    shape = choose_block_shape(b, poses[tune_frame], args.block_shape)
+    if args.block_shape == "auto":
+        shape["chosen_by"] = f"tac_autotune_block_shape on frame {tune_frame} of an untimed first pass"
     b.reset(poses[0])
     stream = torch.cuda.current_stream()
     rec = []
@@ -932,7 +963,7 @@ def run_trajectory(args, frames=60, n_verts=50000):
            "iters_per_pad_frame": {"p50": float(np.percentile(its, 50)), "p99": float(np.percentile(its, 99)),
                                    "max": int(its.max())},
            "counted_gbs": gbs, "frac_of_peak": gbs / peak, "peak": peak, "peak_kind": peak_kind,
-           "clocks": clk.summary()}
+           "clocks": clk.summary(), "block_shape": shape}
     print(json.dumps(out), flush=True)
 
 

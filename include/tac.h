@@ -113,7 +113,9 @@ typedef struct {
  *                 barrier, bound and sum in float32 (the comparator the
  *                 split is measured against)
  *  floor_ulps     the float32 resolution floor of the stopping target in
- *                 ulps of the largest per-corner force F: the target is
+ *                 ulps of the largest force component F summed into the
+ *                 float32 gradient (elastic per-corner forces, barrier and
+ *                 friction per-slot forces): the target is
  *                 max(tol_rel_grad * g_ref, floor_ulps * 2^-24 * F); <= 0
  *                 selects 256 (a float32 gradient is not resolved below a
  *                 few hundred ulps of the forces summed into it; a smaller
@@ -353,7 +355,8 @@ int tac_stats(tac_handle h, long long* stats_dev, void* stream);
 
 /* Convergence record of the last tac_step per pad (device [n_pads*4]
  * double): final max |g_i|, the stopping target, g_ref of the frame, and the
- * largest per-corner force component F. The target is
+ * largest force component F summed into the float32 gradient (elastic
+ * per-corner forces, barrier and friction per-slot forces). The target is
  * max(tol * g_ref, floor_ulps * 2^-24 * F) (tac_params.floor_ulps, 256 by
  * default): a float32 gradient is not resolved below a few hundred ulps of
  * the forces summed into it. */
@@ -388,6 +391,32 @@ int tac_mesh_info(const tac_pad_desc* pad, int* n_patches, int* n_colours, int* 
  * one per pad). A service call for sizing caller buffers; the paper has no
  * counterpart. Any output pointer may be NULL. */
 int tac_sizes(tac_handle h, int* total_verts, int* total_markers, int* pair_capacity, int* grid_ctas);
+
+/* Block shape of tac_step's persistent solve launch. threads = 256: one
+ * 256-thread CTA per pad, two CTAs per SM (the default); 512: one 512-thread
+ * CTA per pad, one per SM, so that each phase of a pad's solve (the
+ * colour-class rounds of the tet passes, the pair and vertex passes) spreads
+ * over twice the threads: the shape for batches with fewer pads than the
+ * 256-thread shape has CTA slots (Sec. 5.1 measures throughput against the
+ * number of environments). Each shape is deterministic and independent of the
+ * pads' order; the two differ in the order of their block reductions, so
+ * their results agree to rounding, not bit for bit. TAC_ERR_INVALID_ARG for
+ * any other value. No device work. */
+int tac_set_block_shape(tac_handle h, int threads);
+
+/* Autotuner of the block shape. From the current state it solves the next
+ * frame (indenter poses pose6_dev, device [n_pads*6]) reps times in each
+ * shape, each time from the same saved state, times each solve with CUDA
+ * events on `stream`, puts back the state, the poses and the per-pad records
+ * the schedule keys on, and selects the shape of the smaller mean time (as
+ * tac_set_block_shape). threads_out (host) receives the chosen shape; ms_out
+ * (host [2], may be NULL) the mean milliseconds of the 256- and 512-thread
+ * solves. The tuning solves count as the last tac_step for tac_stats,
+ * tac_pad_norms and tac_adjoint: call it before a tac_step, not between a
+ * tac_step and its adjoint. Allocates scratch for one copy of the state
+ * (freed before it returns) and synchronises the stream. */
+int tac_autotune_block_shape(tac_handle h, const float* pose6_dev, int reps, int* threads_out, float* ms_out,
+                             void* stream);
 
 /* Message of the last error on this thread (static storage, never NULL). */
 const char* tac_last_error(void);

@@ -12,7 +12,7 @@ import sys
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
-SRC = [os.path.join(PKG, "csrc", f) for f in ("kernels.cu", "api.cu", "mesh.cpp")]
+SRC = [os.path.join(PKG, "csrc", f) for f in ("kernels.cu", "kernels_wide.cu", "api.cu", "mesh.cpp")]
 DEPS = SRC + [os.path.join(PKG, "csrc", f) for f in ("device_math.cuh", "solve.cuh", "mesh.h", "layout.h")] + \
     [os.path.join(ROOT, "include", "tac.h")]
 LIB = os.path.join(PKG, "libtac.so")

@@ -27,6 +27,12 @@ __global__ void adjoint_kernel(const __grid_constant__ Dev D, const float* dLdm,
 size_t shared_bytes();
 cudaError_t configure_kernels();
 void set_last_error(const std::string& msg);
+namespace wide {   // the 512-thread block shape of the solve kernel (kernels_wide.cu)
+constexpr int kThreads = 512;
+__global__ void solve_kernel(const __grid_constant__ Dev D);
+size_t shared_bytes();
+cudaError_t configure_kernels();
+}  // namespace wide
 }  // namespace tac
 
 using namespace tac;
@@ -160,7 +166,9 @@ struct tac_batch {
     int device = 0;
     int n_pads = 0, n_envs = 0, ppe = 1;
     int Vt = 0, XVt = 0, Tt = 0, total_markers = 0, pair_cap = 0;
-    int grid = 0;
+    int grid = 0;                   // CTAs of a 256-thread solve launch
+    int grid_wide = 0;              // CTAs of a 512-thread solve launch
+    int shape = 256;                // block shape of tac_step's solve launch (tac_set_block_shape)
     std::vector<tac_params> params;
     std::vector<PadMesh> meshes;
     std::vector<IndenterMesh> inds;
@@ -209,7 +217,8 @@ void fill_pad_params(tac_batch* b, int p) {
     P.step = q.step_mode;
     P.prec = q.precision_mode;
     // a float32 gradient is resolved only down to a few hundred ulps of the
-    // largest per-corner force that enters it: floor_ulps * 2^-24 (256 by default)
+    // largest force component summed into it (elastic corner forces, barrier
+    // and friction slot forces): floor_ulps * 2^-24 (256 by default)
     P.floor = (q.floor_ulps > 0.0f ? q.floor_ulps : 256.0f) / 16777216.0f;
     b->hstep[p] = q.h;
 }
@@ -544,6 +553,9 @@ int tac_create_batch(const tac_pad_desc* pads, const tac_params* params, int n_p
     CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device));
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, solve_kernel, kThreads, shared_bytes()));
     b->grid = std::max(1, std::min(n_pads, nsm * std::max(1, occ)));
+    CUDA_TRY(wide::configure_kernels());
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, wide::solve_kernel, wide::kThreads, wide::shared_bytes()));
+    b->grid_wide = std::max(1, std::min(n_pads, nsm * std::max(1, occ)));
     CUDA_TRY(cudaStreamSynchronize(st));
     *out = b;
     return TAC_OK;
@@ -594,7 +606,10 @@ int tac_step(tac_handle h, int* pad_status_dev, int* iters_dev, void* stream) {
     // longest predicted pad first (its previous solve time, then its size)
     schedule_kernel<<<1, 1024, 0, st>>>(D, h->d_sched_key, h->d_sched_idx, h->sched_n2, h->d_order);
     CUDA_TRY(cudaGetLastError());
-    solve_kernel<<<h->grid, kThreads, shared_bytes(), st>>>(D);
+    if (h->shape == wide::kThreads)
+        wide::solve_kernel<<<h->grid_wide, wide::kThreads, wide::shared_bytes(), st>>>(D);
+    else
+        solve_kernel<<<h->grid, kThreads, shared_bytes(), st>>>(D);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaMemcpyAsync(h->d_pose_t, h->d_pose_n, 6 * (size_t)h->n_pads * 4, cudaMemcpyDeviceToDevice, st));
     return TAC_OK;
@@ -786,8 +801,95 @@ int tac_sizes(tac_handle h, int* total_verts, int* total_markers, int* pair_capa
     if (total_verts) *total_verts = h->Vt;
     if (total_markers) *total_markers = h->total_markers;
     if (pair_capacity) *pair_capacity = h->pair_cap;
-    if (grid_ctas) *grid_ctas = h->grid;
+    if (grid_ctas) *grid_ctas = h->shape == wide::kThreads ? h->grid_wide : h->grid;
     return TAC_OK;
+}
+
+int tac_set_block_shape(tac_handle h, int threads) {
+    if (!h) return fail(TAC_ERR_INVALID_ARG, "null handle");
+    if (threads != kThreads && threads != wide::kThreads)
+        return fail(TAC_ERR_INVALID_ARG, "block shape must be 256 or 512 threads");
+    h->shape = threads;
+    return TAC_OK;
+}
+
+int tac_autotune_block_shape(tac_handle h, const float* pose6_dev, int reps, int* threads_out, float* ms_out,
+                             void* stream) {
+    if (!h || !pose6_dev || !threads_out || reps < 1) return fail(TAC_ERR_INVALID_ARG, "null argument or reps < 1");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t n3 = 3 * (size_t)h->Vt, np = (size_t)h->n_pads;
+    // the state a solve reads and writes: displacement (hi, lo), velocity,
+    // the three pose arrays and the per-pad records the schedule keys on
+    float* sv = nullptr;
+    float* sp = nullptr;
+    long long* ss = nullptr;
+    int* si = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = TAC_OK;
+    auto release = [&]() {
+        if (sv) cudaFree(sv);
+        if (sp) cudaFree(sp);
+        if (ss) cudaFree(ss);
+        if (si) cudaFree(si);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    auto check = [&](cudaError_t e, const char* what) {
+        if (e != cudaSuccess && rc == TAC_OK) rc = fail(TAC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+        return e == cudaSuccess;
+    };
+    float* const state[3] = {h->dev.uh, h->dev.ul, h->dev.vel};
+    float* const poses[3] = {h->d_pose_t, h->d_pose_n, h->d_pose_s};
+    auto copy_state = [&](bool save) {
+        for (int k = 0; k < 3; ++k) {
+            float* a = sv + k * n3;
+            check(cudaMemcpyAsync(save ? a : state[k], save ? state[k] : a, n3 * 4, cudaMemcpyDeviceToDevice, st),
+                  "state copy");
+            float* b = sp + k * 6 * np;
+            check(cudaMemcpyAsync(save ? b : poses[k], save ? poses[k] : b, 6 * np * 4, cudaMemcpyDeviceToDevice, st),
+                  "pose copy");
+        }
+        check(cudaMemcpyAsync(save ? ss : h->dev.stats, save ? h->dev.stats : ss, 16 * np * 8,
+                              cudaMemcpyDeviceToDevice, st), "record copy");
+    };
+    if (check(cudaMalloc(&sv, 3 * n3 * 4), "cudaMalloc") && check(cudaMalloc(&sp, 18 * np * 4), "cudaMalloc") &&
+        check(cudaMalloc(&ss, 16 * np * 8), "cudaMalloc") && check(cudaMalloc(&si, 2 * np * 4), "cudaMalloc") &&
+        check(cudaEventCreate(&e0), "cudaEventCreate") && check(cudaEventCreate(&e1), "cudaEventCreate")) {
+        copy_state(true);
+        const int shapes[2] = {kThreads, wide::kThreads};
+        float ms[2] = {0.f, 0.f};
+        const int keep = h->shape;
+        for (int c = 0; c < 2 && rc == TAC_OK; ++c) {
+            h->shape = shapes[c];
+            for (int r = 0; r < reps && rc == TAC_OK; ++r) {
+                copy_state(false);
+                int e = tac_set_indenter(h, pose6_dev, nullptr, stream);
+                if (e == TAC_OK) check(cudaEventRecord(e0, st), "cudaEventRecord");
+                if (e == TAC_OK) e = tac_step(h, si, si + np, stream);
+                if (e != TAC_OK) {
+                    rc = e;
+                    break;
+                }
+                float t = 0.f;
+                if (check(cudaEventRecord(e1, st), "cudaEventRecord") && check(cudaEventSynchronize(e1), "sync") &&
+                    check(cudaEventElapsedTime(&t, e0, e1), "cudaEventElapsedTime"))
+                    ms[c] += t / (float)reps;
+            }
+        }
+        copy_state(false);
+        check(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+        h->shape = keep;
+        if (rc == TAC_OK) {
+            h->shape = ms[1] < ms[0] ? wide::kThreads : kThreads;
+            *threads_out = h->shape;
+            if (ms_out) {
+                ms_out[0] = ms[0];
+                ms_out[1] = ms[1];
+            }
+        }
+    }
+    release();
+    return rc;
 }
 
 }  // extern "C"

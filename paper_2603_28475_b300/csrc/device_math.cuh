@@ -170,31 +170,44 @@ __device__ __forceinline__ T seg_param(V3<T> P, V3<T> A, V3<T> B, T& t) {
 
 // Point-triangle feature with slots [P, A, B, C], r = P - closest.
 // Candidates: face interior (if the projection is inside), then edges AB,
-// BC, CA with clamped parameters; the first minimum wins.
+// BC, CA with clamped parameters; the first minimum wins. Bit c of mask
+// selects candidate c (0 face, 1 AB, 2 BC, 3 CA); a candidate left out must
+// be known to lose, which pt_mask certifies from a float32 evaluation. The
+// candidates evaluated are computed exactly as in the full search, so a
+// certified mask gives the full search's result bit for bit.
 template <typename T>
-__device__ Feature<T> pt_feature(V3<T> P, V3<T> A, V3<T> B, V3<T> C) {
+__device__ Feature<T> pt_feature(V3<T> P, V3<T> A, V3<T> B, V3<T> C, int mask = 15) {
     Feature<T> f;
-    V3<T> v0 = B - A, v1 = C - A, v2 = P - A;
-    T d00 = dot(v0, v0), d01 = dot(v0, v1), d11 = dot(v1, v1), d20 = dot(v2, v0), d21 = dot(v2, v1);
-    T den = d00 * d11 - d01 * d01;
-    T l1 = (d11 * d20 - d01 * d21) / den;
-    T l2 = (d00 * d21 - d01 * d20) / den;
-    T l0 = T(1) - l1 - l2;
     T best = sizeof(T) == 8 ? T(1e300) : T(3e38);
     int k = -1;
-    T tab, tbc, tca;
-    if (l0 >= T(0) && l1 >= T(0) && l2 >= T(0) && den > T(0)) {
-        V3<T> n = cross(v0, v1);
-        T s = dot(v2, n);
-        best = s * s / dot(n, n);
-        k = 0;
+    T l0 = T(0), l1 = T(0), l2 = T(0), tab = T(0), tbc = T(0), tca = T(0);
+    if (mask & 1) {
+        V3<T> v0 = B - A, v1 = C - A, v2 = P - A;
+        T d00 = dot(v0, v0), d01 = dot(v0, v1), d11 = dot(v1, v1), d20 = dot(v2, v0), d21 = dot(v2, v1);
+        T den = d00 * d11 - d01 * d01;
+        l1 = (d11 * d20 - d01 * d21) / den;
+        l2 = (d00 * d21 - d01 * d20) / den;
+        l0 = T(1) - l1 - l2;
+        if (l0 >= T(0) && l1 >= T(0) && l2 >= T(0) && den > T(0)) {
+            V3<T> n = cross(v0, v1);
+            T s = dot(v2, n);
+            best = s * s / dot(n, n);
+            k = 0;
+        }
     }
-    T dab = seg_param(P, A, B, tab);
-    if (k < 0 || dab < best) { best = dab; k = 1; }
-    T dbc = seg_param(P, B, C, tbc);
-    if (dbc < best) { best = dbc; k = 2; }
-    T dca = seg_param(P, C, A, tca);
-    if (dca < best) { best = dca; k = 3; }
+    if (k < 0 && !(mask & 14)) mask |= 14;   // the face alone was certified and failed: every edge
+    if (mask & 2) {
+        T dab = seg_param(P, A, B, tab);
+        if (k < 0 || dab < best) { best = dab; k = 1; }
+    }
+    if (mask & 4) {
+        T dbc = seg_param(P, B, C, tbc);
+        if (k < 0 || dbc < best) { best = dbc; k = 2; }
+    }
+    if (mask & 8) {
+        T dca = seg_param(P, C, A, tca);
+        if (k < 0 || dca < best) { best = dca; k = 3; }
+    }
     f.d = sqrt(best);
     f.nf = 0;
 #pragma unroll
@@ -221,33 +234,45 @@ __device__ Feature<T> pt_feature(V3<T> P, V3<T> A, V3<T> B, V3<T> C) {
 // Segment-segment feature with slots [P0, P1, Q0, Q1], r = P(s) - Q(t).
 // Candidates: both interior (non-parallel, unconstrained solution inside
 // [0,1]^2), then P0-vs-Q, P1-vs-Q, Q0-vs-P, Q1-vs-P; the first minimum wins.
+// Bit c of mask selects candidate c, as for pt_feature (ee_mask certifies).
 template <typename T>
-__device__ Feature<T> ee_feature(V3<T> P0, V3<T> P1, V3<T> Q0, V3<T> Q1) {
+__device__ Feature<T> ee_feature(V3<T> P0, V3<T> P1, V3<T> Q0, V3<T> Q1, int mask = 31) {
     Feature<T> f;
-    V3<T> u = P1 - P0, v = Q1 - Q0, w = P0 - Q0;
-    T a = dot(u, u), b = dot(u, v), c = dot(v, v), dd = dot(u, w), e = dot(v, w);
-    T D = a * c - b * b;
     T best = sizeof(T) == 8 ? T(1e300) : T(3e38);
     int k = -1;
     T s = T(0), t = T(0);
-    if (D > T(1e-12) * a * c) {
-        s = (b * e - c * dd) / D;
-        t = (a * e - b * dd) / D;
-        if (s >= T(0) && s <= T(1) && t >= T(0) && t <= T(1)) {
-            V3<T> r = w + s * u - t * v;
-            best = dot(r, r);
-            k = 0;
+    if (mask & 1) {
+        V3<T> u = P1 - P0, v = Q1 - Q0, w = P0 - Q0;
+        T a = dot(u, u), b = dot(u, v), c = dot(v, v), dd = dot(u, w), e = dot(v, w);
+        T D = a * c - b * b;
+        if (D > T(1e-12) * a * c) {
+            s = (b * e - c * dd) / D;
+            t = (a * e - b * dd) / D;
+            if (s >= T(0) && s <= T(1) && t >= T(0) && t <= T(1)) {
+                V3<T> r = w + s * u - t * v;
+                best = dot(r, r);
+                k = 0;
+            }
         }
     }
-    T t0, t1, t2, t3;
-    T d0 = seg_param(P0, Q0, Q1, t0);
-    if (k < 0 || d0 < best) { best = d0; k = 1; }
-    T d1 = seg_param(P1, Q0, Q1, t1);
-    if (d1 < best) { best = d1; k = 2; }
-    T d2 = seg_param(Q0, P0, P1, t2);
-    if (d2 < best) { best = d2; k = 3; }
-    T d3 = seg_param(Q1, P0, P1, t3);
-    if (d3 < best) { best = d3; k = 4; }
+    if (k < 0 && !(mask & 30)) mask |= 30;   // the interior alone was certified and failed
+    T t0 = T(0), t1 = T(0), t2 = T(0), t3 = T(0);
+    if (mask & 2) {
+        T d0 = seg_param(P0, Q0, Q1, t0);
+        if (k < 0 || d0 < best) { best = d0; k = 1; }
+    }
+    if (mask & 4) {
+        T d1 = seg_param(P1, Q0, Q1, t1);
+        if (k < 0 || d1 < best) { best = d1; k = 2; }
+    }
+    if (mask & 8) {
+        T d2 = seg_param(Q0, P0, P1, t2);
+        if (k < 0 || d2 < best) { best = d2; k = 3; }
+    }
+    if (mask & 16) {
+        T d3 = seg_param(Q1, P0, P1, t3);
+        if (k < 0 || d3 < best) { best = d3; k = 4; }
+    }
     f.d = sqrt(best);
 #pragma unroll
     for (int i = 0; i < 4; ++i) f.e[0][i] = f.e[1][i] = T(0);
@@ -263,6 +288,98 @@ __device__ Feature<T> ee_feature(V3<T> P0, V3<T> P1, V3<T> Q0, V3<T> Q1) {
     if (sfree) { f.e[f.nf][0] = T(-1); f.e[f.nf][1] = T(1); f.nf++; }
     if (tfree) { f.e[f.nf][2] = T(1); f.e[f.nf][3] = T(-1); f.nf++; }
     return f;
+}
+
+// ---------------------------------------------------------------------------
+// Float32 certification of the closest-feature search. The float32 slot
+// positions differ from the float64 ones by at most ex per coordinate, so a
+// point-segment candidate's float32 distance is within err = 6 ex + 2^-20 d
+// of its float64 value (the distance is 1-Lipschitz in each slot; the
+// clamped parameter's own error is second order). A candidate whose float32
+// distance exceeds the best by more than 2 err cannot win the float64
+// search. The face (point-triangle) and the interior (edge-edge) candidate,
+// when their projection lies inside with a margin, are the exact minimum
+// and win alone; within the margin the float64 search decides. The masks
+// keep every candidate that can win, so the float64 search over them
+// returns what the full search returns.
+
+__device__ __forceinline__ float cert_err(float ex, float d) { return 6.0f * ex + 9.5367431640625e-7f * d; }
+
+// point-triangle, slots [P, A, B, C]; dmin as pt_feature<float>
+__device__ __forceinline__ int pt_mask(V3<float> P, V3<float> A, V3<float> B, V3<float> C, float ex, float& dmin) {
+    V3<float> v0 = B - A, v1 = C - A, v2 = P - A;
+    float d00 = dot(v0, v0), d01 = dot(v0, v1), d11 = dot(v1, v1), d20 = dot(v2, v0), d21 = dot(v2, v1);
+    float den = d00 * d11 - d01 * d01;
+    float l1 = (d11 * d20 - d01 * d21) / den;
+    float l2 = (d00 * d21 - d01 * d20) / den;
+    float l0 = 1.0f - l1 - l2;
+    float best = 3e38f;
+    if (l0 >= 0.0f && l1 >= 0.0f && l2 >= 0.0f && den > 0.0f) {
+        V3<float> n = cross(v0, v1);
+        float s = dot(v2, n);
+        best = s * s / dot(n, n);
+    }
+    // face status from the projection's distance to each edge line,
+    // l_i |n| / |edge opposite i|: 1 inside, 0 outside, -1 within 16 ex
+    int face = -1;
+    if (den > 1e-6f * d00 * d11) {
+        const float nn = sqrtf(den), tol = 16.0f * ex;
+        const V3<float> v3 = v1 - v0;
+        const float m0 = l0 * nn / sqrtf(dot(v3, v3)), m1 = l1 * nn / sqrtf(d11), m2 = l2 * nn / sqrtf(d00);
+        if (m0 >= tol && m1 >= tol && m2 >= tol) face = 1;
+        else if (m0 <= -tol || m1 <= -tol || m2 <= -tol) face = 0;
+    }
+    float t;
+    const float de[3] = {seg_param(P, A, B, t), seg_param(P, B, C, t), seg_param(P, C, A, t)};
+    float emin = fminf(de[0], fminf(de[1], de[2]));
+    if (best > 2.9e38f || emin < best) best = emin;
+    dmin = sqrtf(best);
+    if (face == 1) return 1;
+    const float r = sqrtf(emin), lim = r + 2.0f * cert_err(ex, r), lim2 = lim * lim;
+    int mask = face < 0 ? 1 : 0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        if (de[j] <= lim2) mask |= 2 << j;
+    return mask;
+}
+
+// edge-edge, slots [P0, P1, Q0, Q1]; dmin as ee_feature<float>
+__device__ __forceinline__ int ee_mask(V3<float> P0, V3<float> P1, V3<float> Q0, V3<float> Q1, float ex, float& dmin) {
+    V3<float> u = P1 - P0, v = Q1 - Q0, w = P0 - Q0;
+    float a = dot(u, u), b = dot(u, v), c = dot(v, v), dd = dot(u, w), e = dot(v, w);
+    float D = a * c - b * b;
+    float best = 3e38f;
+    int inter = -1;   // 1 interior inside, 0 outside, -1 uncertain
+    if (D > 1e-12f * a * c) {
+        float s = (b * e - c * dd) / D;
+        float t = (a * e - b * dd) / D;
+        if (s >= 0.0f && s <= 1.0f && t >= 0.0f && t <= 1.0f) {
+            V3<float> r = w + s * u - t * v;
+            best = dot(r, r);
+        }
+        if (D > 1e-4f * a * c) {
+            // the closest points move by ex / sin(angle) along the edges;
+            // the float32 solve loses (a c / D) ulps to cancellation
+            const float iD = 1.0f / D, sD = sqrtf(D), cond = a * c * iD;
+            const float ar = 1.9073486328125e-6f * cond * (1.0f + sqrtf(dot(w, w) / fminf(a, c)));
+            const float ms = 16.0f * ex * sqrtf(c) / sD + ar, mt = 16.0f * ex * sqrtf(a) / sD + ar;
+            if (s >= ms && s <= 1.0f - ms && t >= mt && t <= 1.0f - mt) inter = 1;
+            else if (s < -ms || s > 1.0f + ms || t < -mt || t > 1.0f + mt) inter = 0;
+        }
+    }
+    float tt;
+    const float de[4] = {seg_param(P0, Q0, Q1, tt), seg_param(P1, Q0, Q1, tt), seg_param(Q0, P0, P1, tt),
+                         seg_param(Q1, P0, P1, tt)};
+    float emin = fminf(fminf(de[0], de[1]), fminf(de[2], de[3]));
+    if (best > 2.9e38f || emin < best) best = emin;
+    dmin = sqrtf(best);
+    if (inter == 1) return 1;
+    const float r = sqrtf(emin), lim = r + 2.0f * cert_err(ex, r), lim2 = lim * lim;
+    int mask = inter < 0 ? 1 : 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (de[j] <= lim2) mask |= 2 << j;
+    return mask;
 }
 
 // r of a feature for slot positions X[4]

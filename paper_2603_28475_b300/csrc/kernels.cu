@@ -22,14 +22,27 @@
 
 #include "solve.cuh"
 
+// TAC_WIDE (kernels_wide.cu) compiles the persistent solve kernel a second
+// time in the 512-thread block shape, in namespace tac::wide; everything
+// else of this file is compiled once, in the 256-thread shape.
+#ifdef TAC_WIDE
 namespace tac {
+namespace wide {
+constexpr int kThreads = 512;         // 16 warps, one CTA per SM
+constexpr int kCtasPerSm = 1;
+#else
+namespace tac {
+constexpr int kCtasPerSm = 2;
+#endif
 
 constexpr float kEta = 0.9f;          // safety factor of the step bounds
 constexpr double kArmijoC = 1e-4;
 constexpr int kMaxHalvings = 20;
 constexpr int kMaxSubsteps = 4000;
 constexpr int kWarps = kThreads / 32;
-static_assert(kWarps == kCtaWarps, "the host balances colour classes for this many warps");
+// the host balances the colour classes for rounds of kCtaWarps patches; a
+// wider CTA runs the same classes in rounds of its own warp count
+static_assert(kWarps % kCtaWarps == 0, "a CTA runs whole rounds of the host's colour classes");
 // A pair whose float32 distance exceeds kNearBand * dhat is outside the
 // barrier's support in float64 as well: at the workloads' coordinate
 // magnitudes (a few cm) the float32 distance is off by ~1e-8 m at most,
@@ -385,11 +398,12 @@ __device__ __forceinline__ double ee_eps(const Dev& D, const MeshDev& M, const E
 
 // feature of a pair from slot positions; type 1 is re-expressed with the gel
 // triangle first and r pointing from the indenter to the gel
+// (mask: the candidates to search, from pair_pick; all by default)
 template <typename T>
-__device__ __forceinline__ Feature<T> pair_feature(int type, const V3<T> X[4]) {
-    if (type == 0) return pt_feature<T>(X[0], X[1], X[2], X[3]);
-    if (type == 2) return ee_feature<T>(X[0], X[1], X[2], X[3]);
-    Feature<T> f = pt_feature<T>(X[3], X[0], X[1], X[2]);
+__device__ __forceinline__ Feature<T> pair_feature(int type, const V3<T> X[4], int mask = 31) {
+    if (type == 0) return pt_feature<T>(X[0], X[1], X[2], X[3], mask & 15);
+    if (type == 2) return ee_feature<T>(X[0], X[1], X[2], X[3], mask);
+    Feature<T> f = pt_feature<T>(X[3], X[0], X[1], X[2], mask & 15);
     Feature<T> g;
     g.d = f.d;
     g.nf = f.nf;
@@ -438,6 +452,23 @@ __device__ __forceinline__ void load_slots<float>(const Dev& D, const PadDev& P,
     }
 }
 
+// Float32 distance of a pair and the mask of the closest-feature candidates
+// that can win its float64 search (pt_mask / ee_mask on the slots in
+// pair_feature's order). The float32 slot positions are within 2 units of
+// 2^-24 of the largest coordinate of the float64 ones (one rounding of the
+// sum and one of the interpolated indenter vertex); ex takes 8.
+__device__ __forceinline__ float pair_pick(int type, const V3<float> X[4], int& mask) {
+    float xm = 0.f;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) xm = fmaxf(xm, fmaxf(fabsf(X[s].x), fmaxf(fabsf(X[s].y), fabsf(X[s].z))));
+    const float ex = 4.76837158203125e-7f * xm;
+    float d;
+    if (type == 0) mask = pt_mask(X[0], X[1], X[2], X[3], ex, d);
+    else if (type == 2) mask = ee_mask(X[0], X[1], X[2], X[3], ex, d);
+    else mask = pt_mask(X[3], X[0], X[1], X[2], ex, d);
+    return d;
+}
+
 // distance of a pair: float32 estimate, float64 when close (relative band);
 // the plain-FP32 form takes the float32 distance
 template <typename R>
@@ -445,14 +476,15 @@ __device__ __forceinline__ R pair_distance(const Dev& D, const PadDev& P, const 
                                            const int gsl[4], const int isl[4], float alpha, double s, double near) {
     V3<float> Xf[4];
     load_slots<float>(D, P, M, gsl, isl, alpha, s, Xf);
-    float df = pair_feature<float>(type, Xf).d;
     if constexpr (sizeof(R) == 4) {
-        return df;                          // the plain-FP32 form
+        return pair_feature<float>(type, Xf).d;   // the plain-FP32 form
     } else {
+        int mask;
+        const float df = pair_pick(type, Xf, mask);
         if ((double)df > near) return (double)df * (1.0 - 1e-5);
         V3<double> Xd[4];
         load_slots<double>(D, P, M, gsl, isl, alpha, s, Xd);
-        return pair_feature<double>(type, Xd).d;
+        return pair_feature<double>(type, Xd, mask).d;
     }
 }
 
@@ -1117,6 +1149,41 @@ __device__ __noinline__ double pair_dmin(const Dev& D, const PadDev& P, const Me
 // p^T H p of the barrier and friction terms and the per-pair step bound at
 // the current point; also stores each pair's barrier value b(d) there, which
 // the line-search trials of this point subtract from (see pair_trial)
+// Float64 features of every pair at the current point u (path parameter s),
+// for a pair set that no trial has evaluated yet (a rebuilt candidate list):
+// what an accepted trial leaves in the feature cache.
+__device__ __noinline__ void pair_cache_fill(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np,
+                                             double s) {
+    const int4* pr = D.pairs + P.pair_off;
+    Feature<double>* fc = D.fcache + P.pair_off;
+    const double dh = P.dhat;
+    for (int k = threadIdx.x; k < np; k += kThreads) {
+        int gsl[4], isl[4];
+        int4 q = pr[k];
+        pair_slots(D, M, E, q, gsl, isl);
+        V3<float> Xf[4];
+        load_slots<float>(D, P, M, gsl, isl, 0.0f, s, Xf);
+        int mask;
+        const float df = pair_pick(q.x, Xf, mask);
+        if ((double)df > kNearBand * dh) {
+            fc[k].nf = -1;
+            fc[k].d = (double)df * (1.0 - 1e-5);
+            continue;
+        }
+        V3<double> X[4];
+        load_slots<double>(D, P, M, gsl, isl, 0.0f, s, X);
+        fc[k] = pair_feature<double>(q.x, X, mask);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) S.fok = 1;
+    __syncthreads();
+}
+
+// p^T H p of the contact and friction terms at u along p, and the CCD bound
+// min_k eta d_k / max_slot |p|. The mixed form takes each pair's float64
+// feature from what the accepted trial at this point left (pair_cache_fill
+// after a rebuild); it stores the barrier values the next trial's remainders
+// subtract from.
 template <typename R>
 __device__ __noinline__ void pair_php(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np, int nl,
                                       double s, double& php, double& accd) {
@@ -1125,52 +1192,52 @@ __device__ __noinline__ void pair_php(const Dev& D, const PadDev& P, const MeshD
     const int4* pr = D.pairs + P.pair_off;
     double* bcur = D.bpair + P.pair_off;
     const Feature<double>* fc = D.fcache + P.pair_off;
-    const bool cached = S.fok != 0;
+    if (kMixed && S.fok == 0) pair_cache_fill(D, P, M, E, np, s);
     const R dh = P.dhat, kap = P.kappa;
     for (int k = threadIdx.x; k < np; k += kThreads) {
         int gsl[4], isl[4];
         int4 q = pr[k];
         pair_slots(D, M, E, q, gsl, isl);
         float pk = 0.f;
-        V3<R> dl[4];
+        V3<float> dl[4];
 #pragma unroll
         for (int sl = 0; sl < 4; ++sl) {
             if (gsl[sl] >= 0) {
                 int si = P.v_off + gsl[sl];
                 float a = D.p[si], b = D.p[D.Vt + si], c = D.p[2 * D.Vt + si];
                 pk = fmaxf(pk, sqrtf(a * a + b * b + c * c));
-                dl[sl] = {R(a), R(b), R(c)};
+                dl[sl] = {a, b, c};
             } else {
-                dl[sl] = {R(0), R(0), R(0)};
+                dl[sl] = {0.f, 0.f, 0.f};
             }
         }
-        V3<float> Xf[4];
-        load_slots<float>(D, P, M, gsl, isl, 0.0f, s, Xf);
-        float df = pair_feature<float>(q.x, Xf).d;
         R d;
         double bv = 0.0;
-        if (kMixed && (double)df > kNearBand * (double)dh) {
-            d = R((double)df * (1.0 - 1e-5));
-        } else {
-            V3<R> X[4];
-            Feature<R> f;
-            if constexpr (kMixed) {
+        if constexpr (kMixed) {
+            d = fc[k].d;
+            if (fc[k].nf >= 0 && d < dh) {
+                V3<double> X[4], dd[4];
                 load_slots<double>(D, P, M, gsl, isl, 0.0f, s, X);
-                if (cached && fc[k].nf >= 0)
-                    f = fc[k];              // computed by the accepted trial at this point
-                else
-                    f = pair_feature<double>(q.x, X);
-            } else {
 #pragma unroll
-                for (int sl = 0; sl < 4; ++sl) X[sl] = Xf[sl];
-                f = pair_feature<float>(q.x, X);
+                for (int sl = 0; sl < 4; ++sl) dd[sl] = {(double)dl[sl].x, (double)dl[sl].y, (double)dl[sl].z};
+                const Feature<double> f = fc[k];
+                double d1, d2;
+                feat_dir_derivs(f, X, dd, d1, d2);
+                const Barrier3 bb = barrier_all(d, (double)dh);
+                const EdgeMoll em = edge_moll(X, ee_eps(D, M, E, q.x, gsl, isl));
+                acc += kap * moll_barrier_dir2(em, dd, d1, d2, bb);
+                bv = em.m * bb.b;
             }
+        } else {
+            V3<float> Xf[4];
+            load_slots<float>(D, P, M, gsl, isl, 0.0f, s, Xf);
+            Feature<float> f = pair_feature<float>(q.x, Xf);
             d = f.d;
             if (d < dh) {
-                R d1, d2;
-                feat_dir_derivs(f, X, dl, d1, d2);
-                const Barrier3T<R> bb = barrier_all(d, dh);
-                const EdgeMollT<R> em = edge_moll(X, R(ee_eps(D, M, E, q.x, gsl, isl)));
+                float d1, d2;
+                feat_dir_derivs(f, Xf, dl, d1, d2);
+                const Barrier3T<float> bb = barrier_all(d, dh);
+                const EdgeMollT<float> em = edge_moll(Xf, (float)ee_eps(D, M, E, q.x, gsl, isl));
                 acc += kap * moll_barrier_dir2(em, dl, d1, d2, bb);
                 bv = (double)(em.m * bb.b);
             }
@@ -1226,10 +1293,11 @@ __device__ __noinline__ void pair_php(const Dev& D, const PadDev& P, const MeshD
 // the current point itself (remainder 0) and needs no stored value.
 template <typename R>
 __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np, int nl, double s,
-                           float alpha, double& rem, int& bad) {
+                           float alpha, double& rem, int& bad, float& fsc) {
     constexpr bool kMixed = sizeof(R) == 8;   // float64 features; else the plain-FP32 form
     R acc = R(0);
     int badl = 0;
+    float fm = 0.f;   // largest slot force component written (float32 resolution scale)
     const int4* pr = D.pairs + P.pair_off;
     const double* bcur = D.bpair + P.pair_off;
     Feature<double>* fc = D.fcache + P.pair_off;
@@ -1242,7 +1310,12 @@ __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const Mes
         pair_slots(D, M, E, q, gsl, isl);
         V3<float> Xf[4];
         load_slots<float>(D, P, M, gsl, isl, alpha, s, Xf);
-        float d1f = pair_feature<float>(q.x, Xf).d;
+        int mask = 31;
+        float d1f;
+        if constexpr (kMixed)
+            d1f = pair_pick(q.x, Xf, mask);
+        else
+            d1f = pair_feature<float>(q.x, Xf).d;
         const R b0 = trial ? R(bcur[k]) : R(0);
         float out[3][9];
 #pragma unroll
@@ -1252,12 +1325,13 @@ __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const Mes
         if (kMixed && (double)d1f > kNearBand * (double)dh) {
             acc += kap * b0;                    // b = 0 at the trial point
             fc[k].nf = -1;
+            fc[k].d = (double)d1f * (1.0 - 1e-5);
         } else {
             V3<R> X1[4];
             Feature<R> f1;
             if constexpr (kMixed) {
                 load_slots<double>(D, P, M, gsl, isl, alpha, s, X1);
-                f1 = pair_feature<double>(q.x, X1);
+                f1 = pair_feature<double>(q.x, X1, mask);
                 fc[k] = f1;
             } else {
 #pragma unroll
@@ -1275,8 +1349,9 @@ __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const Mes
                 const Barrier3T<R> bb = barrier_all(f1.d, dh);
                 const EdgeMollT<R> em = edge_moll(X1, R(ee_eps(D, M, E, q.x, gsl, isl)));
                 // gradient of m(c) b(d): m b' w_s r^ + m' b dc/dX_s; Gauss-Newton
-                // block m b'' w_s^2 r^ r^T
+                // block m b'' w_s^2 r^ r^T (a preconditioner entry: float32)
                 R b1 = kap * em.m * bb.b1, b2 = kap * em.m * bb.b2, cb = kap * em.m1 * bb.b;
+                const float rx = (float)rh.x, ry = (float)rh.y, rz = (float)rh.z;
                 R gdp = R(0);
 #pragma unroll
                 for (int sl = 0; sl < 3; ++sl)
@@ -1286,16 +1361,17 @@ __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const Mes
                         V3<R> gs = (b1 * f1.w[sl]) * rh;
                         if (em.on) gs = gs + cb * edge_moll_grad(em, sl);
                         gdp += dot(gs, pv);
-                        R kw = b2 * f1.w[sl] * f1.w[sl];
+                        const float kw = (float)(b2 * f1.w[sl] * f1.w[sl]);
                         out[sl][0] = (float)gs.x;
                         out[sl][1] = (float)gs.y;
                         out[sl][2] = (float)gs.z;
-                        out[sl][3] = (float)(kw * rh.x * rh.x);
-                        out[sl][4] = (float)(kw * rh.y * rh.y);
-                        out[sl][5] = (float)(kw * rh.z * rh.z);
-                        out[sl][6] = (float)(kw * rh.x * rh.y);
-                        out[sl][7] = (float)(kw * rh.x * rh.z);
-                        out[sl][8] = (float)(kw * rh.y * rh.z);
+                        fm = fmaxf(fm, fmaxf(fabsf(out[sl][0]), fmaxf(fabsf(out[sl][1]), fabsf(out[sl][2]))));
+                        out[sl][3] = kw * rx * rx;
+                        out[sl][4] = kw * ry * ry;
+                        out[sl][5] = kw * rz * rz;
+                        out[sl][6] = kw * rx * ry;
+                        out[sl][7] = kw * rx * rz;
+                        out[sl][8] = kw * ry * rz;
                     }
                 if (trial) acc += kap * b0 - kap * em.m * bb.b + (R)alpha * gdp;
             }
@@ -1355,6 +1431,7 @@ __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const Mes
                 e[0] = (float)(gw * t1[0]);
                 e[1] = (float)(gw * t1[1]);
                 e[2] = (float)(gw * t1[2]);
+                fm = fmaxf(fm, fmaxf(fabsf(e[0]), fmaxf(fabsf(e[1]), fabsf(e[2]))));
                 for (int c = 0; c < 6; ++c) e[3 + c] = (float)(kw * Hn[c]);
             }
     }
@@ -1364,6 +1441,9 @@ __device__ __noinline__ void pair_trial(const Dev& D, const PadDev& P, const Mes
     R v[1] = {acc};
     block_sum_r<R, 1>(v);
     rem = (double)v[0];
+    float fmv[1] = {fm};
+    block_max_f<1>(fmv);
+    fsc = fmv[0];
     if (badl) S.flag = 1;
     __syncthreads();
     bad = S.flag;
@@ -1781,11 +1861,11 @@ __device__ __forceinline__ void pair_php_p(const Dev& D, const PadDev& P, const 
         pair_php<double>(D, P, M, E, np, nl, s, php, accd);
 }
 __device__ __forceinline__ void pair_trial_p(const Dev& D, const PadDev& P, const MeshDev& M, const EnvDev& E, int np,
-                                             int nl, double s, float alpha, double& rem, int& bad) {
+                                             int nl, double s, float alpha, double& rem, int& bad, float& fsc) {
     if (P.prec)
-        pair_trial<float>(D, P, M, E, np, nl, s, alpha, rem, bad);
+        pair_trial<float>(D, P, M, E, np, nl, s, alpha, rem, bad, fsc);
     else
-        pair_trial<double>(D, P, M, E, np, nl, s, alpha, rem, bad);
+        pair_trial<double>(D, P, M, E, np, nl, s, alpha, rem, bad, fsc);
 }
 __device__ __forceinline__ void pair_advance_bound_p(const Dev& D, const PadDev& P, const MeshDev& M,
                                                      const EnvDev& E, int np, double s, double bm[2]) {
@@ -1908,7 +1988,9 @@ __device__ void solve_pad(const Dev& D, int pad) {
     clk.lap(PH_SETUP);
     float g_ref = P.g_ref;   // becomes max(floor, |g| after the first substep)
     bool have_ref = false;
-    float fmax = 0.f;        // force scale of the float32 resolution floor
+    float fmax = 0.f;        // force scale of the float32 resolution floor: the largest force
+                             // component summed into the float32 gradient (elastic corner,
+                             // barrier and friction slot forces)
     float target = 0.f;
     int gc = 0;              // buffer holding the current gradient
     float ginf = 0.f;
@@ -1953,6 +2035,7 @@ __device__ void solve_pad(const Dev& D, int pad) {
         double s1 = s;
         TetOut to{};
         Dots d0{};
+        float fsc0 = 0.f;
         for (int hv = 0; hv <= kMaxHalvings; ++hv) {
             s1 = (ds >= 1.0 - s) ? 1.0 : s + ds;
             const float ag = am * (float)ds;
@@ -1961,7 +2044,7 @@ __device__ void solve_pad(const Dev& D, int pad) {
             clk.lap(PH_TET1);
             double rem0;
             int badp;
-            pair_trial_p(D, P, M, E, cc.npairs, cc.nlag, s1, ag, rem0, badp);
+            pair_trial_p(D, P, M, E, cc.npairs, cc.nlag, s1, ag, rem0, badp, fsc0);
             ctr.pair_evals += cc.npairs;
             contact_gather(D, P, cc, gn);
             clk.lap(PH_PAIR_TRIAL);
@@ -1984,7 +2067,7 @@ __device__ void solve_pad(const Dev& D, int pad) {
         Mb += ds * B;
         ctr.substeps++;
         ginf = d0.ginf;
-        fmax = to.fmax;
+        fmax = fmaxf(to.fmax, fsc0);
         if (!have_ref) {
             g_ref = fmaxf(g_ref, ginf);
             have_ref = true;
@@ -2038,7 +2121,8 @@ __device__ void solve_pad(const Dev& D, int pad) {
                 clk.lap(PH_TET1);
                 double remc;
                 int bp;
-                pair_trial_p(D, P, M, E, cc.npairs, cc.nlag, s, af, remc, bp);
+                float fsc;
+                pair_trial_p(D, P, M, E, cc.npairs, cc.nlag, s, af, remc, bp, fsc);
                 ctr.pair_evals += cc.npairs;
                 contact_gather(D, P, cc, gt);
                 clk.lap(PH_PAIR_TRIAL);
@@ -2053,7 +2137,7 @@ __device__ void solve_pad(const Dev& D, int pad) {
                     if (literal || dE <= kArmijoC * a * dir.gTp) {
                         accepted = true;
                         alpha = a;
-                        fmax = tt.fmax;
+                        fmax = fmaxf(tt.fmax, fsc);
                         break;
                     }
                 }
@@ -2065,6 +2149,7 @@ __device__ void solve_pad(const Dev& D, int pad) {
                 // before the line search counts as failed
                 if (!retried && !literal) {
                     retried = true;
+                    if (tid == 0) S.fok = 0;   // the cached features are the last rejected trial's
                     dir = steepest_direction(D, P, M, gc);
                     ctr.vert_passes++;
                     continue;
@@ -2124,7 +2209,7 @@ __device__ void solve_pad(const Dev& D, int pad) {
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads, 2) solve_kernel(const __grid_constant__ Dev D) {
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) solve_kernel(const __grid_constant__ Dev D) {
     if (threadIdx.x == 0) S.flag = 0;
     for (;;) {
         if (threadIdx.x == 0) S.pad = atomicAdd(D.queue, 1);
@@ -2136,6 +2221,7 @@ __global__ void __launch_bounds__(kThreads, 2) solve_kernel(const __grid_constan
     }
 }
 
+#ifndef TAC_WIDE
 // ---------------------------------------------------------------------------
 // processing order of the next solve launch: longest predicted pad first.
 // The prediction is the pad's solve time in its previous frame (0 before its
@@ -2234,7 +2320,8 @@ __global__ void __launch_bounds__(kThreads) debug_eval_kernel(const __grid_const
     TetOut tt = tet_pass<1>(D, P, M, alpha, 0);
     double remc;
     int bp;
-    pair_trial_p(D, P, M, E, cc.npairs, 0, 1.0, alpha, remc, bp);
+    float fsc;
+    pair_trial_p(D, P, M, E, cc.npairs, 0, 1.0, alpha, remc, bp, fsc);
     contact_gather(D, P, cc, 0);
     // outputs before inertia / inversion: gradient with inertia m alpha p
     double gp[1] = {0.0};
@@ -2860,7 +2947,8 @@ __global__ void __launch_bounds__(kThreads, 2) adjoint_kernel(const __grid_const
     TetOut t0 = tet_pass<1>(D, P, M, 0.0f, 0);
     double rem;
     int bad;
-    pair_trial<double>(D, P, M, E, cc.npairs, cc.nlag, 1.0, 0.0f, rem, bad);
+    float fsc;
+    pair_trial<double>(D, P, M, E, cc.npairs, cc.nlag, 1.0, 0.0f, rem, bad, fsc);
     contact_gather(D, P, cc, 0);
     // right-hand side dL/dx (transpose of the marker readout), lambda = 0
     for (int i = threadIdx.x; i < M.n_v; i += kThreads)
@@ -2995,11 +3083,20 @@ __global__ void __launch_bounds__(kThreads) broadphase_static_kernel2(const __gr
     if (threadIdx.x == 0) *count = n;
 }
 
+#endif  // TAC_WIDE
+
 // ---------------------------------------------------------------------------
 // host side: dynamic shared memory of the kernels that use the CTA scratch
 
 size_t shared_bytes() { return sizeof(Shared); }
 
+#ifdef TAC_WIDE
+cudaError_t configure_kernels() {
+    return cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Shared));
+}
+}  // namespace wide
+}  // namespace tac
+#else
 cudaError_t configure_kernels() {
     int bytes = (int)sizeof(Shared);
     cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -3105,3 +3202,4 @@ extern "C" int tac_broadphase_static(const float* x_dev, const int* surf_verts_d
     if (e != cudaSuccess) return static_fail(TAC_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
     return TAC_OK;
 }
+#endif  // TAC_WIDE

@@ -107,6 +107,7 @@ struct Dev {
     float* slotbuf;           // [6 * pair_cap][9] per pad region (pairs then lag, 3 slots each)
     double* bpair;            // [pair_cap] per pad: barrier value b(d) of each pair at the current point
     Feature<double>* fcache;  // [pair_cap] per pad: float64 feature of each pair at the last trial point
+                              // (nf = -1: farther than the float64 band, d its float32 bound)
     int* ent;                 // [6 * pair_cap]
     int* cvl;                 // [6 * pair_cap + 1] contact vertex list / offsets
     int* cvo;                 // [6 * pair_cap + 1]

@@ -23,7 +23,8 @@ SYMBOLS = ("tac_create_batch", "tac_destroy_batch", "tac_reset", "tac_set_indent
            "tac_get_state", "tac_set_state", "tac_set_params", "tac_get_params", "tac_broadphase",
            "tac_broadphase_static",
            "tac_debug_eval", "tac_stats",
-           "tac_pad_norms", "tac_sizes", "tac_marker_map", "tac_mesh_info", "tac_last_error")
+           "tac_pad_norms", "tac_sizes", "tac_marker_map", "tac_mesh_info", "tac_last_error",
+           "tac_set_block_shape", "tac_autotune_block_shape")
 
 
 class PadDesc(ctypes.Structure):
@@ -76,6 +77,8 @@ def load_library(path=_LIB_PATH):
         "tac_stats": [vp, vp, vp],
         "tac_pad_norms": [vp, vp, vp],
         "tac_sizes": [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)],
+        "tac_set_block_shape": [vp, i],
+        "tac_autotune_block_shape": [vp, vp, i, ctypes.POINTER(i), vp, vp],
         "tac_marker_map": [ctypes.POINTER(PadDesc), i, vp, vp],
         "tac_mesh_info": [ctypes.POINTER(PadDesc), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                           ctypes.POINTER(d), ctypes.POINTER(i), ctypes.POINTER(i)],
@@ -256,6 +259,26 @@ class TacBatch:
         iters = iters if iters is not None else torch.empty(self.n_pads, dtype=torch.int32, device=self.device)
         _check(lib().tac_step(self._h, _ptr(status), _ptr(iters), _stream(stream)))
         return status, iters
+
+    def set_block_shape(self, threads):
+        """tac_set_block_shape: 256 or 512 threads per pad's CTA."""
+        _check(lib().tac_set_block_shape(self._h, int(threads)))
+        self._sync_grid()
+
+    def autotune_block_shape(self, poses, reps=1, stream=None):
+        """tac_autotune_block_shape toward the next frame's poses: returns
+        (chosen threads, [mean ms of the 256- and 512-thread solves])."""
+        p = self._f32(poses).reshape(self.n_pads, 6)
+        th = ctypes.c_int()
+        ms = (ctypes.c_float * 2)()
+        _check(lib().tac_autotune_block_shape(self._h, _ptr(p), int(reps), ctypes.byref(th), ms, _stream(stream)))
+        self._sync_grid()
+        return th.value, [float(ms[0]), float(ms[1])]
+
+    def _sync_grid(self):
+        gr = ctypes.c_int()
+        _check(lib().tac_sizes(self._h, None, None, None, ctypes.byref(gr)))
+        self.grid_ctas = gr.value
 
     def markers(self, out=None, stream=None):
         out = out if out is not None else torch.empty(self.total_markers, 2, dtype=torch.float32, device=self.device)

@@ -88,3 +88,6 @@ def test_null_arguments_are_rejected(lib):
     assert lib.tac_markers(None, None, None) == -1
     h = ctypes.c_void_p()
     assert lib.tac_create_batch(None, None, 0, None, 0, 0, None, None, ctypes.byref(h)) == -1
+    assert lib.tac_set_block_shape(None, 256) == -1
+    th = ctypes.c_int()
+    assert lib.tac_autotune_block_shape(None, None, 1, ctypes.byref(th), None, None) == -1

@@ -109,3 +109,48 @@ def test_adjoint_gradient_lowers_the_target_misfit(setup):
     b.close()
     print(f"misfit {L0:.4e} -> {L1:.4e} after a 1e-3 relative step against the adjoint gradient")
     assert L1 < L0
+
+
+GRAD = os.path.join(os.path.dirname(__file__), "golden", "calibration_gradient.npz")
+
+
+def test_sequence_adjoint_matches_oracle_central_differences(setup):
+    """dL/d(E, nu, mu_f) of the first environment's 16-frame misfit against
+    its oracle targets, at the nominal material: the GPU's relagged sequence
+    adjoint (each frame's friction lag differentiated, the total derivative
+    of the run) against the oracle's central differences in
+    tests/golden/calibration_gradient.npz (written by
+    tests/golden/make_calibration_gradient.py, which calls only oracle/),
+    within 1e-3 relative. The forward frames solve to the same 1e-6 relative
+    gradient with a 32-ulp float32 floor."""
+    from paper_2603_28475_b300 import autograd as A
+    T, g, w, hidden = setup
+    gd = np.load(GRAD)
+    w0 = S.Workload("calibration_env0", w.pads[:1], w.materials[:1], w.indenters[:1], 1, w.poses[:, :1])
+    prm = [T.make_params(w0.materials[0], kappa=float(g["kappa"][0]), eps_v=float(g["eps_v"][0]), floor_ulps=32.0)]
+    b = T.TacBatch(w0.pads, prm, w0.indenters, pads_per_env=1)
+    poses = torch.tensor(w0.poses.astype(np.float64), device=b.device)
+    target = torch.tensor(g["markers"][0], dtype=torch.float32, device=b.device)      # [frame, m, 2]
+    b.reset(poses[0].float())
+    x0, v0 = b.get_state()
+    q = b.get_params()[0]
+    E, nu = float(q.E), float(q.nu)
+    assert np.allclose([E, nu, float(q.mu_f)], gd["theta0"], rtol=1e-7, atol=0)
+    den = (1 + nu) * (1 - 2 * nu)
+    lame = torch.tensor([[E * nu / den, E / (2 * (1 + nu))]], dtype=torch.float64, requires_grad=True)
+    muf = torch.tensor([float(q.mu_f)], dtype=torch.float64, requires_grad=True)
+    m = A.sequence_markers(b, x0, v0, lame, muf, poses, base_params=b.get_params(), adjoint_tol=1e-8, relag=True)
+    loss = ((m.double() - target.double()) ** 2).sum()
+    loss.backward()
+    b.close()
+    dl, dm = lame.grad.numpy()[0]
+    # chain rule from (lambda, mu) to (E, nu)
+    dE = dl * nu / den + dm / (2 * (1 + nu))
+    dnu = dl * E * (1 + 2 * nu * nu) / den ** 2 - dm * E / (2 * (1 + nu) ** 2)
+    got = np.array([dE, dnu, float(muf.grad.numpy()[0])])
+    fd = gd["fd"][:, -1]
+    rel = np.abs(got - fd) / np.abs(fd)
+    print(f"misfit GPU {float(loss.item()):.6e} / oracle {float(gd['L0']):.6e}; dL/d(E, nu, mu_f) GPU {got} "
+          f"oracle FD {fd}; relative errors {rel}")
+    assert float(loss.item()) == pytest.approx(float(gd["L0"]), rel=5e-2)
+    assert np.all(rel <= 1e-3), rel
