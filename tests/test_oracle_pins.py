@@ -1,6 +1,7 @@
-"""Pins of two oracle functions that the GPU is compared against directly:
-the conservative step bound alpha_ccd of the per-pair CCD (its defining
-property, and exactness where the closing speed is known) and the
+"""Pins of oracle functions that the GPU is compared against directly:
+the conservative step bound alpha_ccd of the per-pair CCD and the coupled
+indenter-gel advance bound (their defining property, and exactness where
+the closing speed is known) and the
 candidate predicate of the set C of Eq. (ipc_energy) at its exact boundary
 (inflated-AABB gaps of r and r + one float32 ulp, decided against exact
 rational arithmetic)."""
@@ -87,6 +88,88 @@ def test_ccd_bound_is_tight_for_a_rigid_approach():
     a = SV.ccd_bound(fr, x, p, 0.0, pairs, ETA)
     assert a == pytest.approx(ETA * d0.min() / c, rel=1e-12)
     d1, _, _ = En.distances(pairs, x + a * p, y, pad, ind)
+    k = int(np.argmin(d0))
+    assert d1[k] == pytest.approx((1.0 - ETA) * d0[k], rel=1e-6)
+    assert np.all(d1 >= (1.0 - ETA) * d0 * (1.0 - 1e-9))
+
+
+# ---------------------------------------------------------------------------
+# the coupled indenter-gel advance bound (R11)
+
+
+def _moving_frame(seed):
+    """The near-contact frame with the indenter moving over the frame on its
+    per-vertex straight path: a small rotation and a translation down and
+    sideways, so dy differs per vertex."""
+    fr, x, y, pairs = _frame_near_contact(seed)
+    rng = np.random.default_rng(200 + seed)
+    ind = fr.ind
+    c = y.mean(axis=0)
+    ang = rng.uniform(-0.05, 0.05, 3)
+    th = np.linalg.norm(ang)
+    k = ang / th
+    K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    R = np.eye(3) + np.sin(th) * K + (1 - np.cos(th)) * K @ K
+    y_n = (y - c) @ R.T + c + np.array([0.3, -0.2, -1.5]) * DH
+    fr2 = En.Frame(fr.pad, ind, x, x.copy(), y, y_n, fr.lag)
+    return fr2, x, y, y_n, pairs
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_advance_bound_keeps_every_candidate_gap(seed):
+    """For every advance sigma in (0, ds], ds the bound of the coupled
+    advance at path parameter s (gel along w, indenter on its straight
+    per-vertex path), every candidate keeps
+    d_k(x + sigma w, y(s + sigma)) >= (1 - eta) d_k(x, y(s)): the property
+    the substep bound exists for. Random gel motions, some pushing the gel
+    up into the indenter, and the gel held (w = 0)."""
+    fr, x, y_t, y_n, pairs = _moving_frame(seed)
+    dy = y_n - y_t
+    s = 0.3
+    d0, _, _ = En.distances(pairs, x, fr.y(s), fr.pad, fr.ind)
+    assert len(pairs) > 0 and d0.min() > 0
+    rng = np.random.default_rng(300 + seed)
+    for trial in range(5):
+        w = rng.normal(size=x.shape) * 0.5 * DH
+        if trial % 2:
+            w[:, 2] = np.abs(w[:, 2]) * 2.0
+        if trial == 4:
+            w[:] = 0.0
+        ds = SV.advance_bound(fr, x, s, pairs, w, dy, ETA)
+        assert np.isfinite(ds) and ds > 0
+        for sg in np.linspace(0.0, ds, 17)[1:]:
+            d, _, _ = En.distances(pairs, x + sg * w, y_t + (s + sg) * dy, fr.pad, fr.ind)
+            assert np.all(d >= (1.0 - ETA) * d0 * (1.0 - 1e-9)), (trial, sg / ds)
+
+
+def test_advance_bound_is_tight_for_opposed_translations():
+    """The gel translating up at speed a and the indenter straight down at
+    speed b: every primitive pair closes at most at a + b, the pairs under
+    the indenter's face exactly so. The bound must be eta d_min / (a + b),
+    and there the closest pair has exactly (1 - eta) of its gap left (a
+    bound that drops one side's motion, or adds them with the wrong sign,
+    fails)."""
+    pad_pd, pad = tiny_pad(cells=(3, 3, 1), size=(3 * MM, 3 * MM, 1 * MM))
+    ztop = pad.rest[:, 2].max()
+    gap = 0.4 * DH
+    cx, cy = 1.5 * MM, 1.5 * MM
+    yv = np.array([[cx - 1.2 * MM, cy - 1.2 * MM, ztop + gap], [cx + 1.3 * MM, cy - 1.1 * MM, ztop + gap],
+                   [cx, cy + 1.4 * MM, ztop + gap]])
+    ind = G.build_indenter(yv.astype(np.float32), np.array([[0, 2, 1]], np.int32))
+    y_t = ind.verts.astype(np.float64)
+    a_up, b_down = 1.0e-5, 2.5e-5
+    y_n = y_t - np.array([0.0, 0.0, b_down])
+    x = pad.rest.astype(np.float64)
+    lag = En.friction_lag(np.zeros((0, 3), np.int64), x, y_t, pad, ind)
+    fr = En.Frame(pad, ind, x, x.copy(), y_t, y_n, lag)
+    pairs = BP.candidates(x, y_t, pad, ind, 2 * DH)
+    d0, _, _ = En.distances(pairs, x, y_t, pad, ind)
+    w = np.zeros_like(x)
+    w[:, 2] = a_up
+    dy = y_n - y_t
+    ds = SV.advance_bound(fr, x, 0.0, pairs, w, dy, ETA)
+    assert ds == pytest.approx(ETA * d0.min() / (a_up + b_down), rel=1e-12)
+    d1, _, _ = En.distances(pairs, x + ds * w, y_t + ds * dy, pad, ind)
     k = int(np.argmin(d0))
     assert d1[k] == pytest.approx((1.0 - ETA) * d0[k], rel=1e-6)
     assert np.all(d1 >= (1.0 - ETA) * d0 * (1.0 - 1e-9))
