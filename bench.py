@@ -93,6 +93,9 @@ def parse():
                          "(tests/golden/calibration_targets.npz) instead")
     ap.add_argument("--variants", action="store_true",
                     help="iterations and throughput of the paper-literal variants on the batched workload instead")
+    ap.add_argument("--sweep-points", default="",
+                    help="with --sweep: the points to run, as envs x pad vertices, e.g. 64x50000,1024x2000 "
+                         "(default: all of SWEEP_POINTS)")
     ap.add_argument("--block-shape", default="auto", choices=["auto", "256", "512"],
                     help="threads per pad's CTA in the solve launch: the library's autotuner on the first timed "
                          "frame (auto, before the timed region) or a fixed shape")
@@ -729,7 +732,10 @@ def run_sweep(args):
     W, K = 2, 2
     peak, peak_kind = load_peaks()
     pts = []
-    for envs, nv in SWEEP_POINTS:
+    points = SWEEP_POINTS
+    if args.sweep_points:
+        points = tuple(tuple(int(v) for v in q.split("x")) for q in args.sweep_points.split(","))
+    for envs, nv in points:
         w = S.config_sweep(envs, nv, frames=W + K, seed=args.seed)
         cap = max(args.pair_capacity, int(args.pair_capacity * 1.5 * (nv / 10000.0) ** (2.0 / 3.0)))
         b = tac.batch_from_workload(w, pair_capacity=cap)
