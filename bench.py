@@ -718,6 +718,14 @@ SWEEP_POINTS = ((64, 2000), (256, 2000), (1024, 2000), (1024, 10000), (64, 50000
                 (1024, 50000))
 
 
+def sweep_points(args):
+    """The sweep's (envs, pad vertices) points: --sweep-points "64x50000,..."
+    or all of SWEEP_POINTS."""
+    if not args.sweep_points:
+        return SWEEP_POINTS
+    return tuple(tuple(int(v) for v in q.split("x")) for q in args.sweep_points.split(","))
+
+
 def run_sweep(args):
     """Throughput over environment counts and pad sizes: one pad of ~V
     vertices per env, a cylinder press with friction 0.5 (scenes.config_sweep).
@@ -732,10 +740,7 @@ def run_sweep(args):
     W, K = 2, 2
     peak, peak_kind = load_peaks()
     pts = []
-    points = SWEEP_POINTS
-    if args.sweep_points:
-        points = tuple(tuple(int(v) for v in q.split("x")) for q in args.sweep_points.split(","))
-    for envs, nv in points:
+    for envs, nv in sweep_points(args):
         w = S.config_sweep(envs, nv, frames=W + K, seed=args.seed)
         cap = max(args.pair_capacity, int(args.pair_capacity * 1.5 * (nv / 10000.0) ** (2.0 / 3.0)))
         b = tac.batch_from_workload(w, pair_capacity=cap)
