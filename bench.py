@@ -93,6 +93,9 @@ def parse():
                          "(tests/golden/calibration_targets.npz) instead")
     ap.add_argument("--variants", action="store_true",
                     help="iterations and throughput of the paper-literal variants on the batched workload instead")
+    ap.add_argument("--shard", action="store_true",
+                    help="strong scaling: the --envs environments partitioned over the ranks (balanced by tets) "
+                         "with a per-frame all-gather of the marker fields, instead of one workload per rank")
     ap.add_argument("--sweep-points", default="",
                     help="with --sweep: the points to run, as envs x pad vertices, e.g. 64x50000,1024x2000 "
                          "(default: all of SWEEP_POINTS)")
@@ -642,6 +645,106 @@ def run_ours(args, rank, world):
     b.close()
 
 
+def shard_workload(w, env_ids):
+    """The environments env_ids (ascending) of workload w as a workload of
+    their own: their pads, materials, indenters and poses."""
+    from paper_2603_28475_b300 import scenes as S
+    ppe = w.pads_per_env
+    pads = [ppe * int(e) + q for e in env_ids for q in range(ppe)]
+    return S.Workload(f"{w.name}_shard", [w.pads[k] for k in pads], [w.materials[k] for k in pads],
+                      [w.indenters[int(e)] for e in env_ids], ppe, w.poses[:, pads])
+
+
+def run_sharded(args, rank, world, make_batch=None, device=None):
+    """The job's environments partitioned across the ranks (strong
+    scaling). Every rank builds the same workload, takes its share of
+    partition.balanced_partition (cost: the tets of each env's pads),
+    solves that share with a batch of its own, and every frame all-gathers
+    the marker fields of all environments (partition.gather_markers): the
+    per-frame exchange of the paper's per-GPU simulation actors. W warm-up
+    frames, then K timed frames between barriers; the time is the slowest
+    rank's (CUDA events on the rank's stream, or the host clock for a batch
+    on the host). Rank 0 prints one JSON line; every rank returns the
+    gathered field of the last frame [envs, markers per env, 2]."""
+    import torch
+    import torch.distributed as dist
+    from paper_2603_28475_b300 import partition as PT
+    if device is None:
+        device = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+        torch.cuda.set_device(device)
+    if make_batch is None:
+        from paper_2603_28475_b300 import tac
+
+        def make_batch(ws):
+            return tac.batch_from_workload(ws, pair_capacity=args.pair_capacity, dm_table=not args.no_dm_table)
+    frames = args.warmup + args.steps
+    w = workload(args.envs, frames + 1, args.seed)          # the job's workload, the same on every rank
+    costs = PT.env_costs([p.n_tets for p in w.pads], w.pads_per_env)
+    parts = PT.balanced_partition(costs, world)
+    mine = parts[rank]
+    n_mk = {int(np.asarray(p.markers).shape[0]) for p in w.pads}
+    if len(n_mk) != 1:
+        raise ValueError("the marker gather needs one marker count per pad")
+    per_env = w.pads_per_env * n_mk.pop()
+    ws = shard_workload(w, mine)
+    b = make_batch(ws)
+    poses = torch.tensor(ws.poses, dtype=torch.float32, device=device)
+    st = torch.empty(ws.n_pads, dtype=torch.int32, device=device)
+    it = torch.empty(ws.n_pads, dtype=torch.int32, device=device)
+    on_gpu = device.type == "cuda"
+
+    def frame(f):
+        b.set_indenter(poses[f])
+        b.step(st, it)
+        mk = b.markers().reshape(len(mine), per_env, 2)
+        full = PT.gather_markers(mk, mine, w.n_envs)
+        conv = int((st.reshape(-1, w.pads_per_env) == 0).all(dim=1).sum().item())
+        return full, conv
+
+    b.reset(poses[0])
+    for f in range(1, args.warmup + 1):
+        frame(f)
+    dist.barrier()
+    if on_gpu:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+    t0 = time.perf_counter()
+    conv = 0
+    full = None
+    for f in range(args.warmup + 1, frames + 1):
+        full, c = frame(f)
+        conv += c
+    if on_gpu:
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    else:
+        ms = (time.perf_counter() - t0) * 1e3
+    dist.barrier()
+    t = torch.tensor([ms, float(conv)], dtype=torch.float64, device=device)
+    mx, tot = t.clone(), t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    if rank == 0:
+        loads = PT.rank_loads(costs, parts)
+        out = {"metric": METRIC, "value": float(tot[1]) / (float(mx[0]) / 1e3), "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(mx[0]) / args.steps,
+               "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+               "dtype": "f32 (double-float displacements; f64 pair distance, barrier, CCD and reductions)",
+               "data": "synthetic",
+               "config": {"workload": w.name, "envs": w.n_envs, "pads": w.n_pads,
+                          "parallelism": f"the {w.n_envs} envs partitioned over {world} ranks "
+                                         "(balanced by tets), marker fields all-gathered every frame"},
+               "partition": {"envs_per_rank": [int(len(p)) for p in parts],
+                             "tets_per_rank": [float(v) for v in loads],
+                             "imbalance": float(loads.max() / loads.mean())},
+               "gather_bytes_per_frame": int(w.n_envs * per_env * 2 * 4),
+               "converged_fraction": float(tot[1]) / (args.steps * w.n_envs)}
+        print(json.dumps(out), flush=True)
+    return full
+
+
 def run_adjoint(args):
     """Calibration workload (256 envs x one 5k-class pad, 16-frame
     press-and-slide): targets are the marker fields at hidden per-env
@@ -1064,6 +1167,14 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.shard:
+        import torch
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29511")
+        torch.distributed.init_process_group("nccl", world_size=world, rank=rank)
+        run_sharded(args, rank, world)
+        torch.distributed.destroy_process_group()
         return
     if world > 1:
         import torch

@@ -1,10 +1,13 @@
-"""The multi-rank bench path on the CPU (world size 2, gloo; no GPU).
+"""The multi-rank bench paths on the CPU (world size 2, gloo; no GPU).
 
-Environments shard across ranks with no data-path exchange: each rank
-builds its own workload from its own seed, and only the timed region's
-totals are reduced: the slowest rank's time and the sum of converged envs.
-The reference arm runs on rank 0 alone.
+Weak scaling: environments shard across ranks with no data-path exchange;
+each rank builds its own workload from its own seed, and only the timed
+region's totals are reduced: the slowest rank's time and the sum of
+converged envs. The reference arm runs on rank 0 alone. Strong scaling
+(--shard): one job's environments partitioned across the ranks and their
+marker fields all-gathered every frame.
 """
+import json
 import os
 import socket
 
@@ -122,3 +125,63 @@ def test_marker_gather_reassembles_the_global_field():
         ok, counts = res[r]
         assert ok
         assert sum(counts) == 11 and counts[0] != counts[1]
+
+
+class _FakeShardBatch:
+    """Stands in for a rank's TacBatch on the host: every pad converges and
+    its markers all read the (x, y) translation of its current pose, so the
+    gathered field says which environment each entry came from."""
+
+    def __init__(self, ws):
+        self.ws = ws
+        self.m = int(np.asarray(ws.pads[0].markers).shape[0])
+        self.pose = None
+
+    def reset(self, poses):
+        self.pose = poses
+
+    def set_indenter(self, poses):
+        self.pose = poses
+
+    def step(self, st, it):
+        st.zero_()
+        it.fill_(7)
+
+    def markers(self):
+        xy = self.pose[:, 3:5]
+        return xy.repeat_interleave(self.m, dim=0).contiguous()
+
+
+def _sharded_rank(rank, world, port, out):
+    import argparse
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    args = argparse.Namespace(envs=5, warmup=1, steps=2, seed=0, pair_capacity=16384, no_dm_table=False)
+    full = bench.run_sharded(args, rank, world, make_batch=_FakeShardBatch, device=torch.device("cpu"))
+    w = bench.workload(5, 4, 0)
+    m = int(np.asarray(w.pads[0].markers).shape[0])
+    want = np.repeat(w.poses[3, :, 3:5], m, axis=0).reshape(w.n_envs, w.pads_per_env * m, 2)
+    out[rank] = bool(np.array_equal(full.numpy(), want.astype(np.float32)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_sharded_run_partitions_and_gathers_every_frame(capfd):
+    """bench.run_sharded on 2 gloo ranks with host stand-ins for the
+    batches: each rank solves its partition of the 5 environments, and the
+    last frame's gathered field holds every environment's markers in global
+    order on both ranks; rank 0 reports the partition and the converged
+    fraction."""
+    world, port = 2, _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_sharded_rank, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    assert res == {0: True, 1: True}
+    lines = [ln for ln in capfd.readouterr().out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    assert rec["scaling"] == "strong" and rec["n_gpus"] == 2
+    assert sum(rec["partition"]["envs_per_rank"]) == 5
+    assert rec["converged_fraction"] == 1.0
