@@ -191,7 +191,7 @@ int tac_set_indenter(tac_handle h, const float* pose6_dev, const float* twist6_d
  * previous frame, then by its tet count. Results do not depend on the order. */
 int tac_step(tac_handle h, int* pad_status_dev, int* iters_dev, void* stream);
 
-/* Adjoint of the last frame (north star "Differentiation"; the paper itself
+/* Adjoint of the last frame (gradients for calibration; the paper itself
  * calibrates with gradient-free CMA-ES, Sec. 4.2). At the frame's equilibrium
  * x* the gradient g vanishes on the free DOFs, so for a loss L of the
  * markers dL/dtheta = -lambda^T dg/dtheta with H lambda = dL/dx, H the exact
