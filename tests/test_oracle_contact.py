@@ -220,6 +220,37 @@ def _friction_setup(seed=4):
     return pad, ind, lag, x, y, y2
 
 
+@pytest.mark.parametrize("seed", [4, 7])
+def test_friction_lag_carries_the_barrier_forces(seed):
+    """R13's lag: each pair's lagged normal force lambda_n = -kappa m b'(d),
+    applied along its normal with its closest-point weights, reproduces the
+    contact gradient at the frame start on every gel vertex. Where no
+    edge-edge pair is inside its mollifier band (m = 1, m' = 0) the two are
+    the same vector field: a lag built with the wrong sign, without kappa or
+    from the wrong side's weights fails it."""
+    pad, ind, y = _pair_setup(seed)
+    pad.mu_f = 0.5
+    x = pad.rest
+    pairs = BP.candidates(x, y, pad, ind, 2 * DH)
+    d, _, (ty, gid, iid) = En.distances(pairs, x, y, pad, ind)
+    act = d < pad.dhat
+    P = En._slot_positions(gid[act], iid[act], x, y)
+    c = En.edge_cross_sq(P)
+    eps = En.ee_mollifier_eps(ty[act], gid[act], iid[act], pad, ind)
+    assert np.all((eps == 0) | (c >= eps))          # no pair inside the mollifier band here
+    lag = En.friction_lag(pairs, x, y, pad, ind)
+    assert lag["lam"].size == int(act.sum()) > 0
+    g_lag = np.zeros_like(x)
+    for k in range(lag["lam"].size):
+        for sl in range(4):
+            v = lag["gid"][k, sl]
+            if v >= 0:
+                g_lag[v] -= lag["lam"][k] * lag["w"][k, sl] * lag["n"][k]
+    _, g, _, _ = En.contact(pairs, x, y, pad, ind)
+    assert np.abs(g_lag - g).max() <= 1e-12 * np.abs(g).max()
+    assert np.abs(g).max() > 0
+
+
 def test_friction_gradient_matches_central_differences():
     pad, ind, lag, x, y, y2 = _friction_setup()
     E, g, _ = En.friction(lag, x, pad.rest, y2, y, pad)
