@@ -159,3 +159,25 @@ def test_marker_weights_form_partition_of_unity():
     assert np.all(pad.marker_w >= -1e-12)
     Xq = np.einsum("mk,mkc->mc", pad.marker_w, pad.rest[pad.marker_ids])[:, :2]
     assert np.allclose(Xq, pd_markers(w), atol=1e-12)
+
+
+def test_preconditioner_inverts_the_blocks_and_masks_dirichlet_vertices():
+    """R6: block mode gives P_i = K_i^-1 (P_i K_i = I) on free vertices, the
+    scalar mode the inverse of the blocks' diagonals; Dirichlet vertices get
+    P = 0 in both, so z = P g never moves them."""
+    rng = np.random.default_rng(5)
+    n = 12
+    A = rng.normal(size=(n, 3, 3))
+    K = np.einsum("nij,nkj->nik", A, A) + 0.1 * np.eye(3)
+    free = np.ones(n, bool)
+    free[[0, 5, 11]] = False
+    Pb = SV.precondition(K, free, "block")
+    assert np.allclose(np.einsum("nij,njk->nik", Pb[free], K[free]), np.eye(3), atol=1e-10)
+    assert np.all(Pb[~free] == 0.0)
+    Ps = SV.precondition(K, free, "scalar")
+    dg = np.einsum("nii->ni", K[free])
+    assert np.allclose(Ps[free], np.einsum("ni,ij->nij", 1.0 / dg, np.eye(3)))
+    assert np.all(Ps[~free] == 0.0)
+    g = rng.normal(size=(n, 3))
+    assert np.all(SV.apply_P(Pb, g)[~free] == 0.0)
+    assert np.allclose(SV.apply_P(Pb, g)[free], np.linalg.solve(K[free], g[free][..., None])[..., 0])
