@@ -181,3 +181,27 @@ def test_preconditioner_inverts_the_blocks_and_masks_dirichlet_vertices():
     g = rng.normal(size=(n, 3))
     assert np.all(SV.apply_P(Pb, g)[~free] == 0.0)
     assert np.allclose(SV.apply_P(Pb, g)[free], np.linalg.solve(K[free], g[free][..., None])[..., 0])
+
+
+def test_indenter_pose_is_rotation_vector_then_translation():
+    """The pose (rotation vector, translation) of the indenter: a rotation by
+    theta about z takes e_x to (cos theta, sin theta, 0); the rotation keeps
+    every distance and orientation (det R = 1); the translation applies after
+    it; a zero rotation vector is the identity."""
+    Y = np.array([[1.0, 0.0, 0.0], [0.0, 2.0, 0.0], [0.0, 0.0, 3.0], [1.0, 1.0, 1.0]])
+    th = 0.3
+    y = G.indenter_world(Y, [0.0, 0.0, th, 0.0, 0.0, 0.0])
+    assert np.allclose(y[0], [np.cos(th), np.sin(th), 0.0], atol=1e-15)
+    assert np.allclose(y[2], [0.0, 0.0, 3.0], atol=1e-15)
+    rng = np.random.default_rng(2)
+    rv, t = rng.normal(size=3) * 0.4, rng.normal(size=3) * 1e-3
+    y = G.indenter_world(Y, np.concatenate([rv, t]))
+    y0 = G.indenter_world(Y, np.concatenate([rv, np.zeros(3)]))
+    assert np.allclose(y - y0, t, atol=1e-15)
+    dY = np.linalg.norm(Y[:, None] - Y[None], axis=2)
+    dy = np.linalg.norm(y0[:, None] - y0[None], axis=2)
+    assert np.allclose(dY, dy, atol=1e-14)
+    R = np.linalg.lstsq(Y[:3], y0[:3], rcond=None)[0].T
+    assert np.linalg.det(R) == pytest.approx(1.0, abs=1e-12)
+    assert np.allclose(R @ rv, rv, atol=1e-12)                       # the axis stays fixed
+    assert np.allclose(G.indenter_world(Y, np.zeros(6)), Y, atol=0)
