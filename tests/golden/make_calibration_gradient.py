@@ -11,7 +11,7 @@ computes. Steps of 1e-4 and 3e-5 of each parameter.
   python tests/golden/make_calibration_gradient.py
 
 Only oracle/ and the scene generator are called; one spawned process per
-loss evaluation (12 of them), about 10 minutes on 8 host cores.
+loss evaluation (13 of them), about 25 minutes on 8 host cores.
 """
 import multiprocessing
 import os
